@@ -1,0 +1,184 @@
+/*
+ * ccfr.h - C ABI of the B300 (sm_103a) implementation of Convex Collision-Free
+ * Regions (CCFR): per-vertex convex regions built from nearby vertex-face,
+ * edge-edge and point-point pairs, projection of XPBD iterates into them, and
+ * the XPBD substep that runs both inside every solver iteration.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Positions are float4 records (x, y, z, w) laid out as 4 consecutive
+ *    floats per vertex, 16-byte aligned; w is the vertex's inverse mass
+ *    (0 = static obstacle vertex).  Velocities use the same layout (w unused).
+ *  - Pointers documented as "device" must be CUDA device (or managed) memory of
+ *    the device that was current at ccfr_create; "host" pointers are ordinary
+ *    host memory.  The caller owns every buffer it passes in.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    enqueue work on it and return without synchronising, except where noted.
+ *  - Host-detectable errors are returned at once and leave the context
+ *    unchanged.  Conditions found on the device (non-finite input, plane-list
+ *    overflow) are recorded in the context and reported by ccfr_get_stats.
+ *  - Nothing in this library traps or aborts; no call waits without a bound.
+ *  - A context is not thread-safe: calls on one context must be serialised by
+ *    the caller.  Distinct contexts are independent.
+ *
+ * Citations refer to the paper "Convex Collision-Free Regions" (sections,
+ * equations and algorithms).
+ */
+#ifndef CCFR_H
+#define CCFR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCFR_OK = 0,
+    CCFR_ERR_INVALID_ARG = 1,   /* bad pointer, size, alignment or parameter   */
+    CCFR_ERR_CAPACITY = 2,      /* an output buffer given by the caller is too small */
+    CCFR_ERR_OOM = 3,           /* device allocation failed in ccfr_create     */
+    CCFR_ERR_CUDA = 4,          /* a CUDA runtime call failed                   */
+    CCFR_ERR_TIMEOUT = 5,       /* a bounded wait gave up                       */
+    CCFR_ERR_NONFINITE = 6,     /* a position or velocity was NaN or infinite   */
+    CCFR_ERR_STATE = 7          /* call out of order (e.g. project before build) */
+} ccfr_status;
+
+/* Option bits of ccfr_params.flags. */
+enum {
+    CCFR_FLAG_STORE_KEYS = 1u << 0,  /* store each plane's pair key (tests, tooling) */
+    CCFR_FLAG_EARLY_EXIT = 1u << 1,  /* stop the iteration loop once converged (Alg. 4) */
+    CCFR_FLAG_NO_GRAPH = 1u << 2     /* launch ccfr_step kernel by kernel, no CUDA graph */
+};
+
+/* Parameters of one scene (paper Table 3 and Sec. 3.2, 4.1; Alg. 2, 4). */
+typedef struct {
+    float r;              /* search radius: pairs with gap phi < 2r form planes (Sec. 3.1), and
+                             the max step per iteration (Alg. 4)                          */
+    float xi;             /* offset / minimum separation (Eq. 2)                          */
+    float delta;          /* repulsion range of the soft response; enlarges the AABB pad  */
+    float pad;            /* AABB enlargement r + xi/2 + delta/2 (Sec. 4.1), binary32     */
+    float eps_retract;    /* retraction margin eps (Sec. 3.2), scene units               */
+    float eps_dep;        /* dependence tolerance of Alg. 1                               */
+    float tau_feas;       /* tolerance of the final feasibility check                     */
+    int max_passes;       /* n_maxIterations of Alg. 2; n_max + 1 passes are run          */
+    int solver_iters;     /* solver iterations of Alg. 4                                  */
+    int plane_capacity;   /* planes kept per vertex (K); must be a multiple of 32, >= 32  */
+    float cell_size;      /* uniform-grid cell size; 0 = largest padded primitive extent  */
+    float dt;             /* substep (Alg. 4)                                              */
+    float gravity[3];
+    float compliance;     /* XPBD compliance of the edge-distance constraints             */
+    unsigned flags;       /* CCFR_FLAG_*                                                   */
+} ccfr_params;
+
+/* Topology of one scene.  All arrays are device pointers, read at ccfr_create
+ * only (copied into the context). */
+typedef struct {
+    int n_verts, n_edges, n_tris;
+    const int* edges;      /* n_edges x 2, each (a, b) with a < b, sorted lexicographically,
+                              unique: the unique edges of the triangles plus polyline edges */
+    const int* tris;       /* n_tris x 3 vertex ids (may be NULL when n_tris == 0)         */
+    const float* rest_x;   /* n_verts x 4 rest positions; edge rest lengths are taken from
+                              them (may be NULL: rest lengths from the first step's x)      */
+} ccfr_mesh;
+
+/* Counters accumulated since the last ccfr_reset_stats (device-side, read by
+ * ccfr_get_stats).  Per-iteration quantities are summed over iterations. */
+typedef struct {
+    unsigned long long cand_vf, cand_ee, cand_vv;     /* broad-phase candidates         */
+    unsigned long long pairs_vf, pairs_ee, pairs_vv;  /* accepted pairs (phi < 2r)      */
+    unsigned long long planes;                        /* planes emitted                 */
+    unsigned long long overflow_verts;                /* vertices over the capacity     */
+    unsigned long long violated_verts;                /* vertices with a violated plane */
+    unsigned long long halts;                         /* vertices reset to x (Alg. 2)   */
+    unsigned long long ee_fp64;                       /* near-parallel EE solved in FP64 */
+    unsigned long long feas_fp64;                     /* final checks decided in FP64   */
+    unsigned long long feas_halts;                    /* halts caused by the final check */
+    unsigned long long iterations;                    /* solver iterations executed     */
+    unsigned long long steps;                         /* ccfr_step calls                */
+    unsigned int max_planes;                          /* largest per-vertex plane count */
+    unsigned int error_flags;                         /* bit 0 non-finite input         */
+} ccfr_stats;
+
+typedef struct ccfr_ctx ccfr_ctx;
+
+/* Create a context for one scene: copies the topology, computes edge
+ * colours and rest lengths, and allocates every workspace (grid, plane lists,
+ * multipliers).  No later call allocates device memory.  `stream` orders the
+ * set-up copies.  On failure *out is NULL. */
+ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out);
+
+/* Release the context and all its device memory (synchronises the context's work). */
+ccfr_status ccfr_destroy(ccfr_ctx* ctx);
+
+/* Build every vertex's convex region at the collision-free configuration x
+ * (device, n_verts x 4): broad phase (uniform-grid spatial hash), narrow phase
+ * (Alg. 3 over all VF, EE and point-point pairs; contact normal Eq. 1,
+ * half-space Eq. 2-3), compaction into per-vertex lists of at most
+ * plane_capacity planes (n, d) with (x' - x) . n + d >= 0.  A vertex that
+ * receives more planes than the capacity is marked overflowed: projection
+ * then bounds its step by max(0, min d) instead.  The regions stay in the
+ * context for ccfr_project and ccfr_copy_regions. */
+ccfr_status ccfr_build_regions(ccfr_ctx* ctx, const float* x, void* stream);
+
+/* Project candidate positions into the regions of the last build
+ * (Alg. 2 calling Alg. 1, with the retraction and halt of Sec. 3.2, and a
+ * final feasibility check).  x: device, the build positions; x_io: device,
+ * in = candidates x', out = projected x* (w untouched).  halt_out: optional
+ * device array of n_verts bytes, 1 where the vertex was reset to x.
+ * Returns CCFR_ERR_STATE when no region has been built. */
+ccfr_status ccfr_project(ccfr_ctx* ctx, const float* x, float* x_io, unsigned char* halt_out, void* stream);
+
+/* One XPBD substep (Alg. 4): predict, then solver_iters iterations of
+ * {build regions at x_c, restart from the prediction, XPBD edge sweep,
+ * project, clamp the step to r, convergence test}, then the implicit-Euler
+ * update.  x, v: device, n_verts x 4, updated in place.  The iteration loop is
+ * recorded once per (x, v) pair as a CUDA graph and replayed (unless
+ * CCFR_FLAG_NO_GRAPH). */
+ccfr_status ccfr_step(ccfr_ctx* ctx, float* x, float* v, void* stream);
+
+/* ccfr_step on host buffers: copies x and v (host, n_verts x 4 floats each,
+ * preferably pinned) to the context's device buffers, steps, copies them back,
+ * and synchronises `stream` before returning. */
+ccfr_status ccfr_step_host(ccfr_ctx* ctx, float* x_host, float* v_host, void* stream);
+
+/* Candidate pairs of the broad phase at x (device): vertex-face (v, t),
+ * edge-edge (e, f) with e < f, and point-point (p, q) with p < q, written as
+ * int pairs into the device arrays vf, ee, vv (capacities in pairs).  The
+ * order inside each list is unspecified.  Counts are written to the host
+ * array counts[3] after the call synchronises `stream`; if any count exceeds
+ * its capacity, CCFR_ERR_CAPACITY is returned and the lists are truncated. */
+ccfr_status ccfr_get_candidates(ccfr_ctx* ctx, const float* x, int* vf, long cap_vf, int* ee, long cap_ee,
+                                int* vv, long cap_vv, long* counts, void* stream);
+
+/* Copy the current regions out: planes (device, n_verts * capacity * 4 floats,
+ * vertex-major: slot j of vertex v at [(v*capacity + j)*4]), keys (device,
+ * n_verts * capacity u64, or NULL; valid only with CCFR_FLAG_STORE_KEYS),
+ * count (device, n_verts ints: planes received, may exceed capacity),
+ * dmin_drop (device, n_verts floats: smallest d among planes beyond the
+ * capacity, +inf if none; or NULL). */
+ccfr_status ccfr_copy_regions(ccfr_ctx* ctx, float* planes, unsigned long long* keys, int* count,
+                              float* dmin_drop, void* stream);
+
+/* Replace the current regions with caller-provided ones (same layout as
+ * ccfr_copy_regions, `capacity` slots per vertex, capacity <= the context's).
+ * Used to feed externally built regions to ccfr_project. */
+ccfr_status ccfr_load_regions(ccfr_ctx* ctx, const float* planes, const int* count, int capacity, void* stream);
+
+/* Context geometry: n_verts, plane capacity, number of edge colours. */
+ccfr_status ccfr_get_info(const ccfr_ctx* ctx, int* n_verts, int* capacity, int* n_colors);
+
+/* Synchronise the context's pending work and read the counters. */
+ccfr_status ccfr_get_stats(ccfr_ctx* ctx, ccfr_stats* out);
+
+/* Zero the counters (enqueued on `stream`). */
+ccfr_status ccfr_reset_stats(ccfr_ctx* ctx, void* stream);
+
+/* Human-readable name of a status code (static string). */
+const char* ccfr_status_string(ccfr_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCFR_H */

@@ -1,0 +1,267 @@
+"""ctypes front end of the FP64 CCFR oracle (``ccfr_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg use this module to compute what the CUDA library must
+reproduce.  The library itself never imports it, and nothing here calls the
+library.  ``build()`` compiles the C source with gcc into ``oracle/_build``.
+
+Each wrapper names the part of the paper its C function follows; the C file's
+header lists the readings (R1-R16) taken where the paper is silent or garbled.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "ccfr_oracle.c"
+_LIB = _HERE / "_build" / "libccfr_oracle.so"
+_lib = None
+
+
+class OrcParams(C.Structure):
+    _fields_ = [
+        ("r", C.c_double), ("xi", C.c_double), ("delta", C.c_double),
+        ("pad", C.c_float),
+        ("eps", C.c_double), ("eps_dep", C.c_double), ("tau_feas", C.c_double),
+        ("band", C.c_double),
+        ("n_max", C.c_int), ("iters", C.c_int), ("capacity", C.c_int), ("early_exit", C.c_int),
+        ("dt", C.c_double), ("g", C.c_double * 3), ("compliance", C.c_double),
+    ]
+
+
+class OrcStepInfo(C.Structure):
+    _fields_ = [
+        ("iters_run", C.c_int),
+        ("planes", C.c_long), ("violated", C.c_long), ("halts", C.c_long),
+        ("overflow", C.c_long), ("shortened", C.c_long),
+        ("any_band", C.c_int),
+    ]
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
+        return _LIB
+    _LIB.parent.mkdir(parents=True, exist_ok=True)
+    tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", str(tmp), str(_SRC), "-lm"])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(str(build()))
+        P = C.c_void_p
+        _lib.orc_candidates.restype = C.c_long
+        _lib.orc_candidates.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_float, C.c_int, P, P]
+        _lib.orc_build.restype = C.c_void_p
+        _lib.orc_build.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcParams)]
+        _lib.orc_regions_total.restype = C.c_long
+        _lib.orc_regions_total.argtypes = [P]
+        _lib.orc_regions_export.argtypes = [P, P, P, P, P, P, P, P]
+        _lib.orc_regions_free.argtypes = [P]
+        _lib.orc_project.restype = C.c_long
+        _lib.orc_project.argtypes = [P, P, P, C.c_int, P, P, P, P, C.POINTER(OrcParams), P, P, P]
+        _lib.orc_ortho_sequence.argtypes = [P, P, P, C.c_int, C.c_double, P]
+        _lib.orc_edge_colors.restype = C.c_int
+        _lib.orc_edge_colors.argtypes = [P, C.c_int, C.c_int, P]
+        _lib.orc_step.restype = C.c_int
+        _lib.orc_step.argtypes = [P, P, P, C.c_int, P, C.c_int, P, C.c_int, P,
+                                  C.POINTER(OrcParams), P, C.POINTER(OrcStepInfo)]
+        _lib.orc_rest_lengths.argtypes = [P, P, C.c_int, P]
+        _lib.orc_min_distances.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.c_double, P]
+        _lib.orc_count_edge_triangle_intersections.restype = C.c_long
+        _lib.orc_count_edge_triangle_intersections.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int]
+        _lib.orc_closest_point_triangle.argtypes = [P, P, P, P, P, P]
+        _lib.orc_closest_segments.argtypes = [P, P, P, P, P, P]
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None and a.size else None
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
+                iters: int | None = None, early_exit: bool = False,
+                eps_dep: float | None = None) -> OrcParams:
+    g = p.get("gravity", (0.0, -9.81, 0.0))
+    o = OrcParams()
+    o.r, o.xi, o.delta = p["r"], p["xi"], p.get("delta", 0.0)
+    o.pad = np.float32(p["pad"])
+    o.eps, o.eps_dep, o.tau_feas = p["eps"], p["eps_dep"] if eps_dep is None else eps_dep, p["tau_feas"]
+    o.band = band
+    o.n_max = p["n_max"]
+    o.iters = p["iters"] if iters is None else iters
+    o.capacity = p.get("plane_capacity", 0) if capacity is None else capacity
+    o.early_exit = int(early_exit)
+    o.dt = p["dt"]
+    o.g[0], o.g[1], o.g[2] = g
+    o.compliance = p.get("compliance", 0.0)
+    return o
+
+
+def candidates(x4: np.ndarray, edges: np.ndarray, tris: np.ndarray, pad: float, brute: bool = False):
+    """Candidate sets C_VF, C_EE, C_VV under the binary32 padded-AABB
+    predicate with the exclusions of Alg. 3, each sorted lexicographically."""
+    L = lib()
+    x4 = _c(x4, np.float32)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    counts = np.zeros(3, np.int64)
+    args = (_p(x4), len(x4), _p(e), len(e), _p(t), len(t), C.c_float(pad), int(brute))
+    tot = L.orc_candidates(*args, None, _p(counts))
+    out = np.zeros((max(tot, 1), 2), np.int32)
+    L.orc_candidates(*args, _p(out), _p(counts))
+    c0, c1, c2 = (int(c) for c in counts)
+    return {"vf": out[:c0], "ee": out[c0:c0 + c1], "vv": out[c0 + c1:c0 + c1 + c2]}
+
+
+def build_regions(x3: np.ndarray, x4w: np.ndarray, edges, tris, params: OrcParams):
+    """Per-vertex constraint sets (Alg. 3 over all vertices), CSR by vertex,
+    planes sorted by key within a vertex."""
+    L = lib()
+    x3 = _c(x3, np.float64)
+    x4w = _c(x4w, np.float32)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    n = len(x3)
+    h = L.orc_build(_p(x3), _p(x4w), n, _p(e), len(e), _p(t), len(t), C.byref(params))
+    try:
+        tot = L.orc_regions_total(h)
+        offs = np.zeros(n + 1, np.int64)
+        planes = np.zeros((max(tot, 1), 4), np.float64)
+        phi = np.zeros(max(tot, 1), np.float64)
+        key = np.zeros(max(tot, 1), np.uint64)
+        dlimit = np.zeros(n, np.float64)
+        vflag = np.zeros(n, np.uint8)
+        ca = np.zeros(6, np.int64)
+        L.orc_regions_export(h, _p(offs), _p(planes), _p(phi), _p(key), _p(dlimit), _p(vflag), _p(ca))
+    finally:
+        L.orc_regions_free(h)
+    return {"offs": offs, "planes": planes[:tot], "phi": phi[:tot], "key": key[:tot],
+            "dlimit": dlimit, "vflag": vflag, "cand": ca[:3], "acc": ca[3:]}
+
+
+def project(x3, xp3, w, offs, planes4, keys, dlimit, params: OrcParams):
+    """Alg. 2 (+ Alg. 1, retraction, halt, final check) for every vertex.
+    Returns (x_star, halt, band, nviol)."""
+    L = lib()
+    x3 = _c(x3, np.float64)
+    out = _c(xp3, np.float64).copy()
+    w = _c(w, np.float64)
+    offs = _c(offs, np.int64)
+    planes4 = _c(planes4, np.float64).reshape(-1, 4)
+    keys = _c(keys, np.uint64)
+    dl = None if dlimit is None else _c(dlimit, np.float64)
+    n = len(x3)
+    halt = np.zeros(n, np.uint8)
+    band = np.zeros(n, np.uint8)
+    nviol = np.zeros(n, np.int32)
+    if planes4.size == 0:
+        planes4 = np.zeros((1, 4))
+        keys = np.zeros(1, np.uint64)
+    L.orc_project(_p(x3), _p(out), _p(w), n, _p(offs), _p(planes4), _p(keys), _p(dl),
+                  C.byref(params), _p(halt), _p(band), _p(nviol))
+    return out, halt, band, nviol
+
+
+def ortho_sequence(x0, normals, b, eps_dep=1e-12):
+    """Alg. 1 applied to planes n_i . x = b_i in order from x0 (no retraction)."""
+    L = lib()
+    x0 = _c(x0, np.float64)
+    normals = _c(normals, np.float64).reshape(-1, 3)
+    b = _c(b, np.float64)
+    out = np.zeros(3)
+    L.orc_ortho_sequence(_p(x0), _p(normals), _p(b), len(b), C.c_double(eps_dep), _p(out))
+    return out
+
+
+def edge_colors(edges, n):
+    L = lib()
+    e = _c(edges, np.int32)
+    col = np.zeros(max(len(e), 1), np.int32)
+    nc = L.orc_edge_colors(_p(e), len(e), n, _p(col))
+    return col[: len(e)], nc
+
+
+def rest_lengths(x3, edges):
+    L = lib()
+    x3 = _c(x3, np.float64)
+    e = _c(edges, np.int32)
+    out = np.zeros(max(len(e), 1))
+    L.orc_rest_lengths(_p(x3), _p(e), len(e), _p(out))
+    return out[: len(e)]
+
+
+def step(x3, v3, x4w, edges, tris, rest, params: OrcParams):
+    """One substep of Alg. 4.  Returns (x, v, info, vband)."""
+    L = lib()
+    x = _c(x3, np.float64).copy()
+    v = _c(v3, np.float64).copy()
+    x4w = _c(x4w, np.float32)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    rest = _c(rest, np.float64)
+    vband = np.zeros(len(x), np.uint8)
+    info = OrcStepInfo()
+    rc = L.orc_step(_p(x), _p(v), _p(x4w), len(x), _p(e), len(e), _p(t), len(t), _p(rest),
+                    C.byref(params), _p(vband), C.byref(info))
+    if rc != 0:
+        raise RuntimeError("oracle step failed (edge colouring needs more than 64 colours)")
+    return x, v, info, vband
+
+
+def min_distances(x3, x4w, edges, tris, cutoff):
+    """(min VF, min EE, min VV) distance over non-adjacent pairs, capped at cutoff."""
+    L = lib()
+    x3 = _c(x3, np.float64)
+    x4w = _c(x4w, np.float32)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    out = np.zeros(3)
+    L.orc_min_distances(_p(x3), _p(x4w), len(x3), _p(e), len(e), _p(t), len(t), C.c_double(cutoff), _p(out))
+    return out
+
+
+def count_edge_triangle_intersections(x3, edges, tris):
+    L = lib()
+    x3 = _c(x3, np.float64)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    return int(L.orc_count_edge_triangle_intersections(_p(x3), len(x3), _p(e), len(e), _p(t), len(t)))
+
+
+def closest_point_triangle(p, a, b, c):
+    L = lib()
+    args = [_c(v, np.float64) for v in (p, a, b, c)]
+    q = np.zeros(3)
+    bary = np.zeros(3)
+    L.orc_closest_point_triangle(*[_p(v) for v in args], _p(q), _p(bary))
+    return q, bary
+
+
+def closest_segments(p1, q1, p2, q2):
+    L = lib()
+    args = [_c(v, np.float64) for v in (p1, q1, p2, q2)]
+    s = np.zeros(1)
+    t = np.zeros(1)
+    L.orc_closest_segments(*[_p(v) for v in args], _p(s), _p(t))
+    return float(s[0]), float(t[0])
+
+
+def scene_scale(x4: np.ndarray) -> float:
+    """Diagonal L of the scene's bounding box (the parity tolerance scale)."""
+    p = np.asarray(x4)[:, :3].astype(np.float64)
+    return float(np.linalg.norm(p.max(0) - p.min(0)))
