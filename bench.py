@@ -1,0 +1,353 @@
+"""Benchmark of the CCFR hot path on B300: region build + projection inside
+the XPBD substep (Alg. 4), on the self-colliding cloth stack workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on rank 0.  `value` is whole-job throughput in vertex-iterations
+per second (movable vertices x executed solver iterations / device time),
+inputs resident in HBM; `e2e` is the same metric through ccfr_step_host
+(host buffers, copies inside the timed region).  Ranks run independent
+replicas of the scene (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2607_26901_b300 import scenes as S  # noqa: E402
+
+METRIC = "vertex region-build+project updates/sec and % HBM roofline; served p50/p99 step ms"
+UNIT = "vertex-iter/s"
+
+WORKLOADS = {
+    # name: (builder, description)
+    "cloth_stack": (lambda seed: S.cloth_stack(seed=seed),
+                    "self-colliding stack: 4 layers of 256x256 cloth (262,144 verts) 2 mm apart, "
+                    "iid U(-0.5,0.5) m/s velocities, r=2 mm, xi=1 mm, dt=1/60 s, 20 XPBD iterations"),
+    "cloth_stack_128": (lambda seed: S.cloth_stack(n_side=128, seed=seed),
+                        "profiling case of the stack recipe: 4 layers of 128x128 cloth (65,536 verts)"),
+    "cloth_on_sphere": (lambda seed: S.cloth_on_sphere(seed=seed),
+                        "32x32 cloth (1,024 verts) on a static 4,000-tri sphere, 10 iterations"),
+    "wires": (lambda seed: S.wires(seed=seed),
+              "16,384 helical strands x 64 segments (1,064,960 verts) over a static grate, 10 iterations"),
+}
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted((ROOT / "paper_2607_26901_b300" / "csrc").glob("*")):
+        h.update(f.read_bytes())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> tuple[float, str]:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        try:
+            d = json.loads(p.read_text())
+            for k in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+                if k in d and d[k]:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self) -> dict:
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) >= 9:
+                for nm, val in zip(names, r[5:9]):
+                    if val.strip().lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2):
+    """Bounded CPU sample of the stack workload run by the FP64 oracle:
+    4 layers of n_side^2 vertices, one substep of `iters` iterations."""
+    from oracle import oracle as O
+    sc = S.cloth_stack(n_side=n_side, seed=seed)
+    P = O.make_params(sc.params, iters=iters)
+    x = sc.x[:, :3].astype(np.float64)
+    v = sc.v[:, :3].astype(np.float64)
+    rest = O.rest_lengths(x, sc.edges)
+    t0 = time.perf_counter()
+    O.step(x, v, sc.x, sc.edges, sc.tris, rest, P)
+    dt = time.perf_counter() - t0
+    units = sc.n_movable * iters
+    return units / dt, dt, f"cloth stack recipe at 4 layers x {n_side}x{n_side} ({sc.n_verts} verts), " \
+                           f"1 substep x {iters} iterations, seed {seed}"
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cloth_stack", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    builder, desc = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        run_reference(args, ws, rank, desc)
+        return
+
+    import torch
+    from paper_2607_26901_b300 import ccfr
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    sc = builder(2 + rank if args.workload.startswith("cloth_stack") else rank + 1)
+    iters = sc.params["iters"]
+    x = torch.as_tensor(sc.x).cuda().contiguous()
+    v = torch.as_tensor(sc.v).cuda().contiguous()
+    ctx = ccfr.Context.from_scene(sc)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(x, v)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        # wait for nvidia-smi to deliver its first sample so that its start-up
+        # does not overlap the timed region
+        t_wait = time.perf_counter()
+        while not sampler.rows and time.perf_counter() - t_wait < 15.0:
+            time.sleep(0.05)
+        time.sleep(0.2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(x, v)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms_total = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    st = ctx.stats()
+    iters_run = st["iterations"] / max(args.steps, 1)
+    units_per_rank = sc.n_movable * st["iterations"]
+    value = units_per_rank * ws / (ms_total / 1e3)
+
+    # stage split (kernel-by-kernel launch with CUDA events on the same stream)
+    stage = {}
+    n_timed = 2
+    for _ in range(n_timed):
+        for k, ms in ctx.step_timed(x, v).items():
+            stage[k] = stage.get(k, 0.0) + ms / n_timed
+    st2 = ctx.stats()
+    N, E, T = sc.n_verts, len(sc.edges), len(sc.tris)
+    per_iter = max(st["iterations"], 1)
+    planes_vf = st["planes_vf"] / per_iter
+    planes_ee = st["planes_ee"] / per_iter
+    planes_vv = st["planes_vv"] / per_iter
+    planes_stored = st["planes"] / per_iter
+    n_pts = len(S.isolated_points(sc.x, sc.edges))
+    # algorithmic bytes per launch (one launch per iteration), per kernel
+    alg = {
+        "emit_vf": 16 * N + 12 * T + 32 * T + 16 * planes_vf + 4 * N,
+        "emit_ee": 16 * N + 8 * E + 32 * E + 16 * planes_ee + 4 * N,
+        "emit_pp": 16 * n_pts + 32 * n_pts + 16 * planes_vv,
+        "project": 52 * N + 16 * planes_stored,
+        "xpbd": 8 * E + 4 * E + 4 * E * 2 + 2 * 16 * N,
+        "grid_scatter": 16 * N + 8 * E + 12 * T + 32 * (T + E + n_pts),
+    }
+    iters_timed = iters
+    kernel_ms = {k: stage.get(k, 0.0) / iters_timed for k in alg}
+    dom = max(kernel_ms, key=lambda k: kernel_ms[k])
+    peak, peak_kind = measured_peaks()
+    achieved = alg[dom] / (kernel_ms[dom] / 1e3) / 1e9 if kernel_ms[dom] > 0 else 0.0
+    traffic = None
+    tp = ROOT / "profiles" / "traffic.json"
+    if tp.exists():
+        try:
+            td = json.loads(tp.read_text())
+            ent = td.get(args.workload, {}).get(dom)
+            if ent and ent.get("kernel_sha") == kernel_sha():
+                traffic = ent.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                "traffic": traffic, "algorithmic_bytes_per_launch": int(alg[dom]),
+                "launch_ms": round(kernel_ms[dom], 4)}
+
+    # e2e through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty((N, 4), dtype=torch.float32).pin_memory()
+        vh = torch.empty((N, 4), dtype=torch.float32).pin_memory()
+        xh.copy_(x.cpu())
+        vh.copy_(v.cpu())
+        xa, va = xh.numpy(), vh.numpy()
+        ke = max(1, min(args.steps, 5))
+        ctx.step_host(xa, va)
+        ctx.reset_stats()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            ctx.step_host(xa, va)
+        t1 = time.perf_counter()
+        te = t1 - t0
+        if dist:
+            t = torch.tensor([te], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            te = float(t.item())
+        st3 = ctx.stats()
+        e2e = {"value": sc.n_movable * st3["iterations"] * ws / te, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": 2 * N * 16}
+
+    n_emit = (2 if T > 0 else 0) + (2 if E > 0 else 0) + (1 if n_pts > 1 else 0)
+    # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours, project, iter_end
+    launches_per_iter = 1 + 1 + 1 + 3 + 1 + 1 + n_emit + ctx.n_colors + 1 + 1
+    gpu_launches = args.steps * (2 + iters * launches_per_iter)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        val, secs, sample = oracle_sample()
+        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               "seconds": round(secs, 2)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc, "verts": N, "movable": sc.n_movable,
+                       "edges": E, "tris": T, "iters_per_step": iters, "iters_run_per_step": iters_run,
+                       "plane_capacity": ctx.capacity, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (plane lists %.1f GB)" % (N * ctx.capacity * 16 / 1e9)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "stage_ms_per_step": {k: round(v_, 4) for k, v_ in stage.items()},
+            "stats_per_iter": {"cand_vf": st["cand_vf"] / per_iter, "cand_ee": st["cand_ee"] / per_iter,
+                               "pairs_vf": st["pairs_vf"] / per_iter, "pairs_ee": st["pairs_ee"] / per_iter,
+                               "planes": planes_stored, "max_planes": st2["max_planes"],
+                               "overflow_verts": st["overflow_verts"] / per_iter,
+                               "violated_verts": st["violated_verts"] / per_iter,
+                               "halts": st["halts"] / per_iter, "ee_fp64": st["ee_fp64"] / per_iter,
+                               "feas_fp64": st["feas_fp64"] / per_iter,
+                               "proj_smem_passes": st["aux"][0] / per_iter, "proj_full_passes": st["aux"][1] / per_iter,
+                               "proj_violated_planes": st["aux"][2] / per_iter, "big_tris": st["aux"][3] / per_iter,
+                               "big_edges": st["aux"][4] / per_iter, "proj_retries": st["aux"][5] / per_iter},
+            "kernel_sha": kernel_sha(),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, ws, rank, desc):
+    """The FP64 oracle timed on the host cores, on bounded samples of the
+    workload (the reference arm: the paper's method in its own precision)."""
+    if rank != 0:
+        return
+    vals = []
+    sample = None
+    for i in range(args.warmup + args.steps):
+        val, secs, sample = oracle_sample(iters=1, n_side=48)
+        if i >= args.warmup:
+            vals.append((val, secs))
+    total_units = sum(v * s for v, s in vals)
+    total_s = sum(s for _, s in vals)
+    value = total_units / total_s
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total_s / max(len(vals), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

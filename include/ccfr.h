@@ -64,7 +64,8 @@ typedef struct {
     int max_passes;       /* n_maxIterations of Alg. 2; n_max + 1 passes are run          */
     int solver_iters;     /* solver iterations of Alg. 4                                  */
     int plane_capacity;   /* planes kept per vertex (K); must be a multiple of 32, >= 32  */
-    float cell_size;      /* uniform-grid cell size; 0 = largest padded primitive extent  */
+    float cell_size;      /* uniform-grid cell size; 0 = cell_factor x mean padded extent */
+    float cell_factor;    /* cell size in mean padded primitive extents; 0 = 1.5          */
     float dt;             /* substep (Alg. 4)                                              */
     float gravity[3];
     float compliance;     /* XPBD compliance of the edge-distance constraints             */
@@ -87,7 +88,8 @@ typedef struct {
 typedef struct {
     unsigned long long cand_vf, cand_ee, cand_vv;     /* broad-phase candidates         */
     unsigned long long pairs_vf, pairs_ee, pairs_vv;  /* accepted pairs (phi < 2r)      */
-    unsigned long long planes;                        /* planes emitted                 */
+    unsigned long long planes_vf, planes_ee, planes_vv; /* planes emitted per pair kind  */
+    unsigned long long planes;                        /* planes seen by the projection  */
     unsigned long long overflow_verts;                /* vertices over the capacity     */
     unsigned long long violated_verts;                /* vertices with a violated plane */
     unsigned long long halts;                         /* vertices reset to x (Alg. 2)   */
@@ -96,6 +98,12 @@ typedef struct {
     unsigned long long feas_halts;                    /* halts caused by the final check */
     unsigned long long iterations;                    /* solver iterations executed     */
     unsigned long long steps;                         /* ccfr_step calls                */
+    unsigned long long aux[8];                        /* diagnostics: [0] projection passes
+                                                         run from shared memory, [1] passes
+                                                         over the full list, [2] violated
+                                                         planes processed, [3] oversized
+                                                         triangles, [4] oversized edges,
+                                                         [5] candidate-list retries          */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
 } ccfr_stats;
@@ -136,6 +144,22 @@ ccfr_status ccfr_project(ccfr_ctx* ctx, const float* x, float* x_io, unsigned ch
  * recorded once per (x, v) pair as a CUDA graph and replayed (unless
  * CCFR_FLAG_NO_GRAPH). */
 ccfr_status ccfr_step(ccfr_ctx* ctx, float* x, float* v, void* stream);
+
+/* Number of stages reported by ccfr_step_timed. */
+#define CCFR_N_STAGES 14
+
+/* ccfr_step launched kernel by kernel with CUDA events between the stages
+ * (prediction, grid extent, grid count, grid scan, grid scatter, vertex-face
+ * narrow phase, edge-edge narrow phase, point-point narrow phase, XPBD sweep,
+ * projection, bookkeeping, work units, oversized vertex-face and edge-edge
+ * passes): the per-stage split of the paper's timing table
+ * (Table 1: broad, narrow, resolution, XPBD).  stage_ms (host, n_stages >=
+ * CCFR_N_STAGES doubles) receives milliseconds summed over the iterations.
+ * Synchronises `stream`. */
+ccfr_status ccfr_step_timed(ccfr_ctx* ctx, float* x, float* v, double* stage_ms, int n_stages, void* stream);
+
+/* Name of stage i of ccfr_step_timed (static string; "" when out of range). */
+const char* ccfr_stage_name(int i);
 
 /* ccfr_step on host buffers: copies x and v (host, n_verts x 4 floats each,
  * preferably pinned) to the context's device buffers, steps, copies them back,

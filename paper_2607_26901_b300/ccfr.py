@@ -1,0 +1,246 @@
+"""Python binding of libccfr.so (the C ABI declared in include/ccfr.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  Tensors are torch CUDA tensors (contiguous, float32 for
+positions/velocities/planes, int32 for topology); they are passed by
+``data_ptr()`` together with the current CUDA stream.  There is no CPU
+fallback: if the library is missing the import fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libccfr.so"
+
+FLAG_STORE_KEYS = 1 << 0
+FLAG_EARLY_EXIT = 1 << 1
+FLAG_NO_GRAPH = 1 << 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "capacity exceeded", 3: "device allocation failed",
+          4: "CUDA runtime error", 5: "timeout", 6: "non-finite input", 7: "call out of order"}
+
+
+class CcfrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("r", C.c_float), ("xi", C.c_float), ("delta", C.c_float), ("pad", C.c_float),
+                ("eps_retract", C.c_float), ("eps_dep", C.c_float), ("tau_feas", C.c_float),
+                ("max_passes", C.c_int), ("solver_iters", C.c_int), ("plane_capacity", C.c_int),
+                ("cell_size", C.c_float), ("cell_factor", C.c_float), ("dt", C.c_float), ("gravity", C.c_float * 3),
+                ("compliance", C.c_float), ("flags", C.c_uint)]
+
+
+class Mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int), ("n_edges", C.c_int), ("n_tris", C.c_int),
+                ("edges", C.c_void_p), ("tris", C.c_void_p), ("rest_x", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [(n, C.c_ulonglong) for n in
+                ("cand_vf", "cand_ee", "cand_vv", "pairs_vf", "pairs_ee", "pairs_vv", "planes_vf", "planes_ee",
+                 "planes_vv", "planes",
+                 "overflow_verts", "violated_verts", "halts", "ee_fp64", "feas_fp64", "feas_halts",
+                 "iterations", "steps")] + [("aux", C.c_ulonglong * 8), ("max_planes", C.c_uint),
+                                            ("error_flags", C.c_uint)]
+
+    def as_dict(self) -> dict:
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        d["aux"] = [int(v) for v in self.aux]
+        return {k: (v if k == "aux" else int(v)) for k, v in d.items()}
+
+
+_lib = None
+
+
+def lib():
+    """Load libccfr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise ImportError(f"libccfr.so not built ({_LIB_PATH}); run python -m paper_2607_26901_b300.build_lib")
+        L = C.CDLL(str(_LIB_PATH))
+        P = C.c_void_p
+        sig = {
+            "ccfr_create": [C.POINTER(Mesh), C.POINTER(Params), P, C.POINTER(P)],
+            "ccfr_destroy": [P],
+            "ccfr_build_regions": [P, P, P],
+            "ccfr_project": [P, P, P, P, P],
+            "ccfr_step": [P, P, P, P],
+            "ccfr_step_host": [P, P, P, P],
+            "ccfr_step_timed": [P, P, P, P, C.c_int, P],
+            "ccfr_get_candidates": [P, P, P, C.c_long, P, C.c_long, P, C.c_long, P, P],
+            "ccfr_copy_regions": [P, P, P, P, P, P],
+            "ccfr_load_regions": [P, P, P, C.c_int, P],
+            "ccfr_get_info": [P, P, P, P],
+            "ccfr_get_stats": [P, C.POINTER(Stats)],
+            "ccfr_reset_stats": [P, P],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = C.c_int
+        L.ccfr_stage_name.argtypes = [C.c_int]
+        L.ccfr_stage_name.restype = C.c_char_p
+        L.ccfr_status_string.argtypes = [C.c_int]
+        L.ccfr_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return ["ccfr_create", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
+            "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
+            "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string"]
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise CcfrError(rc, what)
+
+
+def make_params(p: dict, flags: int = 0, plane_capacity: int | None = None,
+                iters: int | None = None, cell_size: float = 0.0, cell_factor: float = 0.0) -> Params:
+    o = Params()
+    o.r, o.xi, o.delta, o.pad = p["r"], p["xi"], p.get("delta", 0.0), p["pad"]
+    o.eps_retract, o.eps_dep, o.tau_feas = p["eps"], p["eps_dep"], p["tau_feas"]
+    o.max_passes = p["n_max"]
+    o.solver_iters = p["iters"] if iters is None else iters
+    o.plane_capacity = p.get("plane_capacity", 64) if plane_capacity is None else plane_capacity
+    o.cell_size = cell_size
+    o.cell_factor = cell_factor
+    o.dt = p["dt"]
+    g = p.get("gravity", (0.0, -9.81, 0.0))
+    o.gravity[0], o.gravity[1], o.gravity[2] = g
+    o.compliance = p.get("compliance", 0.0)
+    o.flags = flags
+    return o
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+class Context:
+    """One scene on the current CUDA device (wraps a ccfr_ctx)."""
+
+    def __init__(self, edges, tris, n_verts: int, params: Params, rest_x=None, stream=None):
+        import torch
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.edges = torch.as_tensor(np.asarray(edges, np.int32).reshape(-1, 2)).to(dev).contiguous()
+        self.tris = torch.as_tensor(np.asarray(tris, np.int32).reshape(-1, 3)).to(dev).contiguous()
+        self.n_verts = int(n_verts)
+        rest = None
+        if rest_x is not None:
+            rest = torch.as_tensor(np.asarray(rest_x, np.float32).reshape(-1, 4)).to(dev).contiguous()
+        m = Mesh(self.n_verts, int(self.edges.shape[0]), int(self.tris.shape[0]),
+                 self.edges.data_ptr() if self.edges.numel() else None,
+                 self.tris.data_ptr() if self.tris.numel() else None,
+                 rest.data_ptr() if rest is not None else None)
+        self.params = params
+        h = C.c_void_p()
+        _check(lib().ccfr_create(C.byref(m), C.byref(params), _stream(stream), C.byref(h)), "ccfr_create")
+        self.h = h
+        nv, cap, ncol = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().ccfr_get_info(h, C.byref(nv), C.byref(cap), C.byref(ncol)), "ccfr_get_info")
+        self.capacity = cap.value
+        self.n_colors = ncol.value
+
+    @classmethod
+    def from_scene(cls, scene, flags: int = 0, plane_capacity: int | None = None, iters: int | None = None,
+                   cell_size: float = 0.0, cell_factor: float = 0.0, stream=None):
+        p = make_params(scene.params, flags, plane_capacity, iters, cell_size, cell_factor)
+        return cls(scene.edges, scene.tris, scene.n_verts, p, rest_x=scene.x, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ccfr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- the three calls of the method -------------------------------------
+    def build_regions(self, x, stream=None):
+        _check(lib().ccfr_build_regions(self.h, _ptr(x), _stream(stream)), "ccfr_build_regions")
+
+    def project(self, x, x_io, halt=None, stream=None):
+        _check(lib().ccfr_project(self.h, _ptr(x), _ptr(x_io), _ptr(halt), _stream(stream)), "ccfr_project")
+
+    def step(self, x, v, stream=None):
+        _check(lib().ccfr_step(self.h, _ptr(x), _ptr(v), _stream(stream)), "ccfr_step")
+
+    def step_timed(self, x, v, stream=None) -> dict:
+        """One step launched kernel by kernel; returns {stage: ms}."""
+        n = 14
+        out = (C.c_double * n)()
+        _check(lib().ccfr_step_timed(self.h, _ptr(x), _ptr(v), out, n, _stream(stream)), "ccfr_step_timed")
+        return {lib().ccfr_stage_name(i).decode(): out[i] for i in range(n)}
+
+    def step_host(self, x_host: np.ndarray, v_host: np.ndarray, stream=None):
+        assert x_host.dtype == np.float32 and x_host.flags.c_contiguous
+        assert v_host.dtype == np.float32 and v_host.flags.c_contiguous
+        _check(lib().ccfr_step_host(self.h, x_host.ctypes.data_as(C.c_void_p),
+                                    v_host.ctypes.data_as(C.c_void_p), _stream(stream)), "ccfr_step_host")
+
+    # --- observability --------------------------------------------------------
+    def candidates(self, x, cap: int | None = None, stream=None) -> dict:
+        torch = self.torch
+        cap = cap or 1 << 16
+        while True:
+            bufs = [torch.empty((cap, 2), dtype=torch.int32, device=x.device) for _ in range(3)]
+            counts = (C.c_long * 3)()
+            rc = lib().ccfr_get_candidates(self.h, _ptr(x), _ptr(bufs[0]), cap, _ptr(bufs[1]), cap,
+                                           _ptr(bufs[2]), cap, counts, _stream(stream))
+            if rc == 2:
+                cap = max(counts) + 16
+                continue
+            _check(rc, "ccfr_get_candidates")
+            return {k: bufs[i][: counts[i]].cpu().numpy() for i, k in enumerate(("vf", "ee", "vv"))}
+
+    def regions(self, keys: bool = False, stream=None) -> dict:
+        torch = self.torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        planes = torch.empty((self.n_verts, self.capacity, 4), dtype=torch.float32, device=dev)
+        count = torch.empty(self.n_verts, dtype=torch.int32, device=dev)
+        dmin = torch.empty(self.n_verts, dtype=torch.float32, device=dev)
+        kt = torch.empty((self.n_verts, self.capacity), dtype=torch.int64, device=dev) if keys else None
+        _check(lib().ccfr_copy_regions(self.h, _ptr(planes), _ptr(kt), _ptr(count), _ptr(dmin), _stream(stream)),
+               "ccfr_copy_regions")
+        out = {"planes": planes, "count": count, "dmin_drop": dmin}
+        if keys:
+            out["keys"] = kt
+        return out
+
+    def load_regions(self, planes, count, stream=None):
+        cap = int(planes.shape[1])
+        _check(lib().ccfr_load_regions(self.h, _ptr(planes), _ptr(count), cap, _stream(stream)), "ccfr_load_regions")
+
+    def stats(self) -> dict:
+        s = Stats()
+        rc = lib().ccfr_get_stats(self.h, C.byref(s))
+        if rc not in (0, 6):
+            _check(rc, "ccfr_get_stats")
+        d = s.as_dict()
+        d["status"] = rc
+        return d
+
+    def reset_stats(self, stream=None):
+        _check(lib().ccfr_reset_stats(self.h, _stream(stream)), "ccfr_reset_stats")

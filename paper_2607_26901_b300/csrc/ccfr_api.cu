@@ -1,0 +1,517 @@
+// C ABI of the CCFR library: context set-up, argument checks, launch
+// orchestration and CUDA-graph capture of the substep.  See include/ccfr.h.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ccfr.h"
+#include "ccfr_internal.h"
+
+using namespace ccfr;
+
+namespace {
+
+struct GraphEntry {
+    float* x;
+    float* v;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct ccfr_ctx {
+    int device = 0;
+    ccfr_params prm{};
+    DevCtx dc{};
+    int n_buckets_total = 0;
+    unsigned* tile_sums = nullptr;
+    std::vector<int> color_off;
+    int n_colors = 0;
+    cudaStream_t cap_stream = nullptr;
+    std::vector<GraphEntry> graphs;
+    bool regions_valid = false;
+    bool rest_pending = false;
+    float4* hx = nullptr;
+    float4* hv = nullptr;
+    unsigned long long* pair_count = nullptr;
+    std::vector<void*> allocs;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+template <typename T>
+cudaError_t dalloc(ccfr_ctx* c, T** p, size_t count) {
+    *p = nullptr;
+    size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)p, bytes);
+    if (e == cudaSuccess) c->allocs.push_back((void*)*p);
+    return e;
+}
+
+void free_ctx(ccfr_ctx* c) {
+    if (!c) return;
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+unsigned next_pow2(unsigned v) {
+    unsigned p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+ccfr_status check_params(const ccfr_params* p) {
+    if (!p) return CCFR_ERR_INVALID_ARG;
+    if (!(p->r > 0.f) || !(p->xi >= 0.f) || !(p->delta >= 0.f) || !(p->pad > 0.f)) return CCFR_ERR_INVALID_ARG;
+    if (!(p->eps_retract >= 0.f) || !(p->eps_dep > 0.f) || !(p->tau_feas >= 0.f)) return CCFR_ERR_INVALID_ARG;
+    if (p->max_passes < 0 || p->max_passes > 64 || p->solver_iters < 1 || p->solver_iters > 10000)
+        return CCFR_ERR_INVALID_ARG;
+    if (p->plane_capacity < 32 || p->plane_capacity % 32 != 0 || p->plane_capacity > 65536) return CCFR_ERR_INVALID_ARG;
+    if (!(p->cell_size >= 0.f) || !(p->dt > 0.f) || !(p->compliance >= 0.f)) return CCFR_ERR_INVALID_ARG;
+    if (!(p->cell_factor >= 0.f) || p->cell_factor > 64.f) return CCFR_ERR_INVALID_ARG;
+    return CCFR_OK;
+}
+
+ccfr_status from_cuda(cudaError_t e) { return e == cudaSuccess ? CCFR_OK : CCFR_ERR_CUDA; }
+
+// Enqueue one full substep (Alg. 4) on stream st.
+void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer* tm = nullptr) {
+    if (tm) tm->mark(ST_MISC, st);
+    launch_predict(c->dc, x, v, st);
+    if (tm) tm->mark(ST_PREDICT, st);
+    int early = (c->prm.flags & CCFR_FLAG_EARLY_EXIT) ? 1 : 0;
+    for (int it = 0; it < c->prm.solver_iters; ++it)
+        launch_iteration(c->dc, x, st, c->color_off.data(), c->n_colors, c->tile_sums, c->n_buckets_total, early, tm);
+    launch_update(c->dc, x, v, st);
+    if (tm) tm->mark(ST_MISC, st);
+}
+
+const char* kStageNames[N_STAGES] = {"predict", "grid_extent", "grid_count", "grid_scan", "grid_scatter",
+                                     "emit_vf", "emit_ee", "emit_pp", "xpbd", "project", "misc",
+                                     "grid_units", "emit_vf_big", "emit_ee_big"};
+
+}  // namespace
+
+extern "C" {
+
+const char* ccfr_status_string(ccfr_status s) {
+    switch (s) {
+        case CCFR_OK: return "ok";
+        case CCFR_ERR_INVALID_ARG: return "invalid argument";
+        case CCFR_ERR_CAPACITY: return "output capacity exceeded";
+        case CCFR_ERR_OOM: return "device allocation failed";
+        case CCFR_ERR_CUDA: return "CUDA runtime error";
+        case CCFR_ERR_TIMEOUT: return "bounded wait timed out";
+        case CCFR_ERR_NONFINITE: return "non-finite input";
+        case CCFR_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
+    if (!out) return CCFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || check_params(params) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
+    const int N = mesh->n_verts, E = mesh->n_edges, T = mesh->n_tris;
+    if (N < 0 || E < 0 || T < 0 || N > (1 << 30) || E > (1 << 30) || T > (1 << 30)) return CCFR_ERR_INVALID_ARG;
+    if ((E > 0 && !mesh->edges) || (T > 0 && !mesh->tris)) return CCFR_ERR_INVALID_ARG;
+    if (mesh->rest_x && !aligned16(mesh->rest_x)) return CCFR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // topology to the host: validation, isolated points, edge colours
+    std::vector<int> he(2 * (size_t)E), ht(3 * (size_t)T);
+    if (E && cudaMemcpy(he.data(), mesh->edges, he.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+        return CCFR_ERR_CUDA;
+    if (T && cudaMemcpy(ht.data(), mesh->tris, ht.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+        return CCFR_ERR_CUDA;
+    for (int e = 0; e < E; ++e) {
+        int a = he[2 * e], b = he[2 * e + 1];
+        if (a < 0 || b >= N || a >= b) return CCFR_ERR_INVALID_ARG;
+        if (e > 0) {
+            int pa = he[2 * e - 2], pb = he[2 * e - 1];
+            if (!(pa < a || (pa == a && pb < b))) return CCFR_ERR_INVALID_ARG;
+        }
+    }
+    for (int t = 0; t < T; ++t) {
+        int a = ht[3 * t], b = ht[3 * t + 1], d = ht[3 * t + 2];
+        if (a < 0 || b < 0 || d < 0 || a >= N || b >= N || d >= N || a == b || b == d || a == d)
+            return CCFR_ERR_INVALID_ARG;
+    }
+    std::vector<char> used(N > 0 ? N : 1, 0);
+    for (int e = 0; e < E; ++e) { used[he[2 * e]] = 1; used[he[2 * e + 1]] = 1; }
+    std::vector<int> pts;
+    for (int i = 0; i < N; ++i) if (!used[i]) pts.push_back(i);
+    // greedy first-fit edge colouring in canonical edge order
+    std::vector<unsigned long long> vmask(N > 0 ? N : 1, 0ull);
+    std::vector<int> col(E > 0 ? E : 1, 0);
+    int ncol = 0;
+    for (int e = 0; e < E; ++e) {
+        unsigned long long m = vmask[he[2 * e]] | vmask[he[2 * e + 1]];
+        int k = 0;
+        while (k < 64 && ((m >> k) & 1ull)) ++k;
+        if (k == 64) return CCFR_ERR_INVALID_ARG;
+        col[e] = k;
+        vmask[he[2 * e]] |= 1ull << k;
+        vmask[he[2 * e + 1]] |= 1ull << k;
+        if (k + 1 > ncol) ncol = k + 1;
+    }
+    std::vector<int> coff(ncol + 1, 0);
+    for (int e = 0; e < E; ++e) coff[col[e] + 1]++;
+    for (int k = 0; k < ncol; ++k) coff[k + 1] += coff[k];
+    std::vector<int> ecol(2 * (size_t)E);
+    {
+        std::vector<int> fill(coff.begin(), coff.end() - 1);
+        for (int e = 0; e < E; ++e) {
+            int pos = fill[col[e]]++;
+            ecol[2 * pos] = he[2 * e];
+            ecol[2 * pos + 1] = he[2 * e + 1];
+        }
+    }
+
+    ccfr_ctx* c = new (std::nothrow) ccfr_ctx();
+    if (!c) return CCFR_ERR_OOM;
+    cudaGetDevice(&c->device);
+    c->prm = *params;
+    c->color_off = coff;
+    c->n_colors = ncol;
+    DevCtx& d = c->dc;
+    d.n_verts = N;
+    d.n_edges = E;
+    d.n_tris = T;
+    d.n_pts = (int)pts.size();
+    d.p.r = params->r;
+    d.p.two_r = 2.f * params->r;
+    d.p.xi = params->xi;
+    d.p.pad = params->pad;
+    d.p.eps = params->eps_retract;
+    d.p.eps_dep = params->eps_dep;
+    d.p.tau = params->tau_feas;
+    d.p.dt = params->dt;
+    d.p.gx = params->gravity[0];
+    d.p.gy = params->gravity[1];
+    d.p.gz = params->gravity[2];
+    d.p.alpha_tilde = params->compliance / (params->dt * params->dt);
+    d.p.max_passes = params->max_passes;
+    d.p.K = params->plane_capacity;
+    d.p.cell_size = params->cell_size;
+    // grid geometry: tables of triangles, edges, isolated points, vertices
+    int nk[4] = {T, E, d.n_pts, N};
+    d.n_items = T + E + d.n_pts + N;
+    d.item_base[0] = 0;
+    d.item_base[1] = T;
+    d.item_base[2] = T + E;
+    d.item_base[3] = T + E + d.n_pts;
+    int btot = 0;
+    for (int k = 0; k < 4; ++k) {
+        unsigned M = next_pow2((unsigned)(2 * nk[k] > 64 ? 2 * nk[k] : 64));
+        d.bucket_base[k] = btot;
+        d.bucket_mask[k] = (int)(M - 1);
+        btot += (int)M;
+    }
+    d.bucket_base[4] = btot;
+    c->n_buckets_total = btot;
+    d.n_kind[0] = T;
+    d.n_kind[1] = E;
+    d.n_kind[2] = d.n_pts;
+    d.cell_factor = params->cell_factor > 0.f ? params->cell_factor : 1.5f;
+    d.big_base[0] = 0;
+    d.big_base[1] = T;
+    d.unit_base[0] = 0;
+    d.unit_base[1] = T + 1;
+    d.unit_base[2] = T + 1 + E + 1;
+    int n_units = T + E + d.n_pts + 3;
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) nsm = 148;
+        d.n_sm = nsm;
+    }
+    const int SCAN_TILE = 4096;
+    if ((btot + 1 + SCAN_TILE - 1) / SCAN_TILE > SCAN_TILE) { free_ctx(c); return CCFR_ERR_INVALID_ARG; }
+
+    size_t NK = (size_t)N * params->plane_capacity;
+    bool ok = true;
+    ok &= dalloc(c, &d.planes, NK) == cudaSuccess;
+    if (params->flags & CCFR_FLAG_STORE_KEYS) ok &= dalloc(c, &d.keys, NK) == cudaSuccess;
+    ok &= dalloc(c, &d.count, N) == cudaSuccess;
+    ok &= dalloc(c, &d.dmin_drop, N) == cudaSuccess;
+    ok &= dalloc(c, &d.x_tilde, N) == cudaSuccess;
+    ok &= dalloc(c, &d.x_n, N) == cudaSuccess;
+    ok &= dalloc(c, &d.x_s, N) == cudaSuccess;
+    ok &= dalloc(c, &d.lambda, E) == cudaSuccess;
+    int2* edges = nullptr;
+    int2* edges_col = nullptr;
+    int3* tris = nullptr;
+    int* dpts = nullptr;
+    float* rest = nullptr;
+    ok &= dalloc(c, &edges, E) == cudaSuccess;
+    ok &= dalloc(c, &edges_col, E) == cudaSuccess;
+    ok &= dalloc(c, &rest, E) == cudaSuccess;
+    ok &= dalloc(c, &tris, T) == cudaSuccess;
+    ok &= dalloc(c, &dpts, pts.size()) == cudaSuccess;
+    ok &= dalloc(c, &d.ext_bits, 3) == cudaSuccess;
+    ok &= dalloc(c, &d.bucket_count, (size_t)btot + 1) == cudaSuccess;
+    ok &= dalloc(c, &d.bucket_fill, (size_t)btot) == cudaSuccess;
+    ok &= dalloc(c, &d.item_bucket, d.n_items) == cudaSuccess;
+    ok &= dalloc(c, &d.rec, 2 * (size_t)d.n_items) == cudaSuccess;
+    ok &= dalloc(c, &d.units, (size_t)n_units) == cudaSuccess;
+    ok &= dalloc(c, &d.ext_sum, 3) == cudaSuccess;
+    ok &= dalloc(c, &d.big, (size_t)T + E) == cudaSuccess;
+    ok &= dalloc(c, &d.big_box, 2 * ((size_t)T + E)) == cudaSuccess;
+    ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
+    ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
+    ok &= dalloc(c, &c->tile_sums, SCAN_TILE) == cudaSuccess;
+    ok &= dalloc(c, &d.flags, 2) == cudaSuccess;
+    ok &= dalloc(c, &d.stats, 1) == cudaSuccess;
+    ok &= dalloc(c, &c->pair_count, 3) == cudaSuccess;
+    ok &= dalloc(c, &c->hx, N) == cudaSuccess;
+    ok &= dalloc(c, &c->hv, N) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); free_ctx(c); return CCFR_ERR_OOM; }
+    d.edges = edges;
+    d.edges_col = edges_col;
+    d.rest_col = rest;
+    d.tris = tris;
+    d.pts = dpts;
+
+    cudaError_t err = cudaSuccess;
+    if (E) {
+        err = cudaMemcpyAsync(edges, he.data(), he.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(edges_col, ecol.data(), ecol.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    }
+    if (err == cudaSuccess && T) err = cudaMemcpyAsync(tris, ht.data(), ht.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess && !pts.empty())
+        err = cudaMemcpyAsync(dpts, pts.data(), pts.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d.flags, 0, 2 * sizeof(int), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d.stats, 0, sizeof(DevStats), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d.count, 0, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(d.dmin_drop, 0xFF, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
+    if (err == cudaSuccess && E) {
+        if (mesh->rest_x) launch_rest_lengths(edges_col, (const float4*)mesh->rest_x, rest, E, st);
+        else c->rest_pending = true;
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) { free_ctx(c); return CCFR_ERR_CUDA; }
+    *out = c;
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_destroy(ccfr_ctx* c) {
+    if (!c) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaDeviceSynchronize();
+    free_ctx(c);
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_build_regions(ccfr_ctx* c, const float* x, void* stream) {
+    if (!c || !x || !aligned16(x)) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    launch_clear_regions(c->dc, st);
+    launch_build(c->dc, (const float4*)x, st, MODE_PLANES, nullptr, c->tile_sums, c->n_buckets_total);
+    c->regions_valid = true;
+    return from_cuda(cudaGetLastError());
+}
+
+ccfr_status ccfr_project(ccfr_ctx* c, const float* x, float* x_io, unsigned char* halt_out, void* stream) {
+    if (!c || !x || !x_io || !aligned16(x) || !aligned16(x_io)) return CCFR_ERR_INVALID_ARG;
+    if (!c->regions_valid) return CCFR_ERR_STATE;
+    DeviceGuard g(c->device);
+    launch_project(c->dc, (const float4*)x, (float4*)x_io, halt_out, (cudaStream_t)stream);
+    return from_cuda(cudaGetLastError());
+}
+
+ccfr_status ccfr_step(ccfr_ctx* c, float* x, float* v, void* stream) {
+    if (!c || !x || !v || !aligned16(x) || !aligned16(v)) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->rest_pending) {
+        launch_rest_lengths(c->dc.edges_col, (const float4*)x, (float*)c->dc.rest_col, c->dc.n_edges, st);
+        c->rest_pending = false;
+    }
+    if (c->prm.flags & CCFR_FLAG_NO_GRAPH) {
+        enqueue_step(c, (float4*)x, (float4*)v, st);
+        c->regions_valid = true;
+        return from_cuda(cudaGetLastError());
+    }
+    cudaGraphExec_t exec = nullptr;
+    for (auto& e : c->graphs)
+        if (e.x == x && e.v == v) { exec = e.exec; break; }
+    if (!exec) {
+        // record the substep once for this (x, v) pair and replay it afterwards
+        cudaError_t err = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (err != cudaSuccess) return CCFR_ERR_CUDA;
+        enqueue_step(c, (float4*)x, (float4*)v, c->cap_stream);
+        cudaGraph_t graph = nullptr;
+        err = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (err != cudaSuccess || !graph) { cudaGetLastError(); return CCFR_ERR_CUDA; }
+        err = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (err != cudaSuccess) { cudaGetLastError(); return CCFR_ERR_CUDA; }
+        if (c->graphs.size() >= 16) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back(GraphEntry{x, v, exec});
+    }
+    cudaError_t err = cudaGraphLaunch(exec, st);
+    c->regions_valid = true;
+    return from_cuda(err);
+}
+
+ccfr_status ccfr_step_timed(ccfr_ctx* c, float* x, float* v, double* stage_ms, int n_stages, void* stream) {
+    if (!c || !x || !v || !stage_ms || n_stages < N_STAGES || !aligned16(x) || !aligned16(v)) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->rest_pending) {
+        launch_rest_lengths(c->dc.edges_col, (const float4*)x, (float*)c->dc.rest_col, c->dc.n_edges, st);
+        c->rest_pending = false;
+    }
+    int cap = 16 + c->prm.solver_iters * 16;
+    std::vector<cudaEvent_t> ev(cap);
+    std::vector<int> stg(cap);
+    for (int i = 0; i < cap; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) {
+            for (int k = 0; k < i; ++k) cudaEventDestroy(ev[k]);
+            return CCFR_ERR_CUDA;
+        }
+    StageTimer tm{ev.data(), stg.data(), 0, cap};
+    enqueue_step(c, (float4*)x, (float4*)v, st, &tm);
+    cudaError_t err = cudaStreamSynchronize(st);
+    for (int i = 0; i < n_stages; ++i) stage_ms[i] = 0.0;
+    for (int i = 1; i < tm.n && err == cudaSuccess; ++i) {
+        float ms = 0.f;
+        err = cudaEventElapsedTime(&ms, ev[i - 1], ev[i]);
+        stage_ms[stg[i]] += ms;
+    }
+    for (int i = 0; i < cap; ++i) cudaEventDestroy(ev[i]);
+    c->regions_valid = true;
+    return from_cuda(err);
+}
+
+const char* ccfr_stage_name(int i) { return (i >= 0 && i < N_STAGES) ? kStageNames[i] : ""; }
+
+ccfr_status ccfr_step_host(ccfr_ctx* c, float* x_host, float* v_host, void* stream) {
+    if (!c || !x_host || !v_host) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = (size_t)c->dc.n_verts * sizeof(float4);
+    cudaError_t err = cudaMemcpyAsync(c->hx, x_host, bytes, cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(c->hv, v_host, bytes, cudaMemcpyHostToDevice, st);
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    ccfr_status s = ccfr_step(c, (float*)c->hx, (float*)c->hv, stream);
+    if (s != CCFR_OK) return s;
+    err = cudaMemcpyAsync(x_host, c->hx, bytes, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaMemcpyAsync(v_host, c->hv, bytes, cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    return from_cuda(err);
+}
+
+ccfr_status ccfr_get_candidates(ccfr_ctx* c, const float* x, int* vf, long cap_vf, int* ee, long cap_ee, int* vv,
+                                long cap_vv, long* counts, void* stream) {
+    if (!c || !x || !aligned16(x) || !counts || cap_vf < 0 || cap_ee < 0 || cap_vv < 0) return CCFR_ERR_INVALID_ARG;
+    if ((cap_vf > 0 && !vf) || (cap_ee > 0 && !ee) || (cap_vv > 0 && !vv)) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    PairOutHost po;
+    po.out[0] = vf; po.out[1] = ee; po.out[2] = vv;
+    po.cap[0] = cap_vf; po.cap[1] = cap_ee; po.cap[2] = cap_vv;
+    po.count = c->pair_count;
+    cudaError_t err = cudaMemsetAsync(c->pair_count, 0, 3 * sizeof(unsigned long long), st);
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    launch_build(c->dc, (const float4*)x, st, MODE_PAIRS, &po, c->tile_sums, c->n_buckets_total);
+    unsigned long long h[3];
+    err = cudaMemcpyAsync(h, c->pair_count, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    for (int k = 0; k < 3; ++k) counts[k] = (long)h[k];
+    if (counts[0] > cap_vf || counts[1] > cap_ee || counts[2] > cap_vv) return CCFR_ERR_CAPACITY;
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_copy_regions(ccfr_ctx* c, float* planes, unsigned long long* keys, int* count, float* dmin_drop,
+                              void* stream) {
+    if (!c) return CCFR_ERR_INVALID_ARG;
+    if (!c->regions_valid) return CCFR_ERR_STATE;
+    if (keys && !c->dc.keys) return CCFR_ERR_STATE;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t NK = (size_t)c->dc.n_verts * c->dc.p.K;
+    cudaError_t err = cudaSuccess;
+    if (planes) err = cudaMemcpyAsync(planes, c->dc.planes, NK * sizeof(float4), cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess && keys)
+        err = cudaMemcpyAsync(keys, c->dc.keys, NK * sizeof(unsigned long long), cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess && count)
+        err = cudaMemcpyAsync(count, c->dc.count, (size_t)c->dc.n_verts * sizeof(int), cudaMemcpyDeviceToDevice, st);
+    if (err == cudaSuccess && dmin_drop) launch_dmin_export(c->dc, dmin_drop, st);
+    if (err == cudaSuccess) err = cudaGetLastError();
+    return from_cuda(err);
+}
+
+ccfr_status ccfr_load_regions(ccfr_ctx* c, const float* planes, const int* count, int capacity, void* stream) {
+    if (!c || !planes || !count || capacity < 1 || capacity > c->dc.p.K || !aligned16(planes))
+        return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    launch_load_regions(c->dc, (const float4*)planes, count, capacity, (cudaStream_t)stream);
+    c->regions_valid = true;
+    return from_cuda(cudaGetLastError());
+}
+
+ccfr_status ccfr_get_info(const ccfr_ctx* c, int* n_verts, int* capacity, int* n_colors) {
+    if (!c) return CCFR_ERR_INVALID_ARG;
+    if (n_verts) *n_verts = c->dc.n_verts;
+    if (capacity) *capacity = c->dc.p.K;
+    if (n_colors) *n_colors = c->n_colors;
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_get_stats(ccfr_ctx* c, ccfr_stats* out) {
+    if (!c || !out) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    DevStats s;
+    cudaError_t err = cudaDeviceSynchronize();
+    if (err == cudaSuccess) err = cudaMemcpy(&s, c->dc.stats, sizeof(s), cudaMemcpyDeviceToHost);
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    out->cand_vf = s.cand[0]; out->cand_ee = s.cand[1]; out->cand_vv = s.cand[2];
+    out->pairs_vf = s.pairs[0]; out->pairs_ee = s.pairs[1]; out->pairs_vv = s.pairs[2];
+    out->planes_vf = s.planes_kind[0]; out->planes_ee = s.planes_kind[1]; out->planes_vv = s.planes_kind[2];
+    out->planes = s.planes;
+    out->overflow_verts = s.overflow_verts;
+    out->violated_verts = s.violated_verts;
+    out->halts = s.halts;
+    out->ee_fp64 = s.ee_fp64;
+    out->feas_fp64 = s.feas_fp64;
+    out->feas_halts = s.feas_halts;
+    out->iterations = s.iterations;
+    out->steps = s.steps;
+    for (int i = 0; i < 8; ++i) out->aux[i] = s.aux[i];
+    out->max_planes = s.max_planes;
+    out->error_flags = s.error_flags;
+    return (s.error_flags & ERR_NONFINITE) ? CCFR_ERR_NONFINITE : CCFR_OK;
+}
+
+ccfr_status ccfr_reset_stats(ccfr_ctx* c, void* stream) {
+    if (!c) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    return from_cuda(cudaMemsetAsync(c->dc.stats, 0, sizeof(DevStats), (cudaStream_t)stream));
+}
+
+}  // extern "C"

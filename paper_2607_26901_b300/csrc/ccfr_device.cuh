@@ -1,0 +1,168 @@
+// Device-side data structures and helpers of the CCFR library (sm_103a).
+//
+// Layout in HBM (one scene per context):
+//   x, v            float4 per vertex (xyz + inverse mass), caller-owned
+//   x_tilde, x_n    float4 per vertex: prediction and step-start positions
+//   x_s             float4 per vertex: XPBD iterate before projection
+//   planes          float4 (n, d) per slot, vertex-major: [v * K + j]
+//   keys            u64 per slot (optional)
+//   count           u32 per vertex (planes received; may exceed K)
+//   dmin_drop       u32 per vertex: order-preserving code of the smallest d
+//                   among planes beyond K (0xFFFFFFFF = none)
+//   grid            one counting-sorted spatial hash per table (triangles,
+//                   edges, isolated points, vertices); buckets of all tables
+//                   are concatenated so one scan serves the four; each item
+//                   record is two float4: (lo.xyz, id), (hi.xyz, packed cell)
+//   units           per query table, (bucket, offset) of every run of up to
+//                   32 queries that share a bucket: one warp work unit
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ccfr {
+
+typedef unsigned long long u64;
+
+// Grid tables: triangles, edges and isolated points (queries and items of
+// their own kind), and all vertices bucketed with the triangle cell size (the
+// items of the vertex-face queries).
+enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, N_KINDS = 4 };
+enum { MODE_PLANES = 0, MODE_PAIRS = 1 };
+enum { ERR_NONFINITE = 1u };
+
+// Near-parallel edge pairs (a*e - b^2 <= NEAR_PARALLEL * a * e in binary32)
+// are re-solved in FP64; below that ratio the binary32 closest points lose
+// more than ~1e-5 of the contact normal.
+constexpr float NEAR_PARALLEL = 1e-3f;
+// The FP64 closest-point solve treats a*e - b^2 <= PARALLEL_EPS * a * e as
+// parallel (textbook clamped rule: s = 0, then t, then s again).
+constexpr double PARALLEL_EPS = 1e-12;
+
+struct DevStats {
+    u64 cand[3];
+    u64 pairs[3];
+    u64 planes_kind[3];
+    u64 planes;
+    u64 overflow_verts;
+    u64 violated_verts;
+    u64 halts;
+    u64 ee_fp64;
+    u64 feas_fp64;
+    u64 feas_halts;
+    u64 iterations;
+    u64 steps;
+    u64 aux[8];
+    unsigned max_planes;
+    unsigned error_flags;
+};
+
+struct DevParams {
+    float r, two_r, xi, pad;
+    float eps, eps_dep, tau;
+    float dt, gx, gy, gz, alpha_tilde;
+    int max_passes;
+    int K;
+    float cell_size;
+};
+
+// Everything a kernel needs, passed by value.
+struct DevCtx {
+    DevParams p;
+    int n_verts, n_edges, n_tris, n_pts;
+    const int2* edges;          // canonical order
+    const int3* tris;
+    const int* pts;             // isolated vertices
+    // XPBD (colour-sorted copies)
+    const int2* edges_col;
+    const float* rest_col;
+    float* lambda;
+    // grid
+    int n_items;                // n_tris + n_edges + n_pts + n_verts
+    int item_base[4];           // first item of each table in the item space
+    int bucket_base[5];         // first bucket of each table (+ total)
+    int bucket_mask[4];         // M_table - 1
+    unsigned* ext_bits;         // [3] largest padded extent per kind (float bits)
+    u64* ext_sum;               // [3] sum of padded extents per kind, in nanometres
+    int n_kind[3];              // primitives per kind (triangles, edges, points)
+    float cell_factor;          // cell size = cell_factor x mean padded extent
+    int* big;                   // [n_tris + n_edges] primitives larger than a cell
+    float4* big_box;            // [2 (n_tris + n_edges)] their padded boxes (lo + id, hi)
+    int big_base[2];            // first slot of the triangles / edges
+    unsigned* big_count;        // [2]
+    int2* units;                // [n_tris + n_edges + n_pts + 3] warp work units
+    int unit_base[3];           // first unit slot of each query table
+    unsigned* unit_count;       // [3]
+    unsigned* bucket_count;     // [Mtot + 1] counts, then exclusive scan (start)
+    unsigned* bucket_fill;      // [Mtot]
+    unsigned* item_bucket;      // [n_items]
+    float4* rec;                // [2 * n_items]
+    // regions
+    float4* planes;
+    u64* keys;                  // may be null
+    unsigned* count;
+    unsigned* dmin_drop;
+    // step state
+    float4* x_tilde;
+    float4* x_n;
+    float4* x_s;
+    int* flags;                 // [0] not converged, [1] done (early exit)
+    int n_sm;                   // streaming multiprocessors (persistent grids)
+    DevStats* stats;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ unsigned f2ord(float f) {
+    unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ord2f(unsigned o) {
+    unsigned u = (o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o;
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
+    return ((u64)kind << 62) | ((u64)(unsigned)a << 31) | (u64)(unsigned)b;
+}
+
+// Cell size of a table: cell_factor x the mean padded extent of its
+// primitives (or the user's cell size if larger), never below the padded
+// vertex box, so vertex boxes always fit in one cell.  Primitives whose box
+// spans more than a cell are handled by the oversized pass.
+__device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
+    float mean = (c.n_kind[kind] > 0) ? (float)((double)c.ext_sum[kind] * 1e-9 / (double)c.n_kind[kind]) : 0.f;
+    float h = mean * c.cell_factor;
+    float hmin = 2.f * c.p.pad * 1.0625f;
+    if (h < hmin) h = hmin;
+    if (c.p.cell_size > h) h = c.p.cell_size;
+    if (!(h > 0.f)) h = 1.f;
+    return h;
+}
+
+// A primitive fits the single-cell scheme when its box is at most h / 1.0625
+// on every axis (the margin absorbs the rounding of the cell coordinates).
+__device__ __forceinline__ bool fits_cell(const float lo[3], const float hi[3], float h) {
+    float lim = h * (1.0f / 1.0625f);
+    return (hi[0] - lo[0]) <= lim && (hi[1] - lo[1]) <= lim && (hi[2] - lo[2]) <= lim;
+}
+
+__device__ __forceinline__ int cell_coord(float v, float inv_h) {
+    return (int)floorf(v * inv_h);
+}
+
+__device__ __forceinline__ unsigned cell_hash(int cx, int cy, int cz) {
+    return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u);
+}
+
+__device__ __forceinline__ unsigned cell_pack(int cx, int cy, int cz) {
+    return ((unsigned)cx & 1023u) | (((unsigned)cy & 1023u) << 10) | (((unsigned)cz & 1023u) << 20);
+}
+
+__device__ __forceinline__ void warp_add_u64(u64* dst, u64 v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+
+}  // namespace ccfr

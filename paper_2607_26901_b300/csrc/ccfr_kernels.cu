@@ -1,0 +1,1285 @@
+// CUDA kernels of the CCFR hot path (sm_103a).  CUDA cores only: nothing on
+// this path is a dense contraction, so no tensor-core path exists.
+//
+//   broad phase   k_extent, k_bucket_count, k_scan_*, k_bucket_scatter:
+//                 padded AABBs (pad = r + xi/2 + delta/2, Sec. 4.1), one
+//                 counting-sorted uniform-grid hash table per primitive kind
+//   narrow phase  k_emit_vf, k_emit_ee, k_emit_pp: each query primitive scans
+//                 its 3x3x3 cell neighbourhood, applies the exact binary32 box
+//                 predicate and the exclusions of Alg. 3, and (fused) computes
+//                 the closest points, the contact normal (Eq. 1) and the
+//                 mass-weighted half-spaces (Eq. 2-3), appending them to the
+//                 receiving vertices' fixed-capacity plane lists
+//   resolution    k_project: Alg. 2 calling Alg. 1 per vertex, one warp per
+//                 vertex streaming its plane list
+//   XPBD          k_predict, k_xpbd_color, k_update (Alg. 4)
+#include "ccfr_device.cuh"
+#include "ccfr_internal.h"
+
+namespace ccfr {
+
+// ------------------------------------------------------------ float3 math
+
+struct f3 { float x, y, z; };
+__device__ __forceinline__ f3 mk(float x, float y, float z) { f3 r; r.x = x; r.y = y; r.z = z; return r; }
+__device__ __forceinline__ f3 sub(f3 a, f3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ f3 add(f3 a, f3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ f3 mul(f3 a, float s) { return mk(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ f3 axpy(float s, f3 a, f3 b) { return mk(fmaf(s, a.x, b.x), fmaf(s, a.y, b.y), fmaf(s, a.z, b.z)); }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ float len(f3 a) { return sqrtf(dot(a, a)); }
+__device__ __forceinline__ f3 xyz(float4 a) { return mk(a.x, a.y, a.z); }
+
+// ---------------------------------------------------------------- boxes
+
+// Padded box of item i of the concatenated item space (triangles, edges,
+// isolated points, vertices): lo = fl32(min - pad), hi = fl32(max + pad).
+__device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restrict__ x, int i,
+                                        float lo[3], float hi[3], int& id) {
+    int kind;
+    float4 a, b, d;
+    if (i < c.item_base[KIND_EDGE]) {
+        kind = KIND_TRI;
+        id = i;
+        int3 t = c.tris[id];
+        a = x[t.x]; b = x[t.y]; d = x[t.z];
+    } else if (i < c.item_base[KIND_PT]) {
+        kind = KIND_EDGE;
+        id = i - c.item_base[KIND_EDGE];
+        int2 e = c.edges[id];
+        a = x[e.x]; b = x[e.y]; d = b;
+    } else if (i < c.item_base[KIND_VQ]) {
+        kind = KIND_PT;
+        id = c.pts[i - c.item_base[KIND_PT]];
+        a = x[id]; b = a; d = a;
+    } else {
+        kind = KIND_VQ;
+        id = i - c.item_base[KIND_VQ];
+        a = x[id]; b = a; d = a;
+    }
+    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), c.p.pad);
+    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), c.p.pad);
+    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), c.p.pad);
+    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), c.p.pad);
+    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), c.p.pad);
+    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), c.p.pad);
+    return kind;
+}
+
+// Cell size of a table: the vertex table shares the triangle cells so that a
+// triangle's 27-cell neighbourhood holds every vertex whose box overlaps it.
+__device__ __forceinline__ int cell_kind(int kind) { return kind == KIND_VQ ? KIND_TRI : kind; }
+
+__global__ void k_extent(DevCtx c, const float4* __restrict__ x) {
+    if (c.flags[1]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned e[3] = {0u, 0u, 0u};
+    u64 sum[3] = {0ull, 0ull, 0ull};
+    if (i < c.n_items) {
+        float lo[3], hi[3];
+        int id;
+        int kind = item_box(c, x, i, lo, hi, id);
+        float m = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+        // positive floats order as integers; the sum is fixed-point (nm) so it is order-independent
+        if (m == m && m < 1e6f && kind < 3) {
+            e[kind] = __float_as_uint(m);
+            sum[kind] = (u64)(m * 1e9f + 0.5f);
+        }
+    }
+    #pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        unsigned v = __reduce_max_sync(0xffffffffu, e[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicMax(&c.ext_bits[k], v);
+        warp_add_u64(&c.ext_sum[k], sum[k]);
+    }
+}
+
+__device__ __forceinline__ unsigned item_bucket_of(const DevCtx& c, int kind, const float lo[3], unsigned& packed) {
+    float h = cell_size_of(c, cell_kind(kind));
+    float inv = 1.0f / h;
+    int cx = cell_coord(lo[0], inv), cy = cell_coord(lo[1], inv), cz = cell_coord(lo[2], inv);
+    packed = cell_pack(cx, cy, cz);
+    return (unsigned)c.bucket_base[kind] + (cell_hash(cx, cy, cz) & (unsigned)c.bucket_mask[kind]);
+}
+
+// Triangles and edges whose box spans more than a cell go to the oversized
+// list instead of the grid (the count pass decides, the scatter pass skips them).
+__global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
+    if (c.flags[1]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n_items) return;
+    float lo[3], hi[3];
+    int id;
+    int kind = item_box(c, x, i, lo, hi, id);
+    if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
+        unsigned s = atomicAdd(&c.big_count[kind], 1u);
+        unsigned o = c.big_base[kind] + s;
+        c.big[o] = id;
+        c.big_box[2 * o] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
+        c.big_box[2 * o + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        return;
+    }
+    unsigned packed;
+    unsigned b = item_bucket_of(c, kind, lo, packed);
+    c.item_bucket[i] = b;
+    atomicAdd(&c.bucket_count[b], 1u);
+}
+
+__global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
+    if (c.flags[1]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n_items) return;
+    float lo[3], hi[3];
+    int id;
+    int kind = item_box(c, x, i, lo, hi, id);
+    if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
+    unsigned packed;
+    unsigned b = item_bucket_of(c, kind, lo, packed);
+    unsigned pos = c.bucket_count[b] + atomicAdd(&c.bucket_fill[b], 1u);
+    c.rec[2 * pos] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
+    c.rec[2 * pos + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(packed));
+}
+
+// ------------------------------------------------------------------ scan
+// Exclusive scan of n unsigned values in place: per-tile sums, a single-block
+// scan of the tile sums, then per-tile scans with the tile offset.
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned v, unsigned* smem, unsigned& total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned incl = v;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) smem[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned s = (lane < (int)(blockDim.x >> 5)) ? smem[lane] : 0u;
+        unsigned si = s;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned t = __shfl_up_sync(0xffffffffu, si, o);
+            if (lane >= o) si += t;
+        }
+        smem[lane] = si - s;
+        if (lane == 31) smem[32] = si;
+    }
+    __syncthreads();
+    unsigned r = smem[wid] + incl - v;
+    total = smem[32];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(DevCtx c, unsigned* data, int n, unsigned* tile_sums) {
+    if (c.flags[1]) return;
+    __shared__ unsigned smem[33];
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    unsigned s = 0;
+    #pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) s += (base + k < n) ? data[base + k] : 0u;
+    unsigned total;
+    block_exclusive_scan(s, smem, total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(DevCtx c, unsigned* tile_sums, int n_tiles) {
+    if (c.flags[1]) return;
+    __shared__ unsigned smem[33];
+    int base = threadIdx.x * SCAN_ITEMS;
+    unsigned vals[SCAN_ITEMS], s = 0;
+    #pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) { vals[k] = (base + k < n_tiles) ? tile_sums[base + k] : 0u; s += vals[k]; }
+    unsigned total;
+    unsigned off = block_exclusive_scan(s, smem, total);
+    #pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n_tiles) tile_sums[base + k] = off;
+        off += vals[k];
+    }
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(DevCtx c, unsigned* data, int n, const unsigned* tile_sums) {
+    if (c.flags[1]) return;
+    __shared__ unsigned smem[33];
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    unsigned vals[SCAN_ITEMS], s = 0;
+    #pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) { vals[k] = (base + k < n) ? data[base + k] : 0u; s += vals[k]; }
+    unsigned total;
+    unsigned off = block_exclusive_scan(s, smem, total) + tile_sums[blockIdx.x];
+    #pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) data[base + k] = off;
+        off += vals[k];
+    }
+}
+
+// ------------------------------------------------------- plane emission
+
+__device__ __forceinline__ void emit_plane(const DevCtx& c, int v, f3 n, float d, u64 key) {
+    unsigned slot = atomicAdd(&c.count[v], 1u);
+    if (slot < (unsigned)c.p.K) {
+        size_t o = (size_t)v * c.p.K + slot;
+        c.planes[o] = make_float4(n.x, n.y, n.z, d);
+        if (c.keys) c.keys[o] = key;
+    } else {
+        atomicMin(&c.dmin_drop[v], f2ord(d));
+    }
+}
+
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// Closest point to the origin on triangle (a, b, c) by Voronoi-region
+// classification: the vertex and edge regions are decided from the signs of
+// first-order dot products (never by comparing squared distances, which
+// differ only at second order near a vertex and would misplace the contact
+// normal).  Returns true when the point is the foot of the perpendicular
+// inside the face; wa, wb, wc are its barycentric weights.
+__device__ bool closest_on_triangle(f3 a, f3 b, f3 cc, f3& q, float& wa, float& wb, float& wc) {
+    f3 ab = sub(b, a), ac = sub(cc, a);
+    f3 pa = mk(-a.x, -a.y, -a.z);                 // origin - a
+    float d1 = dot(ab, pa), d2 = dot(ac, pa);
+    if (d1 <= 0.f && d2 <= 0.f) { q = a; wa = 1.f; wb = 0.f; wc = 0.f; return false; }
+    f3 pb = mk(-b.x, -b.y, -b.z);
+    float d3 = dot(ab, pb), d4 = dot(ac, pb);
+    if (d3 >= 0.f && d4 <= d3) { q = b; wa = 0.f; wb = 1.f; wc = 0.f; return false; }
+    float vc = d1 * d4 - d3 * d2;
+    if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+        float t = d1 / (d1 - d3);
+        q = axpy(t, ab, a); wa = 1.f - t; wb = t; wc = 0.f;
+        return false;
+    }
+    f3 pc = mk(-cc.x, -cc.y, -cc.z);
+    float d5 = dot(ab, pc), d6 = dot(ac, pc);
+    if (d6 >= 0.f && d5 <= d6) { q = cc; wa = 0.f; wb = 0.f; wc = 1.f; return false; }
+    float vb = d5 * d2 - d1 * d6;
+    if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+        float t = d2 / (d2 - d6);
+        q = axpy(t, ac, a); wa = 1.f - t; wb = 0.f; wc = t;
+        return false;
+    }
+    float va = d3 * d6 - d5 * d4;
+    float e43 = d4 - d3, e56 = d5 - d6;
+    if (va <= 0.f && e43 >= 0.f && e56 >= 0.f) {
+        float t = e43 / (e43 + e56);
+        q = axpy(t, sub(cc, b), b); wa = 0.f; wb = 1.f - t; wc = t;
+        return false;
+    }
+    float inv = 1.f / (va + vb + vc);
+    float v = vb * inv, w = vc * inv;
+    q = add(a, add(mul(ab, v), mul(ac, w)));
+    wa = 1.f - v - w; wb = v; wc = w;
+    return true;
+}
+
+// Vertex-face pair (Alg. 3): p against triangle t = (ta, tb, tc).  Local
+// coordinates centred at p.  Returns 1 if the pair is accepted (phi < 2r).
+__device__ int narrow_vf(const DevCtx& c, int p, float4 P, int t, int3 T, float4 A, float4 B, float4 C) {
+    f3 o = xyz(P);
+    f3 a = sub(xyz(A), o), b = sub(xyz(B), o), cc = sub(xyz(C), o);
+    f3 q;
+    float wa, wb, wc;
+    bool inside = closest_on_triangle(a, b, cc, q, wa, wb, wc);
+    f3 diff = mk(-q.x, -q.y, -q.z);
+    if (inside) {
+        // foot of the perpendicular: the separation is along the face normal,
+        // which the cross product gives to binary32 accuracy
+        f3 N = cross(sub(b, a), sub(cc, a));
+        float nl = len(N);
+        if (nl > 0.f) {
+            f3 nh = mk(N.x / nl, N.y / nl, N.z / nl);
+            float h = -dot(a, nh);
+            diff = mul(nh, h);
+        }
+    }
+    float dist = len(diff);
+    if (dist == 0.f) return 0;
+    float phi = dist - c.p.xi;
+    if (!(phi < c.p.two_r)) return 0;
+    float wf = wa * A.w + wb * B.w + wc * C.w;
+    float W = P.w + wf;
+    if (W == 0.f) return 0;
+    f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
+    f3 mn = mk(-n.x, -n.y, -n.z);
+    u64 key = pair_key(0, p, t);
+    int k = 0;
+    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, key); ++k; }
+    float df = (wf / W) * phi;
+    if (A.w > 0.f) { emit_plane(c, T.x, mn, df, key); ++k; }
+    if (B.w > 0.f) { emit_plane(c, T.y, mn, df, key); ++k; }
+    if (C.w > 0.f) { emit_plane(c, T.z, mn, df, key); ++k; }
+    return k;
+}
+
+// Closest points of segments p1 + s d1 and p2 + t d2 in FP64 with the
+// textbook clamped rule (parallel: s = 0 first).
+__device__ void closest_segments_fp64(float4 P1, float4 Q1, float4 P2, float4 Q2, double& s, double& t) {
+    double d1x = (double)Q1.x - P1.x, d1y = (double)Q1.y - P1.y, d1z = (double)Q1.z - P1.z;
+    double d2x = (double)Q2.x - P2.x, d2y = (double)Q2.y - P2.y, d2z = (double)Q2.z - P2.z;
+    double rx = (double)P1.x - P2.x, ry = (double)P1.y - P2.y, rz = (double)P1.z - P2.z;
+    double a = d1x * d1x + d1y * d1y + d1z * d1z;
+    double e = d2x * d2x + d2y * d2y + d2z * d2z;
+    double f = d2x * rx + d2y * ry + d2z * rz;
+    double cc = d1x * rx + d1y * ry + d1z * rz;
+    double b = d1x * d2x + d1y * d2y + d1z * d2z;
+    if (a <= 0.0 && e <= 0.0) { s = t = 0.0; return; }
+    if (a <= 0.0) { s = 0.0; t = fmin(fmax(f / e, 0.0), 1.0); return; }
+    if (e <= 0.0) { t = 0.0; s = fmin(fmax(-cc / a, 0.0), 1.0); return; }
+    double den = a * e - b * b;
+    s = (den > PARALLEL_EPS * a * e) ? fmin(fmax((b * f - cc * e) / den, 0.0), 1.0) : 0.0;
+    t = (b * s + f) / e;
+    if (t < 0.0) { t = 0.0; s = fmin(fmax(-cc / a, 0.0), 1.0); }
+    else if (t > 1.0) { t = 1.0; s = fmin(fmax((b - cc) / a, 0.0), 1.0); }
+}
+
+// Edge-edge pair (Alg. 3): e = (e0, e1) against f = (f0, f1), local
+// coordinates centred at e0.  Returns 1 if accepted; *fp64 is set when the
+// near-parallel FP64 solve was used.
+__device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A0, float4 A1, float4 B0,
+                         float4 B1, int& fp64) {
+    f3 o = xyz(A0);
+    f3 d1 = sub(xyz(A1), o), p2 = sub(xyz(B0), o), d2 = sub(xyz(B1), xyz(B0));
+    // r = p1 - p2 = -p2
+    float a = dot(d1, d1), ee = dot(d2, d2);
+    float f_ = -dot(d2, p2), cc = -dot(d1, p2), b = dot(d1, d2);
+    // |d1 x d2|^2 = a e - b^2 (Lagrange), and the unclamped line parameter
+    // s* = ((p2 - p1) x d2) . N / |N|^2 loses a factor 1/sin(theta) less than
+    // the dot-product form
+    f3 N = cross(d1, d2);
+    float den = dot(N, N);
+    float s, t;
+    f3 diff;
+    if (den > NEAR_PARALLEL * a * ee) {
+        s = fminf(fmaxf(dot(cross(p2, d2), N) / den, 0.f), 1.f);
+        t = (b * s + f_) / ee;
+        if (t < 0.f) { t = 0.f; s = fminf(fmaxf(-cc / a, 0.f), 1.f); }
+        else if (t > 1.f) { t = 1.f; s = fminf(fmaxf((b - cc) / a, 0.f), 1.f); }
+        f3 pa = mul(d1, s);
+        f3 pb = axpy(t, d2, p2);
+        diff = sub(pa, pb);
+        if (s > 0.f && s < 1.f && t > 0.f && t < 1.f) {
+            // interior closest points: the separation is along d1 x d2
+            float nl = sqrtf(den);
+            if (nl > 0.f) {
+                f3 nh = mk(N.x / nl, N.y / nl, N.z / nl);
+                diff = mul(nh, -dot(p2, nh));
+            }
+        }
+    } else {
+        double sd, td;
+        closest_segments_fp64(A0, A1, B0, B1, sd, td);
+        fp64 = 1;
+        double ax = (double)A0.x + sd * ((double)A1.x - A0.x), ay = (double)A0.y + sd * ((double)A1.y - A0.y),
+               az = (double)A0.z + sd * ((double)A1.z - A0.z);
+        double bx = (double)B0.x + td * ((double)B1.x - B0.x), by = (double)B0.y + td * ((double)B1.y - B0.y),
+               bz = (double)B0.z + td * ((double)B1.z - B0.z);
+        diff = mk((float)(ax - bx), (float)(ay - by), (float)(az - bz));
+        s = (float)sd;
+        t = (float)td;
+    }
+    float dist = len(diff);
+    if (dist == 0.f) return 0;
+    float phi = dist - c.p.xi;
+    if (!(phi < c.p.two_r)) return 0;
+    float wa = (1.f - s) * A0.w + s * A1.w;
+    float wb = (1.f - t) * B0.w + t * B1.w;
+    float W = wa + wb;
+    if (W == 0.f) return 0;
+    f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
+    f3 mn = mk(-n.x, -n.y, -n.z);
+    u64 key = pair_key(1, e, f);
+    float da = (wa / W) * phi, db = (wb / W) * phi;
+    int k = 0;
+    if (A0.w > 0.f) { emit_plane(c, E.x, n, da, key); ++k; }
+    if (A1.w > 0.f) { emit_plane(c, E.y, n, da, key); ++k; }
+    if (B0.w > 0.f) { emit_plane(c, F.x, mn, db, key); ++k; }
+    if (B1.w > 0.f) { emit_plane(c, F.y, mn, db, key); ++k; }
+    return k;
+}
+
+// Point-point pair (isolated particles).
+__device__ int narrow_pp(const DevCtx& c, int p, int q, float4 P, float4 Q) {
+    f3 diff = sub(xyz(P), xyz(Q));
+    float dist = len(diff);
+    if (dist == 0.f) return 0;
+    float phi = dist - c.p.xi;
+    if (!(phi < c.p.two_r)) return 0;
+    float W = P.w + Q.w;
+    if (W == 0.f) return 0;
+    f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
+    u64 key = pair_key(2, p, q);
+    int k = 0;
+    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, key); ++k; }
+    if (Q.w > 0.f) { emit_plane(c, q, mk(-n.x, -n.y, -n.z), (Q.w / W) * phi, key); ++k; }
+    return k;
+}
+
+// ------------------------------------------------------ neighbourhood scan
+//
+// Work is organised by grid cell.  A work unit is a run of up to 32 query
+// primitives that share a bucket of the query table; the lanes of a warp hold
+// one query each, and the queries of one cell share one 3x3x3 neighbourhood
+// in the item table.  The warp walks that neighbourhood item by item (every
+// lane loads the same record: one broadcast transaction), tests its own query
+// against the item with the exact binary32 box predicate, and appends the
+// hits to a per-warp queue in shared memory.  Whenever 32 pairs are queued,
+// every lane runs the narrow phase of one pair, so the closest-point work
+// always runs on full warps.
+
+struct PairOut {
+    int* out[3];
+    long cap[3];
+    unsigned long long* count;   // [3]
+};
+
+__device__ __forceinline__ void write_pair(const PairOut& po, int kind, int a, int b) {
+    unsigned long long s = atomicAdd(&po.count[kind], 1ull);
+    if ((long)s < po.cap[kind]) {
+        po.out[kind][2 * s] = a;
+        po.out[kind][2 * s + 1] = b;
+    }
+}
+
+constexpr int EMIT_WARPS = 8;     // warps per block
+constexpr int QCAP = 64;          // pair queue per warp (two warps' worth of hits)
+constexpr unsigned FULL = 0xffffffffu;
+
+// Work units: one per run of up to 32 items of a non-empty bucket of the
+// triangle, edge and point tables.
+__global__ void k_make_units(DevCtx c) {
+    if (c.flags[1]) return;
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) {
+        c.stats->aux[3] += c.big_count[KIND_TRI];
+        c.stats->aux[4] += c.big_count[KIND_EDGE];
+    }
+    if (b >= c.bucket_base[KIND_VQ]) return;
+    int kind = (b < c.bucket_base[KIND_EDGE]) ? KIND_TRI : ((b < c.bucket_base[KIND_PT]) ? KIND_EDGE : KIND_PT);
+    unsigned n = c.bucket_count[b + 1] - c.bucket_count[b];
+    if (n == 0) return;
+    unsigned nu = (n + 31u) / 32u;
+    unsigned u0 = atomicAdd(&c.unit_count[kind], nu);
+    for (unsigned k = 0; k < nu; ++k) c.units[c.unit_base[kind] + u0 + k] = make_int2(b, (int)(32u * k));
+}
+
+struct EmitCounters { u64 cand, acc, planes, fp64; };
+
+// Narrow phase of one queued pair (a = query id, b = item id).
+template <int QK, int MODE>
+__device__ __forceinline__ void process_pair(const DevCtx& c, const float4* __restrict__ x, const PairOut& po,
+                                             int2 pr, EmitCounters& k) {
+    if (QK == KIND_TRI) {                          // (triangle, vertex)
+        int t = pr.x, v = pr.y;
+        int3 T = c.tris[t];
+        float4 P = x[v], A = x[T.x], B = x[T.y], C = x[T.z];
+        if (!(P.w > 0.f || A.w > 0.f || B.w > 0.f || C.w > 0.f)) return;
+        ++k.cand;
+        if (MODE == MODE_PAIRS) { write_pair(po, 0, v, t); return; }
+        int np = narrow_vf(c, v, P, t, T, A, B, C);
+        k.acc += (np > 0);
+        k.planes += np;
+    } else if (QK == KIND_EDGE) {                  // (edge, edge), e < f
+        int e = pr.x, f = pr.y;
+        int2 E = c.edges[e], F = c.edges[f];
+        if (F.x == E.x || F.x == E.y || F.y == E.x || F.y == E.y) return;
+        float4 A0 = x[E.x], A1 = x[E.y], B0 = x[F.x], B1 = x[F.y];
+        if (!(A0.w > 0.f || A1.w > 0.f || B0.w > 0.f || B1.w > 0.f)) return;
+        ++k.cand;
+        if (MODE == MODE_PAIRS) { write_pair(po, 1, e, f); return; }
+        int fp64 = 0;
+        int np = narrow_ee(c, e, E, f, F, A0, A1, B0, B1, fp64);
+        k.acc += (np > 0);
+        k.planes += np;
+        k.fp64 += fp64;
+    } else {                                       // (point, point), p < q
+        int p = pr.x, q = pr.y;
+        float4 P = x[p], Q = x[q];
+        if (!(P.w > 0.f || Q.w > 0.f)) return;
+        ++k.cand;
+        if (MODE == MODE_PAIRS) { write_pair(po, 2, p, q); return; }
+        int np = narrow_pp(c, p, q, P, Q);
+        k.acc += (np > 0);
+        k.planes += np;
+    }
+}
+
+// QK: query table (KIND_TRI: triangles against the vertex table, KIND_EDGE,
+// KIND_PT: against their own table).  Persistent warps stride over the units.
+template <int QK, int MODE>
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po) {
+    if (c.flags[1]) return;
+    __shared__ int2 queue[EMIT_WARPS][QCAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int2* q = queue[wib];
+    int qn = 0;
+    EmitCounters k{0, 0, 0, 0};
+    const int IK = (QK == KIND_TRI) ? KIND_VQ : QK;
+    const float inv = 1.0f / cell_size_of(c, QK);
+    const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
+    const unsigned nunits = c.unit_count[QK];
+    const unsigned stride = gridDim.x * EMIT_WARPS;
+    for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nunits; u += stride) {
+        int2 U = c.units[c.unit_base[QK] + u];
+        unsigned s0 = c.bucket_count[U.x] + (unsigned)U.y, s1 = c.bucket_count[U.x + 1];
+        unsigned n = min(32u, s1 - s0);
+        bool act = (unsigned)lane < n;
+        float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+        if (act) { r0 = c.rec[2 * (s0 + lane)]; r1 = c.rec[2 * (s0 + lane) + 1]; }
+        const int qid = __float_as_int(r0.w);
+        int3 qt = make_int3(-1, -1, -1);
+        if (QK == KIND_TRI && act) qt = c.tris[qid];
+        const int mx = cell_coord(r0.x, inv), my = cell_coord(r0.y, inv), mz = cell_coord(r0.z, inv);
+        unsigned pending = __ballot_sync(FULL, act);
+        while (pending) {
+            // the queries of one cell share its neighbourhood
+            const int leader = __ffs(pending) - 1;
+            const int cx = __shfl_sync(FULL, mx, leader), cy = __shfl_sync(FULL, my, leader),
+                      cz = __shfl_sync(FULL, mz, leader);
+            const bool in = ((pending >> lane) & 1u) && mx == cx && my == cy && mz == cz;
+            pending &= ~__ballot_sync(FULL, in);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const unsigned b = ibase + (cell_hash(cx + dx, cy + dy, cz + dz) & imask);
+                        const unsigned pk = cell_pack(cx + dx, cy + dy, cz + dz);
+                        const unsigned t1 = c.bucket_count[b + 1];
+                        for (unsigned s = c.bucket_count[b]; s < t1; ++s) {
+                            const float4 i1 = c.rec[2 * s + 1];
+                            if (__float_as_uint(i1.w) != pk) continue;
+                            const float4 i0 = c.rec[2 * s];
+                            const int iid = __float_as_int(i0.w);
+                            bool hit = in && r0.x <= i1.x && i0.x <= r1.x && r0.y <= i1.y && i0.y <= r1.y &&
+                                       r0.z <= i1.z && i0.z <= r1.z;
+                            if (QK == KIND_TRI) hit = hit && iid != qt.x && iid != qt.y && iid != qt.z;
+                            else hit = hit && iid > qid;
+                            const unsigned hb = __ballot_sync(FULL, hit);
+                            if (!hb) continue;
+                            if (hit) q[qn + __popc(hb & ((1u << lane) - 1u))] = make_int2(qid, iid);
+                            qn += __popc(hb);
+                            if (qn >= 32) {
+                                __syncwarp();
+                                process_pair<QK, MODE>(c, x, po, q[lane], k);
+                                int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
+                                __syncwarp();
+                                if (lane < qn - 32) q[lane] = rest;
+                                qn -= 32;
+                                __syncwarp();
+                            }
+                        }
+                    }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) process_pair<QK, MODE>(c, x, po, q[lane], k);
+    warp_add_u64(&c.stats->cand[QK], k.cand);
+    warp_add_u64(&c.stats->pairs[QK], k.acc);
+    warp_add_u64(&c.stats->planes_kind[QK], k.planes);
+    if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+}
+
+// Oversized primitives (box larger than a cell): one warp per primitive scans
+// every cell its box can reach, lanes striding over the items of each cell;
+// edges also test the other oversized edges with a larger id.  Together with
+// the per-cell pass over the fitting primitives this visits every candidate
+// pair exactly once.
+__device__ __forceinline__ void prim_box(const DevCtx& c, const float4* __restrict__ x, int kind, int id,
+                                         float lo[3], float hi[3]) {
+    float4 a, b, d;
+    if (kind == KIND_TRI) {
+        int3 t = c.tris[id];
+        a = x[t.x]; b = x[t.y]; d = x[t.z];
+    } else {
+        int2 e = c.edges[id];
+        a = x[e.x]; b = x[e.y]; d = b;
+    }
+    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), c.p.pad);
+    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), c.p.pad);
+    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), c.p.pad);
+    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), c.p.pad);
+    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), c.p.pad);
+    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), c.p.pad);
+}
+
+template <int QK, int MODE>
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po) {
+    if (c.flags[1]) return;
+    __shared__ int2 queue[EMIT_WARPS][QCAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int2* q = queue[wib];
+    int qn = 0;
+    EmitCounters k{0, 0, 0, 0};
+    const int IK = (QK == KIND_TRI) ? KIND_VQ : KIND_EDGE;
+    const float inv = 1.0f / cell_size_of(c, QK);
+    const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
+    const unsigned nbig = c.big_count[QK];
+    const unsigned stride = gridDim.x * EMIT_WARPS;
+    // append a hit to the warp queue; process 32 queued pairs at a time
+    auto push = [&](bool hit, int2 pr) {
+        const unsigned hb = __ballot_sync(FULL, hit);
+        if (!hb) return;
+        if (hit) q[qn + __popc(hb & ((1u << lane) - 1u))] = pr;
+        qn += __popc(hb);
+        if (qn >= 32) {
+            __syncwarp();
+            process_pair<QK, MODE>(c, x, po, q[lane], k);
+            int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
+            __syncwarp();
+            if (lane < qn - 32) q[lane] = rest;
+            qn -= 32;
+            __syncwarp();
+        }
+    };
+    for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nbig; u += stride) {
+        const int o = c.big[c.big_base[QK] + u];
+        float lo[3], hi[3];
+        prim_box(c, x, QK, o, lo, hi);
+        int3 ot = make_int3(-1, -1, -1);
+        if (QK == KIND_TRI) ot = c.tris[o];
+        bool fin = isfinite(lo[0]) && isfinite(lo[1]) && isfinite(lo[2]) && isfinite(hi[0]) && isfinite(hi[1]) &&
+                   isfinite(hi[2]);
+        if (!fin) {
+            if (lane == 0) atomicOr(&c.stats->error_flags, ERR_NONFINITE);
+            continue;
+        }
+        const float fx0 = floorf(lo[0] * inv) - 1.f, fx1 = floorf(hi[0] * inv);
+        const float fy0 = floorf(lo[1] * inv) - 1.f, fy1 = floorf(hi[1] * inv);
+        const float fz0 = floorf(lo[2] * inv) - 1.f, fz1 = floorf(hi[2] * inv);
+        const double ncell = (double)(fx1 - fx0 + 1.f) * (double)(fy1 - fy0 + 1.f) * (double)(fz1 - fz0 + 1.f);
+        const unsigned t_begin = c.bucket_count[ibase], t_end = c.bucket_count[c.bucket_base[IK + 1]];
+        auto test = [&](float4 i0, float4 i1) -> int2 {
+            const int iid = __float_as_int(i0.w);
+            bool hit = lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
+            if (QK == KIND_TRI) {
+                if (!(hit && iid != ot.x && iid != ot.y && iid != ot.z)) return make_int2(-1, -1);
+                return make_int2(o, iid);
+            }
+            if (!hit) return make_int2(-1, -1);
+            return make_int2(min(o, iid), max(o, iid));
+        };
+        const float cmax = 1e9f;
+        const bool huge = fabsf(fx0) > cmax || fabsf(fx1) > cmax || fabsf(fy0) > cmax || fabsf(fy1) > cmax ||
+                          fabsf(fz0) > cmax || fabsf(fz1) > cmax;
+        if (huge || ncell * 8.0 > (double)(t_end - t_begin)) {
+            // cheaper to test the whole table
+            for (unsigned s0 = t_begin; s0 < t_end; s0 += 32) {
+                const unsigned s = s0 + lane;
+                int2 pr = make_int2(-1, -1);
+                if (s < t_end) pr = test(c.rec[2 * s], c.rec[2 * s + 1]);
+                push(pr.x >= 0, pr);
+            }
+        } else {
+            const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1, z0 = (int)fz0, z1 = (int)fz1;
+            for (int cz = z0; cz <= z1; ++cz)
+                for (int cy = y0; cy <= y1; ++cy)
+                    for (int cx = x0; cx <= x1; ++cx) {
+                        const unsigned b = ibase + (cell_hash(cx, cy, cz) & imask);
+                        const unsigned pk = cell_pack(cx, cy, cz);
+                        const unsigned t1 = c.bucket_count[b + 1];
+                        for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
+                            const unsigned s = s0 + lane;
+                            int2 pr = make_int2(-1, -1);
+                            if (s < t1) {
+                                const float4 i1 = c.rec[2 * s + 1];
+                                if (__float_as_uint(i1.w) == pk) pr = test(c.rec[2 * s], i1);
+                            }
+                            push(pr.x >= 0, pr);
+                        }
+                    }
+        }
+        if (QK == KIND_EDGE) {
+            // oversized-oversized pairs, found from the smaller id
+            for (unsigned w0 = 0; w0 < nbig; w0 += 32) {
+                const unsigned w = w0 + lane;
+                int2 pr = make_int2(-1, -1);
+                if (w < nbig) {
+                    const float4 b0 = c.big_box[2 * (c.big_base[QK] + w)];
+                    const int o2 = __float_as_int(b0.w);
+                    if (o2 > o) {
+                        const float4 b1 = c.big_box[2 * (c.big_base[QK] + w) + 1];
+                        if (lo[0] <= b1.x && b0.x <= hi[0] && lo[1] <= b1.y && b0.y <= hi[1] && lo[2] <= b1.z &&
+                            b0.z <= hi[2])
+                            pr = make_int2(o, o2);
+                    }
+                }
+                push(pr.x >= 0, pr);
+            }
+        }
+    }
+    __syncwarp();
+    if (lane < qn) process_pair<QK, MODE>(c, x, po, q[lane], k);
+    warp_add_u64(&c.stats->cand[QK], k.cand);
+    warp_add_u64(&c.stats->pairs[QK], k.acc);
+    warp_add_u64(&c.stats->planes_kind[QK], k.planes);
+    if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+}
+
+// -------------------------------------------------------------- Alg. 1/2
+
+// Plesnik's ERO-line state (Alg. 1), kept in FP64 and in coordinates
+// centred at the pass start x^(0), so that the auxiliary point w starts at the
+// normal itself.  Alg. 1 divides by the dependence measures beta; with nearly
+// dependent planes (beta ~ 1e-3) binary32 would lose the result's accuracy, and
+// the step runs at most three times per pass, so it is done in FP64.
+struct d3 { double x, y, z; };
+__device__ __forceinline__ d3 dk(double x, double y, double z) { d3 r; r.x = x; r.y = y; r.z = z; return r; }
+__device__ __forceinline__ d3 dsub(d3 a, d3 b) { return dk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ d3 dadd(d3 a, d3 b) { return dk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ d3 dmul(d3 a, double s) { return dk(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ d3 daxpy(double s, d3 a, d3 b) { return dk(fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z)); }
+__device__ __forceinline__ double ddot(d3 a, d3 b) { return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ double dlen(d3 a) { return sqrt(ddot(a, a)); }
+__device__ __forceinline__ d3 d_of(f3 a) { return dk(a.x, a.y, a.z); }
+__device__ __forceinline__ f3 f_of(d3 a) { return mk((float)a.x, (float)a.y, (float)a.z); }
+
+struct Ero {
+    int m;
+    d3 V[3], A[3];
+    double B[3];
+};
+
+__device__ __forceinline__ void ero_push(Ero& S, d3 v, d3 n, double b) {
+    if (S.m < 3) { S.V[S.m] = v; S.A[S.m] = n; S.B[S.m] = b; S.m++; }
+}
+
+// One Alg. 1 step: project zt onto the intersection of the stored hyperplanes
+// and n . z = b.
+__device__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double eps) {
+    if (S.m == 0) {
+        double beta0 = ddot(n, n);
+        if (fabs(beta0) < eps) return;
+        zt = daxpy((b - ddot(n, zt)) / beta0, n, zt);
+        ero_push(S, n, n, b);
+        return;
+    }
+    const int m = S.m;
+    const d3 n0 = S.A[0];
+    const double b0 = S.B[0];
+    const d3 vm = S.V[m - 1];
+    double beta_u = ddot(dsub(n, n0), vm);
+    if (fabs(beta_u) < eps) return;
+    d3 u = daxpy((b - ddot(n, zt)) / beta_u, vm, zt);
+    d3 w = n;
+    #pragma unroll
+    for (int j = 1; j <= 2; ++j) {
+        if (j > m) break;
+        d3 nj = (j < m) ? S.A[j] : n;
+        double bj = (j < m) ? S.B[j] : b;
+        d3 dnj = dsub(nj, n0);
+        double beta_w = ddot(dnj, S.V[j - 1]);
+        if (fabs(beta_w) > eps) w = daxpy((bj - b0 - ddot(dnj, w)) / beta_w, S.V[j - 1], w);
+    }
+    d3 vn = dsub(w, u);
+    if (dlen(vn) > eps) {
+        double beta_new = ddot(n0, vn);
+        zt = (fabs(beta_new) < eps) ? u : daxpy((b0 - ddot(n0, u)) / beta_new, vn, u);
+        ero_push(S, vn, n, b);
+    }
+}
+
+// Sort tuple of a plane: rho at the pass input (Alg. 2 sorts once), then the
+// plane's own bits and slot, so that equal keys break ties deterministically.
+struct Tup { u64 a, b, c; };
+__device__ __forceinline__ bool tless(const Tup& x, const Tup& y) {
+    return x.a < y.a || (x.a == y.a && (x.b < y.b || (x.b == y.b && x.c < y.c)));
+}
+__device__ __forceinline__ Tup make_tup(float key, float4 P, int j) {
+    Tup t;
+    t.a = ((u64)f2ord(key) << 32) | f2ord(P.w);
+    t.b = ((u64)f2ord(P.x) << 32) | f2ord(P.y);
+    t.c = ((u64)f2ord(P.z) << 32) | (unsigned)j;
+    return t;
+}
+
+__device__ __forceinline__ f3 clamp_len(f3 y, float lim) {
+    if (!(lim > 0.f)) return mk(0.f, 0.f, 0.f);
+    float L = len(y);
+    return (L > lim) ? mul(y, lim / L) : y;
+}
+
+struct BlockCounters { unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry; unsigned long long planes; };
+
+// Per-warp shared-memory list of the planes that can become violated during
+// one pass of Alg. 2 (see k_project).
+constexpr int PCAP = 480;
+constexpr int PROJ_WARPS = 4;
+struct PlaneBuf {
+    float4 pl[PCAP];
+    float key[PCAP];
+    int idx[PCAP];
+};
+
+__device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
+
+__device__ __forceinline__ Tup warp_min_tup(Tup best) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Tup t;
+        t.a = __shfl_xor_sync(FULL, best.a, o);
+        t.b = __shfl_xor_sync(FULL, best.b, o);
+        t.c = __shfl_xor_sync(FULL, best.c, o);
+        if (tless(t, best)) best = t;
+    }
+    return best;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// One pass of Alg. 2 from the pass input ypass: visit the planes in ascending
+// order of the sort key (rho at the first input y0, then the plane's bits and
+// slot), call Alg. 1 on each plane violated at the current iterate and
+// retract by eps towards the build position.  `get(e, P, key, j)` yields
+// source entry e of n.  Returns the number of violated planes; zt receives the
+// iterate in coordinates centred at ypass and Dmax the largest |zt| reached.
+template <typename Get>
+__device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get get, f3 ypass, f3& y_out, float& Dmax) {
+    d3 zt = dk(0.0, 0.0, 0.0);
+    const d3 yp = d_of(ypass);
+    Dmax = 0.f;
+    Ero S;
+    S.m = 0;
+    int nv = 0;
+    Tup cur = {0ull, 0ull, 0ull};
+    for (int it = 0; it <= n; ++it) {
+        f3 yt = f_of(dadd(yp, zt));
+        Tup best = {~0ull, ~0ull, ~0ull};
+        for (int e = lane; e < n; e += 32) {
+            float4 P;
+            float key;
+            int j;
+            get(e, P, key, j);
+            if (rho_at(yt, P) < 0.f) {
+                Tup t = make_tup(key, P, j);
+                if (tless(cur, t) && tless(t, best)) best = t;
+            }
+        }
+        best = warp_min_tup(best);
+        if (best.a == ~0ull) break;
+        cur = best;
+        ++nv;
+        d3 nrm = dk(ord2f((unsigned)(best.b >> 32)), ord2f((unsigned)best.b), ord2f((unsigned)(best.c >> 32)));
+        double d = ord2f((unsigned)best.a);
+        // the plane n . y = -d in coordinates centred at the pass input
+        double bz = -d - ddot(nrm, yp);
+        if (S.m < 3) ortho_step(zt, nrm, bz, S, (double)c.p.eps_dep);
+        // retraction by eps towards the build position (Sec. 3.2); a binary32
+        // scaling is accurate to ~u |y| here (no cancellation), so only the
+        // Alg. 1 step above runs in FP64
+        f3 yn = f_of(dadd(yp, zt));
+        float L = len(yn);
+        yn = (L > c.p.eps) ? mul(yn, (L - c.p.eps) / L) : mk(0.f, 0.f, 0.f);
+        zt = dsub(d_of(yn), yp);
+        Dmax = fmaxf(Dmax, len(sub(yn, ypass)));
+    }
+    y_out = f_of(dadd(yp, zt));
+    return nv;
+}
+
+// One warp per vertex.  STEP = true: x_b is the collision-free iterate x_c
+// (read and overwritten), candidates come from x_in (the XPBD iterate), the
+// step is clamped to r, and the convergence flag is raised.
+//
+// A pass of Alg. 2 only ever acts on planes that are violated at its current
+// iterate.  With b the pass input and D the largest distance the iterate
+// moves from b during the pass, rho_k(y) >= rho_k(b) - D for every plane, so
+// planes with rho_k(b) > T >= D + margin are never touched.  The pass is run
+// on the planes with rho_k(b) <= T, gathered into shared memory, and is
+// repeated with a larger T if D turns out to exceed T - margin; the result is
+// the same as a pass over the full sorted list.  The final pass can only
+// confirm convergence (any violation there ends in the halt), so it is a
+// single scan.
+template <bool STEP>
+__global__ void __launch_bounds__(PROJ_WARPS * 32) k_project(DevCtx c, const float4* x_b, const float4* x_in,
+                                                              float4* x_out, unsigned char* halt_out) {
+    if (STEP && c.flags[1]) return;
+    __shared__ BlockCounters bc;
+    __shared__ PlaneBuf pbuf[PROJ_WARPS];
+    if (threadIdx.x == 0) {
+        bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.smem_pass = bc.glob_pass = bc.nviol = bc.retry = 0u;
+        bc.planes = 0ull;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    PlaneBuf& buf = pbuf[threadIdx.x >> 5];
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const float U = 5.9604645e-8f;   // unit roundoff of binary32
+    if (v < c.n_verts) {
+        float4 X = x_b[v];
+        float4 XP = x_in[v];
+        bool halted = false;
+        const f3 y0 = sub(xyz(XP), xyz(X));
+        f3 y = y0;
+        const bool movable = X.w > 0.f;
+        unsigned cnt = 0;
+        int np = 0;
+        bool over = false;
+        if (movable) {
+            cnt = c.count[v];
+            np = (int)min(cnt, (unsigned)c.p.K);
+            over = cnt > (unsigned)c.p.K;
+        }
+        const float4* pl = c.planes + (size_t)v * c.p.K;
+        if (!movable) {
+            y = mk(0.f, 0.f, 0.f);
+        } else if (over) {
+            // more planes than slots: bound the step by the smallest d of all planes
+            unsigned code = c.dmin_drop[v];
+            float dmin = (code == 0xFFFFFFFFu) ? 3.4e38f : ord2f(code);
+            for (int j = lane; j < np; j += 32) dmin = fminf(dmin, pl[j].w);
+            dmin = warp_min(dmin);
+            y = clamp_len(y0, fmaxf(dmin, 0.f));
+            if (lane == 0) atomicAdd(&bc.over, 1u);
+        } else if (np > 0) {
+            float mn = 3.4e38f, dabs = 0.f;
+            for (int j = lane; j < np; j += 32) {
+                float4 P = pl[j];
+                mn = fminf(mn, rho_at(y0, P));
+                dabs = fmaxf(dabs, fabsf(P.w));
+            }
+            mn = warp_min(mn);
+            dabs = warp_max(dabs);
+            if (mn < 0.f) {
+                if (lane == 0) atomicAdd(&bc.viol, 1u);
+                f3 ypass = y0;
+                bool conv = false;
+                for (int pass = 0; pass <= c.p.max_passes; ++pass) {
+                    float mnb = mn;
+                    if (pass > 0) {
+                        mnb = 3.4e38f;
+                        for (int j = lane; j < np; j += 32) mnb = fminf(mnb, rho_at(ypass, pl[j]));
+                        mnb = warp_min(mnb);
+                    }
+                    if (mnb >= 0.f) { conv = true; break; }
+                    if (pass == c.p.max_passes) break;
+                    f3 ynext;
+                    float Dmax;
+                    bool done = false;
+                    const float yb = len(ypass);
+                    float T = 2.f * (-mnb);
+                    for (int attempt = 0; attempt < 3 && !done; ++attempt) {
+                        float margin = 1e-3f * T + 64.f * U * (yb + T + dabs) + 1e-12f;
+                        T += margin;
+                        int m = 0;
+                        for (int j0 = 0; j0 < np; j0 += 32) {
+                            int j = j0 + lane;
+                            float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+                            bool take = false;
+                            if (j < np) {
+                                P = pl[j];
+                                take = rho_at(ypass, P) <= T;
+                            }
+                            unsigned bal = __ballot_sync(FULL, take);
+                            int pos = m + __popc(bal & ((1u << lane) - 1u));
+                            if (take && pos < PCAP) {
+                                buf.pl[pos] = P;
+                                buf.key[pos] = rho_at(y0, P);
+                                buf.idx[pos] = j;
+                            }
+                            m += __popc(bal);
+                        }
+                        __syncwarp();
+                        if (m > PCAP) break;
+                        if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
+                        int nvp = alg2_pass(c, lane, m,
+                                  [&](int e, float4& P, float& key, int& j) { P = buf.pl[e]; key = buf.key[e]; j = buf.idx[e]; },
+                                  ypass, ynext, Dmax);
+                        __syncwarp();
+                        if (Dmax <= T - margin) {
+                            done = true;
+                            if (lane == 0) { atomicAdd(&bc.smem_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
+                        } else {
+                            T = 2.f * Dmax;
+                        }
+                    }
+                    if (!done) {
+                        // too many candidate planes: pass over the full list in global memory
+                        int nvp = alg2_pass(c, lane, np,
+                                  [&](int e, float4& P, float& key, int& j) { P = pl[e]; key = rho_at(y0, P); j = e; },
+                                  ypass, ynext, Dmax);
+                        if (lane == 0) { atomicAdd(&bc.glob_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
+                    }
+                    ypass = ynext;
+                }
+                if (conv) y = ypass;
+                else { y = mk(0.f, 0.f, 0.f); halted = true; }
+            }
+        }
+        if (STEP && movable && !halted) y = clamp_len(y, c.p.r);
+        f3 xn = add(xyz(X), y);
+        // final feasibility check on the stored binary32 position: a
+        // rounding-error filter decides most planes, FP64 the rest
+        bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
+        if (movable && !halted && np > 0 && (changed || over)) {
+            f3 dl = sub(xn, xyz(X));
+            float tau = c.p.tau + 2.f * U * (fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z));
+            bool fail = false, undecided = false;
+            for (int j = lane; j < np; j += 32) {
+                float4 P = pl[j];
+                float rho = rho_at(dl, P);
+                float S = fabsf(dl.x * P.x) + fabsf(dl.y * P.y) + fabsf(dl.z * P.z) + fabsf(P.w);
+                float err = 8.f * U * S;
+                if (rho - err >= -tau) continue;
+                if (rho + err < -tau) { fail = true; continue; }
+                double rd = ((double)xn.x - X.x) * P.x + ((double)xn.y - X.y) * P.y +
+                            ((double)xn.z - X.z) * P.z + (double)P.w;
+                undecided = true;
+                if (rd < -(double)tau) fail = true;
+            }
+            unsigned und = __ballot_sync(FULL, undecided);
+            if (und && lane == 0) atomicAdd(&bc.f64, 1u);
+            if (__any_sync(FULL, fail)) {
+                halted = true;
+                y = mk(0.f, 0.f, 0.f);
+                xn = xyz(X);
+                if (lane == 0) atomicAdd(&bc.fhalt, 1u);
+            }
+        }
+        if (halted && lane == 0) atomicAdd(&bc.halt, 1u);
+        if (lane == 0 && movable && cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
+        if (lane == 0) {
+            if (STEP) {
+                f3 dd = sub(y, y0);
+                if (movable && len(dd) > 2.f * c.p.eps) c.flags[0] = 1;
+                if (movable) x_out[v] = make_float4(xn.x, xn.y, xn.z, X.w);
+            } else {
+                if (movable) x_out[v] = make_float4(xn.x, xn.y, xn.z, XP.w);
+                if (halt_out) halt_out[v] = halted ? 1 : 0;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (bc.viol) atomicAdd(&c.stats->violated_verts, (u64)bc.viol);
+        if (bc.halt) atomicAdd(&c.stats->halts, (u64)bc.halt);
+        if (bc.over) atomicAdd(&c.stats->overflow_verts, (u64)bc.over);
+        if (bc.f64) atomicAdd(&c.stats->feas_fp64, (u64)bc.f64);
+        if (bc.fhalt) atomicAdd(&c.stats->feas_halts, (u64)bc.fhalt);
+        if (bc.maxc) atomicMax(&c.stats->max_planes, bc.maxc);
+        if (bc.planes) atomicAdd(&c.stats->planes, bc.planes);
+        if (bc.smem_pass) atomicAdd(&c.stats->aux[0], (u64)bc.smem_pass);
+        if (bc.glob_pass) atomicAdd(&c.stats->aux[1], (u64)bc.glob_pass);
+        if (bc.nviol) atomicAdd(&c.stats->aux[2], (u64)bc.nviol);
+        if (bc.retry) atomicAdd(&c.stats->aux[5], (u64)bc.retry);
+    }
+}
+
+// ------------------------------------------------------------------ XPBD
+
+// Alg. 4 prediction: x~ = x + dt v + dt^2 g for movable vertices; keeps x^n.
+__global__ void k_predict(DevCtx c, const float4* __restrict__ x, const float4* __restrict__ vel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n_verts) return;
+    float4 X = x[i], V = vel[i];
+    bool fin = isfinite(X.x) && isfinite(X.y) && isfinite(X.z) && isfinite(X.w) &&
+               isfinite(V.x) && isfinite(V.y) && isfinite(V.z);
+    if (!fin) atomicOr(&c.stats->error_flags, ERR_NONFINITE);
+    c.x_n[i] = X;
+    float dt = c.p.dt;
+    if (X.w > 0.f) {
+        X.x = X.x + dt * V.x + dt * dt * c.p.gx;
+        X.y = X.y + dt * V.y + dt * dt * c.p.gy;
+        X.z = X.z + dt * V.z + dt * dt * c.p.gz;
+    }
+    c.x_tilde[i] = X;
+}
+
+// Start of an iteration: x_s <- x~; clear the per-iteration region counters.
+__global__ void k_iter_begin(DevCtx c) {
+    if (c.flags[1]) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < c.n_verts) {
+        c.x_s[i] = c.x_tilde[i];
+        c.count[i] = 0u;
+        c.dmin_drop[i] = 0xFFFFFFFFu;
+    }
+    if (i == 0) c.flags[0] = 0;
+}
+
+// One colour of the Gauss-Seidel sweep over edge-distance constraints:
+// C = |xa - xb| - L0, dlambda = (-C - alpha~ lambda) / (wa + wb + alpha~).
+__global__ void k_xpbd_color(DevCtx c, int e0, int e1) {
+    if (c.flags[1]) return;
+    int i = e0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= e1) return;
+    int2 e = c.edges_col[i];
+    float4 A = c.x_s[e.x], B = c.x_s[e.y];
+    float at = c.p.alpha_tilde;
+    float wsum = A.w + B.w + at;
+    if (wsum == 0.f) return;
+    f3 d = sub(xyz(A), xyz(B));
+    float L = len(d);
+    if (L == 0.f) return;
+    float lam = c.lambda[i];
+    float dl = (-(L - c.rest_col[i]) - at * lam) / wsum;
+    f3 nd = mul(d, 1.f / L);
+    float sa = A.w * dl, sb = B.w * dl;
+    c.x_s[e.x] = make_float4(A.x + sa * nd.x, A.y + sa * nd.y, A.z + sa * nd.z, A.w);
+    c.x_s[e.y] = make_float4(B.x - sb * nd.x, B.y - sb * nd.y, B.z - sb * nd.z, B.w);
+    c.lambda[i] = lam + dl;
+}
+
+// End of an iteration: count it, and with early exit stop once converged.
+__global__ void k_iter_end(DevCtx c, int early_exit) {
+    if (c.flags[1]) return;
+    c.stats->iterations += 1ull;
+    if (early_exit && c.flags[0] == 0) c.flags[1] = 1;
+}
+
+// Alg. 4 update: v = (x - x^n) / dt.
+__global__ void k_update(DevCtx c, const float4* __restrict__ x, float4* vel) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) { c.flags[1] = 0; c.stats->steps += 1ull; }
+    if (i >= c.n_verts) return;
+    float4 X = x[i], N = c.x_n[i];
+    float inv = 1.f / c.p.dt;
+    vel[i] = make_float4((X.x - N.x) * inv, (X.y - N.y) * inv, (X.z - N.z) * inv, vel[i].w);
+}
+
+__global__ void k_rest_lengths(const int2* edges_col, const float4* __restrict__ x, float* rest, int ne) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ne) return;
+    int2 e = edges_col[i];
+    rest[i] = len(sub(xyz(x[e.x]), xyz(x[e.y])));
+}
+
+__global__ void k_load_regions(DevCtx c, const float4* planes, const int* count, int cap) {
+    long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)c.n_verts * cap;
+    if (idx >= total) return;
+    int v = (int)(idx / cap), j = (int)(idx % cap);
+    int n = count[v];
+    if (j == 0) { c.count[v] = (unsigned)n; c.dmin_drop[v] = 0xFFFFFFFFu; }
+    if (j < n && j < c.p.K) c.planes[(size_t)v * c.p.K + j] = planes[(size_t)v * cap + j];
+}
+
+__global__ void k_dmin_export(DevCtx c, float* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n_verts) return;
+    unsigned code = c.dmin_drop[i];
+    out[i] = (code == 0xFFFFFFFFu) ? __int_as_float(0x7f800000) : ord2f(code);
+}
+
+// ------------------------------------------------------------- launchers
+
+static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
+
+void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* poh,
+                  unsigned* tile_sums, int n_buckets_total, StageTimer* tm) {
+    PairOut po{};
+    if (poh) {
+        for (int k = 0; k < 3; ++k) { po.out[k] = poh->out[k]; po.cap[k] = poh->cap[k]; }
+        po.count = poh->count;
+    }
+    cudaMemsetAsync(c.ext_bits, 0, 3 * sizeof(unsigned), st);
+    cudaMemsetAsync(c.ext_sum, 0, 3 * sizeof(u64), st);
+    cudaMemsetAsync(c.big_count, 0, 2 * sizeof(unsigned), st);
+    cudaMemsetAsync(c.bucket_count, 0, (size_t)(n_buckets_total + 1) * sizeof(unsigned), st);
+    cudaMemsetAsync(c.bucket_fill, 0, (size_t)n_buckets_total * sizeof(unsigned), st);
+    if (tm) tm->mark(ST_MISC, st);
+    if (c.n_items > 0) k_extent<<<nblk(c.n_items, 256), 256, 0, st>>>(c, x);
+    if (tm) tm->mark(ST_GRID_EXTENT, st);
+    if (c.n_items > 0) k_bucket_count<<<nblk(c.n_items, 256), 256, 0, st>>>(c, x);
+    if (tm) tm->mark(ST_GRID_COUNT, st);
+    int n = n_buckets_total + 1;
+    int tiles = nblk(n, SCAN_TILE);
+    k_scan_tiles<<<tiles, SCAN_THREADS, 0, st>>>(c, c.bucket_count, n, tile_sums);
+    k_scan_top<<<1, SCAN_THREADS, 0, st>>>(c, tile_sums, tiles);
+    k_scan_apply<<<tiles, SCAN_THREADS, 0, st>>>(c, c.bucket_count, n, tile_sums);
+    if (tm) tm->mark(ST_GRID_SCAN, st);
+    if (c.n_items > 0) k_bucket_scatter<<<nblk(c.n_items, 256), 256, 0, st>>>(c, x);
+    if (tm) tm->mark(ST_GRID_SCATTER, st);
+    cudaMemsetAsync(c.unit_count, 0, 3 * sizeof(unsigned), st);
+    int nqb = c.bucket_base[KIND_VQ];
+    k_make_units<<<nblk(nqb, 256), 256, 0, st>>>(c);
+    if (tm) tm->mark(ST_GRID_UNITS, st);
+    const int G = c.n_sm * 8;
+    if (mode == MODE_PLANES) {
+        if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (tm) tm->mark(ST_EMIT_VF, st);
+        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (tm) tm->mark(ST_EMIT_VF_BIG, st);
+        if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (tm) tm->mark(ST_EMIT_EE, st);
+        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (tm) tm->mark(ST_EMIT_EE_BIG, st);
+        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (tm) tm->mark(ST_EMIT_PP, st);
+    } else {
+        if (c.n_tris > 0) {
+            k_emit<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+            k_emit_big<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        }
+        if (c.n_edges > 0) {
+            k_emit<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+            k_emit_big<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        }
+        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+    }
+}
+
+void launch_clear_regions(const DevCtx& c, cudaStream_t st) {
+    cudaMemsetAsync(c.count, 0, (size_t)c.n_verts * sizeof(unsigned), st);
+    cudaMemsetAsync(c.dmin_drop, 0xFF, (size_t)c.n_verts * sizeof(unsigned), st);
+}
+
+void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st) {
+    long threads = (long)c.n_verts * 32;
+    if (threads > 0) k_project<false><<<nblk(threads, PROJ_WARPS * 32), PROJ_WARPS * 32, 0, st>>>(c, xb, xio, xio, halt);
+}
+
+void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st) {
+    cudaMemsetAsync(c.lambda, 0, (size_t)(c.n_edges > 0 ? c.n_edges : 1) * sizeof(float), st);
+    cudaMemsetAsync(c.flags, 0, 2 * sizeof(int), st);
+    if (c.n_verts > 0) k_predict<<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, v);
+}
+
+void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* color_off, int n_colors,
+                      unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm) {
+    if (c.n_verts > 0) k_iter_begin<<<nblk(c.n_verts, 256), 256, 0, st>>>(c);
+    launch_build(c, x, st, MODE_PLANES, nullptr, tile_sums, n_buckets_total, tm);
+    for (int k = 0; k < n_colors; ++k) {
+        int e0 = color_off[k], e1 = color_off[k + 1];
+        if (e1 > e0) k_xpbd_color<<<nblk(e1 - e0, 256), 256, 0, st>>>(c, e0, e1);
+    }
+    if (tm) tm->mark(ST_XPBD, st);
+    long threads = (long)c.n_verts * 32;
+    if (threads > 0) k_project<true><<<nblk(threads, PROJ_WARPS * 32), PROJ_WARPS * 32, 0, st>>>(c, x, c.x_s, x, nullptr);
+    if (tm) tm->mark(ST_PROJECT, st);
+    k_iter_end<<<1, 1, 0, st>>>(c, early_exit);
+}
+
+void launch_update(const DevCtx& c, const float4* x, float4* v, cudaStream_t st) {
+    if (c.n_verts > 0) k_update<<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, v);
+    else k_update<<<1, 32, 0, st>>>(c, x, v);
+}
+
+void launch_rest_lengths(const int2* edges_col, const float4* x, float* rest, int ne, cudaStream_t st) {
+    if (ne > 0) k_rest_lengths<<<nblk(ne, 256), 256, 0, st>>>(edges_col, x, rest, ne);
+}
+
+void launch_load_regions(const DevCtx& c, const float4* planes, const int* count, int cap, cudaStream_t st) {
+    long total = (long)c.n_verts * cap;
+    if (total > 0) k_load_regions<<<nblk(total, 256), 256, 0, st>>>(c, planes, count, cap);
+}
+
+void launch_dmin_export(const DevCtx& c, float* out, cudaStream_t st) {
+    if (c.n_verts > 0) k_dmin_export<<<nblk(c.n_verts, 256), 256, 0, st>>>(c, out);
+}
+
+}  // namespace ccfr

@@ -166,7 +166,7 @@ def _assemble(name, parts_p, parts_w, parts_tris, parts_edges, params, v=None) -
 def cloth_on_sphere(n_side: int = 32, spacing: float = 0.01, jitter: float = 1e-3,
                     radius: float = 0.10, slices: int = 50, stacks: int = 41,
                     lift: float = 0.02, seed: int = 1, iters: int = 10, steps: int = 20,
-                    cloth_mass: float = 1e-3, plane_capacity: int = 64) -> Scene:
+                    cloth_mass: float = 1e-3, plane_capacity: int = 256) -> Scene:
     """Square cloth dropped on a static UV sphere.
 
     Defaults: 32x32 vertices at 1 cm (1,922 triangles) with seeded +-1 mm
@@ -187,7 +187,7 @@ def cloth_on_sphere(n_side: int = 32, spacing: float = 0.01, jitter: float = 1e-
 def cloth_stack(n_side: int = 256, layers: int = 4, spacing: float = 4e-3,
                 gap: float = 2e-3, speed: float = 0.5, seed: int = 2, jitter: float = 0.0,
                 iters: int = 20, steps: int = 100, cloth_mass: float = 1e-3,
-                r: float = 2e-3, xi: float = 1e-3, plane_capacity: int = 128) -> Scene:
+                r: float = 2e-3, xi: float = 1e-3, plane_capacity: int = 1024) -> Scene:
     """Self-colliding stack of parallel cloth layers.
 
     Defaults: 4 layers of 256x256 vertices at 4 mm, 2 mm apart in y, every
@@ -212,7 +212,7 @@ def cloth_stack(n_side: int = 256, layers: int = 4, spacing: float = 4e-3,
 def wires(n_grid: int = 128, n_seg: int = 64, seg_len: float = 2e-3, axis_pitch: float = 0.02,
           seed: int = 3, grate: bool = True, grate_pitch: float = 0.01,
           iters: int = 10, steps: int = 50, strand_mass: float = 1e-4,
-          plane_capacity: int = 64) -> Scene:
+          plane_capacity: int = 128) -> Scene:
     """Helical polyline strands above a static grate of rods (edge-edge only).
 
     Defaults: 128x128 = 16,384 strands of 64 segments of 2 mm, helix radius
