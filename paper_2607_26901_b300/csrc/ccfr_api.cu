@@ -211,20 +211,23 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     d.p.K = params->plane_capacity;
     d.p.cell_size = params->cell_size;
     // grid geometry: tables of triangles, edges, isolated points, vertices
-    int nk[4] = {T, E, d.n_pts, N};
-    d.n_items = T + E + d.n_pts + N;
+    int nk[5] = {T, E, d.n_pts, N, E};
+    d.n_items = T + E + d.n_pts + N + E;
     d.item_base[0] = 0;
     d.item_base[1] = T;
     d.item_base[2] = T + E;
     d.item_base[3] = T + E + d.n_pts;
+    d.item_base[4] = T + E + d.n_pts + N;
     int btot = 0;
-    for (int k = 0; k < 4; ++k) {
-        unsigned M = next_pow2((unsigned)(2 * nk[k] > 64 ? 2 * nk[k] : 64));
+    for (int k = 0; k < 5; ++k) {
+        // the oversized-edge table is sized for a quarter of the edges (load factor <= 8 if all are oversized)
+        int want = (k == KIND_BIGE) ? nk[k] / 4 : 2 * nk[k];
+        unsigned M = next_pow2((unsigned)(want > 64 ? want : 64));
         d.bucket_base[k] = btot;
         d.bucket_mask[k] = (int)(M - 1);
         btot += (int)M;
     }
-    d.bucket_base[4] = btot;
+    d.bucket_base[5] = btot;
     c->n_buckets_total = btot;
     d.n_kind[0] = T;
     d.n_kind[1] = E;

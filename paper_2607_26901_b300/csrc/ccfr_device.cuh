@@ -27,7 +27,9 @@ typedef unsigned long long u64;
 // Grid tables: triangles, edges and isolated points (queries and items of
 // their own kind), and all vertices bucketed with the triangle cell size (the
 // items of the vertex-face queries).
-enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, N_KINDS = 4 };
+// A fifth table holds the oversized edges again, with a cell as large as the
+// largest edge, so that oversized edge pairs are found by a local search.
+enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, N_TABLES = 5 };
 enum { MODE_PLANES = 0, MODE_PAIRS = 1 };
 enum { ERR_NONFINITE = 1u };
 
@@ -78,10 +80,10 @@ struct DevCtx {
     const float* rest_col;
     float* lambda;
     // grid
-    int n_items;                // n_tris + n_edges + n_pts + n_verts
-    int item_base[4];           // first item of each table in the item space
-    int bucket_base[5];         // first bucket of each table (+ total)
-    int bucket_mask[4];         // M_table - 1
+    int n_items;                // n_tris + 2 n_edges + n_pts + n_verts
+    int item_base[5];           // first item of each table in the item space
+    int bucket_base[6];         // first bucket of each table (+ total)
+    int bucket_mask[5];         // M_table - 1
     unsigned* ext_bits;         // [3] largest padded extent per kind (float bits)
     u64* ext_sum;               // [3] sum of padded extents per kind, in nanometres
     int n_kind[3];              // primitives per kind (triangles, edges, points)
@@ -131,6 +133,10 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // vertex box, so vertex boxes always fit in one cell.  Primitives whose box
 // spans more than a cell are handled by the oversized pass.
 __device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
+    if (kind == KIND_BIGE) {
+        float h = __uint_as_float(c.ext_bits[KIND_EDGE]) * 1.0625f;
+        return (h > 0.f) ? h : 1.f;
+    }
     float mean = (c.n_kind[kind] > 0) ? (float)((double)c.ext_sum[kind] * 1e-9 / (double)c.n_kind[kind]) : 0.f;
     float h = mean * c.cell_factor;
     float hmin = 2.f * c.p.pad * 1.0625f;

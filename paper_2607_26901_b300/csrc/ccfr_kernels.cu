@@ -52,10 +52,15 @@ __device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restric
         kind = KIND_PT;
         id = c.pts[i - c.item_base[KIND_PT]];
         a = x[id]; b = a; d = a;
-    } else {
+    } else if (i < c.item_base[KIND_BIGE]) {
         kind = KIND_VQ;
         id = i - c.item_base[KIND_VQ];
         a = x[id]; b = a; d = a;
+    } else {
+        kind = KIND_BIGE;
+        id = i - c.item_base[KIND_BIGE];
+        int2 e = c.edges[id];
+        a = x[e.x]; b = x[e.y]; d = b;
     }
     lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), c.p.pad);
     lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), c.p.pad);
@@ -111,6 +116,7 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     float lo[3], hi[3];
     int id;
     int kind = item_box(c, x, i, lo, hi, id);
+    if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
         unsigned s = atomicAdd(&c.big_count[kind], 1u);
         unsigned o = c.big_base[kind] + s;
@@ -132,6 +138,7 @@ __global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
     float lo[3], hi[3];
     int id;
     int kind = item_box(c, x, i, lo, hi, id);
+    if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
     unsigned packed;
     unsigned b = item_bucket_of(c, kind, lo, packed);
@@ -695,22 +702,33 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                     }
         }
         if (QK == KIND_EDGE) {
-            // oversized-oversized pairs, found from the smaller id
-            for (unsigned w0 = 0; w0 < nbig; w0 += 32) {
-                const unsigned w = w0 + lane;
-                int2 pr = make_int2(-1, -1);
-                if (w < nbig) {
-                    const float4 b0 = c.big_box[2 * (c.big_base[QK] + w)];
-                    const int o2 = __float_as_int(b0.w);
-                    if (o2 > o) {
-                        const float4 b1 = c.big_box[2 * (c.big_base[QK] + w) + 1];
-                        if (lo[0] <= b1.x && b0.x <= hi[0] && lo[1] <= b1.y && b0.y <= hi[1] && lo[2] <= b1.z &&
-                            b0.z <= hi[2])
-                            pr = make_int2(o, o2);
+            // oversized-oversized pairs, found from the smaller id in the table of
+            // oversized edges (cell = the largest edge box: a 3x3x3 search)
+            const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
+            const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
+            const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
+            for (int dz = -1; dz <= 1; ++dz)
+                for (int dy = -1; dy <= 1; ++dy)
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        const unsigned b = bb + (cell_hash(bx + dx, by + dy, bz + dz) & bm);
+                        const unsigned pk = cell_pack(bx + dx, by + dy, bz + dz);
+                        const unsigned t1 = c.bucket_count[b + 1];
+                        for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
+                            const unsigned s = s0 + lane;
+                            int2 pr = make_int2(-1, -1);
+                            if (s < t1) {
+                                const float4 i1 = c.rec[2 * s + 1];
+                                if (__float_as_uint(i1.w) == pk) {
+                                    const float4 i0 = c.rec[2 * s];
+                                    const int o2 = __float_as_int(i0.w);
+                                    if (o2 > o && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] &&
+                                        lo[2] <= i1.z && i0.z <= hi[2])
+                                        pr = make_int2(o, o2);
+                                }
+                            }
+                            push(pr.x >= 0, pr);
+                        }
                     }
-                }
-                push(pr.x >= 0, pr);
-            }
         }
     }
     __syncwarp();
