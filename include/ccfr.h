@@ -103,7 +103,8 @@ typedef struct {
                                                          over the full list, [2] violated
                                                          planes processed, [3] oversized
                                                          triangles, [4] oversized edges,
-                                                         [5] candidate-list retries          */
+                                                         [5] candidate-list retries, [6]
+                                                         planes of the violated vertices     */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
 } ccfr_stats;
@@ -146,13 +147,13 @@ ccfr_status ccfr_project(ccfr_ctx* ctx, const float* x, float* x_io, unsigned ch
 ccfr_status ccfr_step(ccfr_ctx* ctx, float* x, float* v, void* stream);
 
 /* Number of stages reported by ccfr_step_timed. */
-#define CCFR_N_STAGES 14
+#define CCFR_N_STAGES 15
 
 /* ccfr_step launched kernel by kernel with CUDA events between the stages
  * (prediction, grid extent, grid count, grid scan, grid scatter, vertex-face
  * narrow phase, edge-edge narrow phase, point-point narrow phase, XPBD sweep,
- * projection, bookkeeping, work units, oversized vertex-face and edge-edge
- * passes): the per-stage split of the paper's timing table
+ * projection scan, bookkeeping, work units, oversized vertex-face and
+ * edge-edge passes, projection of the violated vertices): the per-stage split of the paper's timing table
  * (Table 1: broad, narrow, resolution, XPBD).  stage_ms (host, n_stages >=
  * CCFR_N_STAGES doubles) receives milliseconds summed over the iterations.
  * Synchronises `stream`. */

@@ -189,7 +189,7 @@ class Context:
 
     def step_timed(self, x, v, stream=None) -> dict:
         """One step launched kernel by kernel; returns {stage: ms}."""
-        n = 14
+        n = 15
         out = (C.c_double * n)()
         _check(lib().ccfr_step_timed(self.h, _ptr(x), _ptr(v), out, n, _stream(stream)), "ccfr_step_timed")
         return {lib().ccfr_stage_name(i).decode(): out[i] for i in range(n)}

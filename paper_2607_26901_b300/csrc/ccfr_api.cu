@@ -6,7 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/ccfr.h"
+#include "ccfr.h"
 #include "ccfr_internal.h"
 
 using namespace ccfr;
@@ -104,7 +104,7 @@ void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer
 
 const char* kStageNames[N_STAGES] = {"predict", "grid_extent", "grid_count", "grid_scan", "grid_scatter",
                                      "emit_vf", "emit_ee", "emit_pp", "xpbd", "project", "misc",
-                                     "grid_units", "emit_vf_big", "emit_ee_big"};
+                                     "grid_units", "emit_vf_big", "emit_ee_big", "project_heavy"};
 
 }  // namespace
 
@@ -277,6 +277,8 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     ok &= dalloc(c, &d.ext_sum, 3) == cudaSuccess;
     ok &= dalloc(c, &d.big, (size_t)T + E) == cudaSuccess;
     ok &= dalloc(c, &d.big_box, 2 * ((size_t)T + E)) == cudaSuccess;
+    ok &= dalloc(c, &d.work, (size_t)N) == cudaSuccess;
+    ok &= dalloc(c, &d.work_count, 1) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
     ok &= dalloc(c, &c->tile_sums, SCAN_TILE) == cudaSuccess;
@@ -309,6 +311,7 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
         else c->rest_pending = true;
         err = cudaGetLastError();
     }
+    if (err == cudaSuccess) err = configure_kernels();
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) { free_ctx(c); return CCFR_ERR_CUDA; }

@@ -110,6 +110,8 @@ struct DevCtx {
     float4* x_s;
     int* flags;                 // [0] not converged, [1] done (early exit)
     int n_sm;                   // streaming multiprocessors (persistent grids)
+    int4* work;                 // [n_verts] vertices queued for the heavy projection
+    unsigned* work_count;       // [1]
     DevStats* stats;
 };
 

@@ -9,7 +9,7 @@ namespace ccfr {
 enum Stage {
     ST_PREDICT = 0, ST_GRID_EXTENT, ST_GRID_COUNT, ST_GRID_SCAN, ST_GRID_SCATTER,
     ST_EMIT_VF, ST_EMIT_EE, ST_EMIT_PP, ST_XPBD, ST_PROJECT, ST_MISC, ST_GRID_UNITS, ST_EMIT_VF_BIG,
-    ST_EMIT_EE_BIG, N_STAGES
+    ST_EMIT_EE_BIG, ST_PROJECT_HEAVY, N_STAGES
 };
 
 struct StageTimer {
@@ -29,6 +29,7 @@ struct PairOutHost {
 
 void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* po,
                   unsigned* tile_sums, int n_buckets_total, StageTimer* tm = nullptr);
+cudaError_t configure_kernels();
 void launch_clear_regions(const DevCtx& c, cudaStream_t st);
 void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st);
 void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st);

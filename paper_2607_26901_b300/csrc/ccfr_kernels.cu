@@ -769,7 +769,7 @@ __device__ __forceinline__ void ero_push(Ero& S, d3 v, d3 n, double b) {
 
 // One Alg. 1 step: project zt onto the intersection of the stored hyperplanes
 // and n . z = b.
-__device__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double eps) {
+__device__ __noinline__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double eps) {
     if (S.m == 0) {
         double beta0 = ddot(n, n);
         if (fabs(beta0) < eps) return;
@@ -822,17 +822,22 @@ __device__ __forceinline__ f3 clamp_len(f3 y, float lim) {
     return (L > lim) ? mul(y, lim / L) : y;
 }
 
-struct BlockCounters { unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry; unsigned long long planes; };
-
-// Per-warp shared-memory list of the planes that can become violated during
-// one pass of Alg. 2 (see k_project).
-constexpr int PCAP = 480;
-constexpr int PROJ_WARPS = 4;
-struct PlaneBuf {
-    float4 pl[PCAP];
-    float key[PCAP];
-    int idx[PCAP];
+struct BlockCounters {
+    unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry;
+    unsigned long long planes, heavy_planes;
 };
+
+// Per-warp shared memory of the projection: the candidate planes of a pass
+// as (sort key, slot) pairs, double-buffered for a stable radix sort, plus
+// the digit histogram.  Dynamic shared memory (PROJ_WARPS x 13 KB).
+constexpr int SCAP = 1024;
+constexpr int PROJ_WARPS = 4;
+struct SortBuf {
+    unsigned key[2][SCAP];
+    unsigned short idx[2][SCAP];
+    unsigned hist[256];
+};
+constexpr size_t PROJ_SMEM = PROJ_WARPS * sizeof(SortBuf);
 
 __device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
 
@@ -909,178 +914,206 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
     return nv;
 }
 
-// One warp per vertex.  STEP = true: x_b is the collision-free iterate x_c
-// (read and overwritten), candidates come from x_in (the XPBD iterate), the
-// step is clamped to r, and the convergence flag is raised.
-//
-// A pass of Alg. 2 only ever acts on planes that are violated at its current
-// iterate.  With b the pass input and D the largest distance the iterate
-// moves from b during the pass, rho_k(y) >= rho_k(b) - D for every plane, so
-// planes with rho_k(b) > T >= D + margin are never touched.  The pass is run
-// on the planes with rho_k(b) <= T, gathered into shared memory, and is
-// repeated with a larger T if D turns out to exceed T - margin; the result is
-// the same as a pass over the full sorted list.  The final pass can only
-// confirm convergence (any violation there ends in the halt), so it is a
-// single scan.
+// Stable LSD radix sort (four 8-bit digits) of n (key, slot) pairs held in
+// buffer 0, by one warp; the result is in buffer 0.  Equal digits keep their
+// relative order (ranks from __match_any_sync within each 32-entry chunk).
+__device__ void warp_radix_sort(SortBuf& sb, int n, int lane) {
+    int src = 0;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int shift = 0; shift < 32; shift += 8) {
+        for (int b = lane; b < 256; b += 32) sb.hist[b] = 0u;
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) atomicAdd(&sb.hist[(sb.key[src][i] >> shift) & 255u], 1u);
+        __syncwarp();
+        // exclusive scan of the 256 bins, 8 per lane
+        unsigned loc[8], tot = 0;
+        #pragma unroll
+        for (int k = 0; k < 8; ++k) { loc[k] = sb.hist[lane * 8 + k]; tot += loc[k]; }
+        unsigned inc = tot;
+        #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
+        }
+        unsigned off = inc - tot;
+        __syncwarp();
+        #pragma unroll
+        for (int k = 0; k < 8; ++k) { sb.hist[lane * 8 + k] = off; off += loc[k]; }
+        __syncwarp();
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < n;
+            const unsigned k = valid ? sb.key[src][i] : 0u;
+            const unsigned short j = valid ? sb.idx[src][i] : 0;
+            const unsigned dg = valid ? ((k >> shift) & 255u) : 256u;
+            // lanes holding the same digit: intersect the eight bit-slice ballots
+            unsigned peers = __ballot_sync(FULL, valid) ;
+            if (!valid) peers = ~peers;
+            #pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const unsigned bit = __ballot_sync(FULL, (dg >> b) & 1u);
+                peers &= ((dg >> b) & 1u) ? bit : ~bit;
+            }
+            const unsigned start = valid ? sb.hist[dg] : 0u;
+            __syncwarp();
+            if (valid) {
+                const unsigned dst = start + __popc(peers & lt);
+                sb.key[src ^ 1][dst] = k;
+                sb.idx[src ^ 1][dst] = j;
+                if ((peers & lt) == 0u) sb.hist[dg] = start + __popc(peers);
+            }
+            __syncwarp();
+        }
+        src ^= 1;
+    }
+    // four passes: the sorted data is back in buffer 0
+}
+
+// Plane order of Alg. 2 among equal sort keys: the plane's own bits and its
+// slot (identical planes may go in any order; distinct ones need a fixed one).
+__device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
+    float4 A = pl[a], B = pl[b];
+    unsigned x0 = f2ord(A.w), y0 = f2ord(B.w);
+    if (x0 != y0) return x0 < y0;
+    x0 = f2ord(A.x); y0 = f2ord(B.x);
+    if (x0 != y0) return x0 < y0;
+    x0 = f2ord(A.y); y0 = f2ord(B.y);
+    if (x0 != y0) return x0 < y0;
+    x0 = f2ord(A.z); y0 = f2ord(B.z);
+    if (x0 != y0) return x0 < y0;
+    return a < b;
+}
+
+// One pass of Alg. 2 over the sorted candidates sb.key/idx[0][0..m): walk
+// the list in order, 32 planes per step; the first violated plane of a step
+// is handled (Alg. 1 + retraction) and the walk resumes right after it.
+__device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, const float4* pl, f3 ypass,
+                           f3& y_out, float& Dmax) {
+    d3 zt = dk(0.0, 0.0, 0.0);
+    const d3 yp = d_of(ypass);
+    Dmax = 0.f;
+    Ero S;
+    S.m = 0;
+    int nv = 0;
+    f3 yt = ypass;
+    int pos = 0;
+    while (pos < m) {
+        const int e = pos + lane;
+        float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool viol = false;
+        if (e < m) {
+            P = pl[sb.idx[0][e]];
+            viol = rho_at(yt, P) < 0.f;
+        }
+        const unsigned bal = __ballot_sync(FULL, viol);
+        if (!bal) { pos += 32; continue; }
+        const int f = __ffs(bal) - 1;
+        const d3 nrm = dk(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f), __shfl_sync(FULL, P.z, f));
+        const double d = __shfl_sync(FULL, P.w, f);
+        ++nv;
+        double bz = -d - ddot(nrm, yp);
+        if (S.m < 3) ortho_step(zt, nrm, bz, S, (double)c.p.eps_dep);
+        f3 yn = f_of(dadd(yp, zt));
+        float L = len(yn);
+        yn = (L > c.p.eps) ? mul(yn, (L - c.p.eps) / L) : mk(0.f, 0.f, 0.f);
+        zt = dsub(d_of(yn), yp);
+        Dmax = fmaxf(Dmax, len(sub(yn, ypass)));
+        yt = f_of(dadd(yp, zt));
+        pos += f + 1;
+    }
+    y_out = f_of(dadd(yp, zt));
+    return nv;
+}
+
+// Minimum of rho over a vertex's planes at y, and the largest |d|; four
+// independent loads in flight per lane.
+__device__ __forceinline__ void scan_min_rho(const float4* pl, int np, f3 y, int lane, float& mn, float& dabs) {
+    mn = 3.4e38f;
+    dabs = 0.f;
+    for (int j0 = lane; j0 < np; j0 += 128) {
+        float4 P[4];
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int j = j0 + 32 * k;
+            P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 3.4e38f);
+        }
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            mn = fminf(mn, rho_at(y, P[k]));
+            if (j0 + 32 * k < np) dabs = fmaxf(dabs, fabsf(P[k].w));
+        }
+    }
+    mn = warp_min(mn);
+    dabs = warp_max(dabs);
+}
+
+// Final feasibility check on the stored binary32 position xn: every plane
+// must hold within tau plus the binary32 rounding of the position; a
+// rounding-error filter decides most planes, FP64 the rest.  Returns true
+// when the position fails (the vertex then halts).
+__device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4* pl, int np, float4 X, f3 xn,
+                                                  int lane, bool& used_fp64) {
+    const float U = 5.9604645e-8f;
+    f3 dl = sub(xn, xyz(X));
+    float tau = c.p.tau + 2.f * U * (fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z));
+    bool fail = false, undecided = false;
+    for (int j0 = lane; j0 < np; j0 += 128) {
+        float4 P[4];
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int j = j0 + 32 * k;
+            P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 1.f);
+        }
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float rho = rho_at(dl, P[k]);
+            float S = fabsf(dl.x * P[k].x) + fabsf(dl.y * P[k].y) + fabsf(dl.z * P[k].z) + fabsf(P[k].w);
+            float err = 8.f * U * S;
+            if (rho - err >= -tau) continue;
+            if (rho + err < -tau) { fail = true; continue; }
+            double rd = ((double)xn.x - X.x) * P[k].x + ((double)xn.y - X.y) * P[k].y + ((double)xn.z - X.z) * P[k].z +
+                        (double)P[k].w;
+            undecided = true;
+            if (rd < -(double)tau) fail = true;
+        }
+    }
+    used_fp64 = __any_sync(FULL, undecided);
+    return __any_sync(FULL, fail);
+}
+
+// Common end of a vertex: max-step clamp (STEP), final check, write-back,
+// convergence flag and counters.
 template <bool STEP>
-__global__ void __launch_bounds__(PROJ_WARPS * 32) k_project(DevCtx c, const float4* x_b, const float4* x_in,
-                                                              float4* x_out, unsigned char* halt_out) {
-    if (STEP && c.flags[1]) return;
-    __shared__ BlockCounters bc;
-    __shared__ PlaneBuf pbuf[PROJ_WARPS];
-    if (threadIdx.x == 0) {
-        bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.smem_pass = bc.glob_pass = bc.nviol = bc.retry = 0u;
-        bc.planes = 0ull;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    PlaneBuf& buf = pbuf[threadIdx.x >> 5];
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const float U = 5.9604645e-8f;   // unit roundoff of binary32
-    if (v < c.n_verts) {
-        float4 X = x_b[v];
-        float4 XP = x_in[v];
-        bool halted = false;
-        const f3 y0 = sub(xyz(XP), xyz(X));
-        f3 y = y0;
-        const bool movable = X.w > 0.f;
-        unsigned cnt = 0;
-        int np = 0;
-        bool over = false;
-        if (movable) {
-            cnt = c.count[v];
-            np = (int)min(cnt, (unsigned)c.p.K);
-            over = cnt > (unsigned)c.p.K;
-        }
-        const float4* pl = c.planes + (size_t)v * c.p.K;
-        if (!movable) {
+__device__ __forceinline__ void finish_vertex(const DevCtx& c, int lane, int v, float4 X, float4 XP, f3 y0, f3 y,
+                                              bool halted, const float4* pl, int np, bool over, unsigned cnt,
+                                              BlockCounters& bc, float4* x_out, unsigned char* halt_out) {
+    if (STEP && !halted) y = clamp_len(y, c.p.r);
+    f3 xn = add(xyz(X), y);
+    bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
+    if (!halted && np > 0 && (changed || over)) {
+        bool f64 = false;
+        if (final_check_fails(c, pl, np, X, xn, lane, f64)) {
+            halted = true;
             y = mk(0.f, 0.f, 0.f);
-        } else if (over) {
-            // more planes than slots: bound the step by the smallest d of all planes
-            unsigned code = c.dmin_drop[v];
-            float dmin = (code == 0xFFFFFFFFu) ? 3.4e38f : ord2f(code);
-            for (int j = lane; j < np; j += 32) dmin = fminf(dmin, pl[j].w);
-            dmin = warp_min(dmin);
-            y = clamp_len(y0, fmaxf(dmin, 0.f));
-            if (lane == 0) atomicAdd(&bc.over, 1u);
-        } else if (np > 0) {
-            float mn = 3.4e38f, dabs = 0.f;
-            for (int j = lane; j < np; j += 32) {
-                float4 P = pl[j];
-                mn = fminf(mn, rho_at(y0, P));
-                dabs = fmaxf(dabs, fabsf(P.w));
-            }
-            mn = warp_min(mn);
-            dabs = warp_max(dabs);
-            if (mn < 0.f) {
-                if (lane == 0) atomicAdd(&bc.viol, 1u);
-                f3 ypass = y0;
-                bool conv = false;
-                for (int pass = 0; pass <= c.p.max_passes; ++pass) {
-                    float mnb = mn;
-                    if (pass > 0) {
-                        mnb = 3.4e38f;
-                        for (int j = lane; j < np; j += 32) mnb = fminf(mnb, rho_at(ypass, pl[j]));
-                        mnb = warp_min(mnb);
-                    }
-                    if (mnb >= 0.f) { conv = true; break; }
-                    if (pass == c.p.max_passes) break;
-                    f3 ynext;
-                    float Dmax;
-                    bool done = false;
-                    const float yb = len(ypass);
-                    float T = 2.f * (-mnb);
-                    for (int attempt = 0; attempt < 3 && !done; ++attempt) {
-                        float margin = 1e-3f * T + 64.f * U * (yb + T + dabs) + 1e-12f;
-                        T += margin;
-                        int m = 0;
-                        for (int j0 = 0; j0 < np; j0 += 32) {
-                            int j = j0 + lane;
-                            float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-                            bool take = false;
-                            if (j < np) {
-                                P = pl[j];
-                                take = rho_at(ypass, P) <= T;
-                            }
-                            unsigned bal = __ballot_sync(FULL, take);
-                            int pos = m + __popc(bal & ((1u << lane) - 1u));
-                            if (take && pos < PCAP) {
-                                buf.pl[pos] = P;
-                                buf.key[pos] = rho_at(y0, P);
-                                buf.idx[pos] = j;
-                            }
-                            m += __popc(bal);
-                        }
-                        __syncwarp();
-                        if (m > PCAP) break;
-                        if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
-                        int nvp = alg2_pass(c, lane, m,
-                                  [&](int e, float4& P, float& key, int& j) { P = buf.pl[e]; key = buf.key[e]; j = buf.idx[e]; },
-                                  ypass, ynext, Dmax);
-                        __syncwarp();
-                        if (Dmax <= T - margin) {
-                            done = true;
-                            if (lane == 0) { atomicAdd(&bc.smem_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
-                        } else {
-                            T = 2.f * Dmax;
-                        }
-                    }
-                    if (!done) {
-                        // too many candidate planes: pass over the full list in global memory
-                        int nvp = alg2_pass(c, lane, np,
-                                  [&](int e, float4& P, float& key, int& j) { P = pl[e]; key = rho_at(y0, P); j = e; },
-                                  ypass, ynext, Dmax);
-                        if (lane == 0) { atomicAdd(&bc.glob_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
-                    }
-                    ypass = ynext;
-                }
-                if (conv) y = ypass;
-                else { y = mk(0.f, 0.f, 0.f); halted = true; }
-            }
+            xn = xyz(X);
+            if (lane == 0) atomicAdd(&bc.fhalt, 1u);
         }
-        if (STEP && movable && !halted) y = clamp_len(y, c.p.r);
-        f3 xn = add(xyz(X), y);
-        // final feasibility check on the stored binary32 position: a
-        // rounding-error filter decides most planes, FP64 the rest
-        bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
-        if (movable && !halted && np > 0 && (changed || over)) {
-            f3 dl = sub(xn, xyz(X));
-            float tau = c.p.tau + 2.f * U * (fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z));
-            bool fail = false, undecided = false;
-            for (int j = lane; j < np; j += 32) {
-                float4 P = pl[j];
-                float rho = rho_at(dl, P);
-                float S = fabsf(dl.x * P.x) + fabsf(dl.y * P.y) + fabsf(dl.z * P.z) + fabsf(P.w);
-                float err = 8.f * U * S;
-                if (rho - err >= -tau) continue;
-                if (rho + err < -tau) { fail = true; continue; }
-                double rd = ((double)xn.x - X.x) * P.x + ((double)xn.y - X.y) * P.y +
-                            ((double)xn.z - X.z) * P.z + (double)P.w;
-                undecided = true;
-                if (rd < -(double)tau) fail = true;
-            }
-            unsigned und = __ballot_sync(FULL, undecided);
-            if (und && lane == 0) atomicAdd(&bc.f64, 1u);
-            if (__any_sync(FULL, fail)) {
-                halted = true;
-                y = mk(0.f, 0.f, 0.f);
-                xn = xyz(X);
-                if (lane == 0) atomicAdd(&bc.fhalt, 1u);
-            }
-        }
-        if (halted && lane == 0) atomicAdd(&bc.halt, 1u);
-        if (lane == 0 && movable && cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
-        if (lane == 0) {
-            if (STEP) {
-                f3 dd = sub(y, y0);
-                if (movable && len(dd) > 2.f * c.p.eps) c.flags[0] = 1;
-                if (movable) x_out[v] = make_float4(xn.x, xn.y, xn.z, X.w);
-            } else {
-                if (movable) x_out[v] = make_float4(xn.x, xn.y, xn.z, XP.w);
-                if (halt_out) halt_out[v] = halted ? 1 : 0;
-            }
+        if (f64 && lane == 0) atomicAdd(&bc.f64, 1u);
+    }
+    if (lane == 0) {
+        if (halted) atomicAdd(&bc.halt, 1u);
+        if (cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
+        if (STEP) {
+            if (len(sub(y, y0)) > 2.f * c.p.eps) c.flags[0] = 1;
+            x_out[v] = make_float4(xn.x, xn.y, xn.z, X.w);
+        } else {
+            x_out[v] = make_float4(xn.x, xn.y, xn.z, XP.w);
+            if (halt_out) halt_out[v] = halted ? 1 : 0;
         }
     }
+}
+
+__device__ __forceinline__ void flush_block_counters(const DevCtx& c, BlockCounters& bc) {
     __syncthreads();
     if (threadIdx.x == 0) {
         if (bc.viol) atomicAdd(&c.stats->violated_verts, (u64)bc.viol);
@@ -1094,7 +1127,195 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project(DevCtx c, const flo
         if (bc.glob_pass) atomicAdd(&c.stats->aux[1], (u64)bc.glob_pass);
         if (bc.nviol) atomicAdd(&c.stats->aux[2], (u64)bc.nviol);
         if (bc.retry) atomicAdd(&c.stats->aux[5], (u64)bc.retry);
+        if (bc.heavy_planes) atomicAdd(&c.stats->aux[6], bc.heavy_planes);
     }
+}
+
+__device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
+    if (threadIdx.x == 0) {
+        bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.smem_pass = bc.glob_pass = bc.nviol = bc.retry = 0u;
+        bc.planes = 0ull;
+        bc.heavy_planes = 0ull;
+    }
+    __syncthreads();
+}
+
+// Projection, first kernel: one warp per vertex.  Vertices whose planes all
+// hold at the candidate (rho_k(x') >= 0: Alg. 2 returns x' after its first
+// pass), vertices without planes, and overflowed vertices are finished here;
+// the others are queued for k_project_heavy.  STEP = true: x_b is the
+// collision-free iterate x_c (read and overwritten), candidates come from
+// x_in (the XPBD iterate), and the step is clamped to r.
+template <bool STEP>
+__global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, const float4* x_in, float4* x_out,
+                                                  unsigned char* halt_out) {
+    if (STEP && c.flags[1]) return;
+    __shared__ BlockCounters bc;
+    zero_block_counters(bc);
+    const int lane = threadIdx.x & 31;
+    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (v < c.n_verts) {
+        const float4 X = x_b[v];
+        const float4 XP = x_in[v];
+        if (X.w > 0.f) {
+            const f3 y0 = sub(xyz(XP), xyz(X));
+            const unsigned cnt = c.count[v];
+            const int np = (int)min(cnt, (unsigned)c.p.K);
+            const bool over = cnt > (unsigned)c.p.K;
+            const float4* pl = c.planes + (size_t)v * c.p.K;
+            f3 y = y0;
+            bool queued = false;
+            if (over) {
+                // more planes than slots: bound the step by the smallest d of all planes
+                unsigned code = c.dmin_drop[v];
+                float dmin = (code == 0xFFFFFFFFu) ? 3.4e38f : ord2f(code);
+                float mn, dabs;
+                scan_min_rho(pl, np, mk(0.f, 0.f, 0.f), lane, mn, dabs);   // rho at x is d
+                y = clamp_len(y0, fmaxf(fminf(dmin, mn), 0.f));
+                if (lane == 0) atomicAdd(&bc.over, 1u);
+            } else if (np > 0) {
+                float mn, dabs;
+                scan_min_rho(pl, np, y0, lane, mn, dabs);
+                if (mn < 0.f) {
+                    queued = true;
+                    if (lane == 0) {
+                        unsigned w = atomicAdd(c.work_count, 1u);
+                        c.work[w] = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
+                        atomicAdd(&bc.viol, 1u);
+                    }
+                }
+            }
+            if (!queued) finish_vertex<STEP>(c, lane, v, X, XP, y0, y, false, pl, np, over, cnt, bc, x_out, halt_out);
+        } else if (!STEP && lane == 0 && halt_out) {
+            halt_out[v] = 0;
+        }
+    }
+    flush_block_counters(c, bc);
+}
+
+// Projection, second kernel: the vertices with a violated plane, one warp
+// each (persistent warps over the queue).  A pass of Alg. 2 only ever acts on
+// planes violated at its current iterate.  With b the pass input and D the
+// largest distance the iterate moves from b during the pass,
+// rho_k(y) >= rho_k(b) - D for every plane, so planes with rho_k(b) > T >=
+// D + margin are never touched: the pass runs on the planes with
+// rho_k(b) <= T, sorted in shared memory, and is repeated with a larger T if
+// D turns out to exceed T - margin; the result equals a pass over the full
+// sorted list.  The last pass can only confirm convergence (any violation
+// there ends in the halt), so it is a single scan.
+template <bool STEP>
+__global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, const float4* x_b, const float4* x_in,
+                                                                    float4* x_out, unsigned char* halt_out) {
+    if (STEP && c.flags[1]) return;
+    __shared__ BlockCounters bc;
+    extern __shared__ __align__(16) unsigned char proj_smem[];
+    zero_block_counters(bc);
+    const int lane = threadIdx.x & 31;
+    SortBuf& sb = reinterpret_cast<SortBuf*>(proj_smem)[threadIdx.x >> 5];
+    const float U = 5.9604645e-8f;   // unit roundoff of binary32
+    const unsigned nwork = *c.work_count;
+    const unsigned stride = gridDim.x * PROJ_WARPS;
+    for (unsigned wi = blockIdx.x * PROJ_WARPS + (threadIdx.x >> 5); wi < nwork; wi += stride) {
+        const int4 wk = c.work[wi];
+        const int v = wk.x;
+        const float mn = __int_as_float(wk.y), dabs = __int_as_float(wk.z);
+        const float4 X = x_b[v];
+        const float4 XP = x_in[v];
+        const f3 y0 = sub(xyz(XP), xyz(X));
+        const unsigned cnt = c.count[v];
+        const int np = (int)min(cnt, (unsigned)c.p.K);
+        const float4* pl = c.planes + (size_t)v * c.p.K;
+        if (lane == 0) atomicAdd(&bc.heavy_planes, (unsigned long long)np);
+        f3 ypass = y0;
+        bool conv = false;
+        for (int pass = 0; pass <= c.p.max_passes; ++pass) {
+            float mnb = mn, dd;
+            if (pass > 0) scan_min_rho(pl, np, ypass, lane, mnb, dd);
+            if (mnb >= 0.f) { conv = true; break; }
+            if (pass == c.p.max_passes) break;
+            f3 ynext;
+            float Dmax;
+            bool done = false;
+            const float yb = len(ypass);
+            float T = 2.f * (-mnb);
+            for (int attempt = 0; attempt < 3 && !done; ++attempt) {
+                float margin = 1e-3f * T + 64.f * U * (yb + T + dabs) + 1e-12f;
+                T += margin;
+                // gather the planes with rho(ypass) <= T, keyed by rho at the first input
+                int m = 0;
+                for (int j0 = 0; j0 < np; j0 += 128) {
+                    float4 P[4];
+                    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = j0 + 32 * k + lane;
+                        P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 3.4e38f);
+                    }
+                    #pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int j = j0 + 32 * k + lane;
+                        const bool take = (j < np) && rho_at(ypass, P[k]) <= T;
+                        const unsigned bal = __ballot_sync(FULL, take);
+                        const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                        if (take && pos < SCAP) {
+                            sb.key[0][pos] = f2ord(rho_at(y0, P[k]));
+                            sb.idx[0][pos] = (unsigned short)j;
+                        }
+                        m += __popc(bal);
+                    }
+                }
+                __syncwarp();
+                if (m > SCAP || np > 65535) break;
+                if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
+                warp_radix_sort(sb, m, lane);
+                // equal keys on distinct planes: order by the plane itself (rare; one
+                // lane).  Bitwise-identical planes act identically in any order.
+                bool tie = false;
+                for (int i = lane; i + 1 < m; i += 32) {
+                    if (sb.key[0][i] == sb.key[0][i + 1]) {
+                        const float4 A = pl[sb.idx[0][i]], B = pl[sb.idx[0][i + 1]];
+                        tie |= !(A.x == B.x && A.y == B.y && A.z == B.z && A.w == B.w);
+                    }
+                }
+                if (__any_sync(FULL, tie)) {
+                    if (lane == 0) {
+                        for (int i = 1; i < m; ++i) {
+                            unsigned kk = sb.key[0][i];
+                            unsigned short jj = sb.idx[0][i];
+                            int q = i - 1;
+                            while (q >= 0 && sb.key[0][q] == kk && plane_less(pl, jj, sb.idx[0][q])) {
+                                sb.key[0][q + 1] = sb.key[0][q];
+                                sb.idx[0][q + 1] = sb.idx[0][q];
+                                --q;
+                            }
+                            sb.key[0][q + 1] = kk;
+                            sb.idx[0][q + 1] = jj;
+                        }
+                    }
+                    __syncwarp();
+                }
+                int nvp = sorted_pass(c, lane, sb, m, pl, ypass, ynext, Dmax);
+                __syncwarp();
+                if (Dmax <= T - margin) {
+                    done = true;
+                    if (lane == 0) { atomicAdd(&bc.smem_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
+                } else {
+                    T = 2.f * Dmax;
+                }
+            }
+            if (!done) {
+                // too many candidate planes: pass over the full list in global memory
+                int nvp = alg2_pass(c, lane, np,
+                                    [&](int e, float4& P, float& key, int& j) { P = pl[e]; key = rho_at(y0, P); j = e; },
+                                    ypass, ynext, Dmax);
+                if (lane == 0) { atomicAdd(&bc.glob_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
+            }
+            ypass = ynext;
+        }
+        const bool halted = !conv;
+        finish_vertex<STEP>(c, lane, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, false, cnt, bc,
+                            x_out, halt_out);
+    }
+    flush_block_counters(c, bc);
 }
 
 // ------------------------------------------------------------------ XPBD
@@ -1251,6 +1472,14 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     }
 }
 
+cudaError_t configure_kernels() {
+    cudaError_t e = cudaFuncSetAttribute(k_project_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PROJ_SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_project_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJ_SMEM);
+    return e;
+}
+
 void launch_clear_regions(const DevCtx& c, cudaStream_t st) {
     cudaMemsetAsync(c.count, 0, (size_t)c.n_verts * sizeof(unsigned), st);
     cudaMemsetAsync(c.dmin_drop, 0xFF, (size_t)c.n_verts * sizeof(unsigned), st);
@@ -1258,7 +1487,11 @@ void launch_clear_regions(const DevCtx& c, cudaStream_t st) {
 
 void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st) {
     long threads = (long)c.n_verts * 32;
-    if (threads > 0) k_project<false><<<nblk(threads, PROJ_WARPS * 32), PROJ_WARPS * 32, 0, st>>>(c, xb, xio, xio, halt);
+    cudaMemsetAsync(c.work_count, 0, sizeof(unsigned), st);
+    if (threads > 0) {
+        k_project<false><<<nblk(threads, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
+        k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
+    }
 }
 
 void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st) {
@@ -1277,8 +1510,11 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
     }
     if (tm) tm->mark(ST_XPBD, st);
     long threads = (long)c.n_verts * 32;
-    if (threads > 0) k_project<true><<<nblk(threads, PROJ_WARPS * 32), PROJ_WARPS * 32, 0, st>>>(c, x, c.x_s, x, nullptr);
+    cudaMemsetAsync(c.work_count, 0, sizeof(unsigned), st);
+    if (threads > 0) k_project<true><<<nblk(threads, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
+    if (threads > 0) k_project_heavy<true><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
+    if (tm) tm->mark(ST_PROJECT_HEAVY, st);
     k_iter_end<<<1, 1, 0, st>>>(c, early_exit);
 }
 
