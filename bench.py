@@ -149,6 +149,7 @@ def main():
     ap.add_argument("--workload", default="cloth_stack", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     builder, desc = WORKLOADS[args.workload]
@@ -178,7 +179,7 @@ def main():
     torch.cuda.synchronize()
     ctx.reset_stats()
 
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 and not args.no_clocks else None
     if sampler:
         sampler.start()
         # wait for nvidia-smi to deliver its first sample so that its start-up
@@ -190,13 +191,14 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
         ctx.step(x, v)
-    e1.record(stream)
+        evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    e0, e1 = evs[0], evs[-1]
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
@@ -297,6 +299,7 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "step_ms": [round(t, 3) for t in step_ms],
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "verts": N, "movable": sc.n_movable,
                        "edges": E, "tris": T, "iters_per_step": iters, "iters_run_per_step": iters_run,
