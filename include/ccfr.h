@@ -190,6 +190,33 @@ ccfr_status ccfr_copy_regions(ccfr_ctx* ctx, float* planes, unsigned long long* 
  * Used to feed externally built regions to ccfr_project. */
 ccfr_status ccfr_load_regions(ccfr_ctx* ctx, const float* planes, const int* count, int capacity, void* stream);
 
+/* Projection that allocates nothing, for callers that cannot allocate device
+ * memory: a caller whose memory is fully owned by another allocator or
+ * budget (a host engine or plug-in that hands this library fixed buffers),
+ * or a caller on a path where cudaMalloc is not permitted.  (The paper has no
+ * counterpart; this is an interface of this library.)
+ *
+ * Same computation as ccfr_project (Alg. 2 with Alg. 1, retraction, halt,
+ * final check) on regions the caller holds, in the layout of
+ * ccfr_copy_regions: planes (device, n_verts * capacity float4, vertex-major),
+ * count (device, n_verts ints), dmin_drop (device, n_verts floats, +inf =
+ * none; or NULL when no vertex has more than `capacity` planes).  x: device,
+ * build positions; x_io: device, candidates in, projected positions out;
+ * halt_out: optional device bytes.  params: r, eps_retract, eps_dep, tau_feas
+ * and max_passes are used.
+ *
+ * Scratch: a file-scope device array sized for n_verts <= 262,144 (about
+ * 5 MB on every GPU that loads the library, held until the process exits).
+ * Larger n_verts is rejected with CCFR_ERR_INVALID_ARG.  The first call on a
+ * device, with that device current, looks up the array's device address and
+ * sets the kernels' shared-memory limit; make that first call before any
+ * stream capture.  Every call shares the one array and clears what must start
+ * at zero, so calls that overlap on the GPU (other streams, other threads)
+ * race: serialise them.  No call allocates or frees device memory. */
+ccfr_status ccfr_project_static(const float* x, float* x_io, const float* planes, const int* count,
+                                const float* dmin_drop, int n_verts, int capacity, const ccfr_params* params,
+                                unsigned char* halt_out, void* stream);
+
 /* Context geometry: n_verts, plane capacity, number of edge colours. */
 ccfr_status ccfr_get_info(const ccfr_ctx* ctx, int* n_verts, int* capacity, int* n_colors);
 

@@ -81,6 +81,7 @@ def lib():
             "ccfr_get_info": [P, P, P, P],
             "ccfr_get_stats": [P, C.POINTER(Stats)],
             "ccfr_reset_stats": [P, P],
+            "ccfr_project_static": [P, P, P, P, P, C.c_int, C.c_int, C.POINTER(Params), P, P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -97,7 +98,8 @@ def lib():
 def exported_symbols() -> list[str]:
     return ["ccfr_create", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
             "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
-            "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string"]
+            "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
+            "ccfr_project_static"]
 
 
 def _check(rc: int, what: str):
@@ -132,6 +134,16 @@ def _stream(stream):
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def project_static(x, x_io, planes, count, params: Params, dmin_drop=None, halt=None, stream=None):
+    """ccfr_project_static: the projection on caller-held regions, for callers
+    that cannot allocate device memory (all scratch is a fixed device array
+    inside the library; at most 262,144 vertices; overlapping calls race)."""
+    n = int(count.shape[0])
+    cap = int(planes.shape[1])
+    _check(lib().ccfr_project_static(_ptr(x), _ptr(x_io), _ptr(planes), _ptr(count), _ptr(dmin_drop), n, cap,
+                                     C.byref(params), _ptr(halt), _stream(stream)), "ccfr_project_static")
 
 
 class Context:

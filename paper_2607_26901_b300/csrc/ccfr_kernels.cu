@@ -1537,3 +1537,124 @@ void launch_dmin_export(const DevCtx& c, float* out, cudaStream_t st) {
 }
 
 }  // namespace ccfr
+
+// ------------------------------------------------ projection without allocation
+//
+// ccfr_project_static runs the projection (k_project + k_project_heavy) on
+// regions the caller already holds, for callers that cannot allocate device
+// memory at all.  Its scratch (queue of violated vertices, overflow codes,
+// counters) is the file-scope array below: every GPU that loads the library
+// holds it until the process exits, and every call shares it.
+
+#include <cstddef>
+#include <mutex>
+
+#include "ccfr.h"
+
+namespace ccfr {
+
+constexpr int STATIC_MAX_VERTS = 1 << 18;   // 262,144 vertices
+
+struct StaticScratch {
+    DevStats stats;
+    int flags[2];
+    unsigned work_count;
+    unsigned pad_[13];
+    int4 work[STATIC_MAX_VERTS];
+    unsigned dmin[STATIC_MAX_VERTS];
+};
+
+static __device__ __align__(256) StaticScratch g_static_scratch;
+
+// Overflow codes for the projection: the caller's smallest dropped d (float,
+// +inf = none) in the order-preserving encoding the kernels read.
+__global__ void k_static_dmin(const float* dmin_drop, unsigned* out, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float d = dmin_drop ? dmin_drop[i] : __int_as_float(0x7f800000);
+    out[i] = (d == __int_as_float(0x7f800000)) ? 0xFFFFFFFFu : f2ord(d);
+}
+
+namespace {
+
+struct StaticSetup {
+    StaticScratch* ptr = nullptr;
+    int n_sm = 0;
+    bool ready = false;
+};
+constexpr int MAX_DEVICES = 64;
+StaticSetup g_setup[MAX_DEVICES];
+std::mutex g_setup_mutex;
+
+// Once per device, with that device current: the device address of the
+// scratch array (its host-side name is only a stand-in) and the kernels'
+// shared-memory limit.
+ccfr_status static_setup(int dev, StaticSetup** out) {
+    if (dev < 0 || dev >= MAX_DEVICES) return CCFR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    StaticSetup& s = g_setup[dev];
+    if (!s.ready) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return CCFR_ERR_CUDA;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) return CCFR_ERR_CUDA;
+        if (configure_kernels() != cudaSuccess) return CCFR_ERR_CUDA;
+        s.ptr = (StaticScratch*)p;
+        s.n_sm = nsm;
+        s.ready = true;
+    }
+    *out = &s;
+    return CCFR_OK;
+}
+
+}  // namespace
+}  // namespace ccfr
+
+extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const float* planes, const int* count,
+                                          const float* dmin_drop, int n_verts, int capacity,
+                                          const ccfr_params* params, unsigned char* halt_out, void* stream) {
+    using namespace ccfr;
+    if (!x || !x_io || !params || n_verts < 0 || capacity < 1 || capacity > 65535) return CCFR_ERR_INVALID_ARG;
+    if (n_verts > STATIC_MAX_VERTS) return CCFR_ERR_INVALID_ARG;     // beyond the scratch array
+    if (n_verts > 0 && (!planes || !count)) return CCFR_ERR_INVALID_ARG;
+    if (((uintptr_t)x & 15u) || ((uintptr_t)x_io & 15u) || ((uintptr_t)planes & 15u)) return CCFR_ERR_INVALID_ARG;
+    if (!(params->eps_retract >= 0.f) || !(params->eps_dep > 0.f) || !(params->tau_feas >= 0.f) ||
+        params->max_passes < 0 || params->max_passes > 64 || !(params->r > 0.f))
+        return CCFR_ERR_INVALID_ARG;
+    if (n_verts == 0) return CCFR_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CCFR_ERR_CUDA;
+    StaticSetup* su = nullptr;
+    ccfr_status st = static_setup(dev, &su);
+    if (st != CCFR_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    StaticScratch* sc = su->ptr;
+    // what must start at zero: the queue length, the flags and the counters
+    cudaError_t e = cudaMemsetAsync(sc, 0, offsetof(StaticScratch, work), s);
+    if (e != cudaSuccess) return CCFR_ERR_CUDA;
+    DevCtx c{};
+    c.p.r = params->r;
+    c.p.two_r = 2.f * params->r;
+    c.p.xi = params->xi;
+    c.p.pad = params->pad;
+    c.p.eps = params->eps_retract;
+    c.p.eps_dep = params->eps_dep;
+    c.p.tau = params->tau_feas;
+    c.p.max_passes = params->max_passes;
+    c.p.K = capacity;
+    c.n_verts = n_verts;
+    c.planes = const_cast<float4*>((const float4*)planes);
+    c.count = const_cast<unsigned*>((const unsigned*)count);
+    c.dmin_drop = sc->dmin;
+    c.flags = sc->flags;
+    c.stats = &sc->stats;
+    c.work = sc->work;
+    c.work_count = &sc->work_count;
+    c.n_sm = su->n_sm;
+    k_static_dmin<<<nblk(n_verts, 256), 256, 0, s>>>(dmin_drop, sc->dmin, n_verts);
+    long threads = (long)n_verts * 32;
+    k_project<false><<<nblk(threads, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
+    k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
+                                                                         (float4*)x_io, halt_out);
+    return (cudaGetLastError() == cudaSuccess) ? CCFR_OK : CCFR_ERR_CUDA;
+}
