@@ -41,6 +41,8 @@ WORKLOADS = {
                         "profiling case of the stack recipe: 4 layers of 128x128 cloth (65,536 verts)"),
     "cloth_on_sphere": (lambda seed: S.cloth_on_sphere(seed=seed),
                         "32x32 cloth (1,024 verts) on a static 4,000-tri sphere, 10 iterations"),
+    "batch": (None, "512 independent scenes, sizes lognormal(ln 8192, ln 2) in [1k, 64k] verts: 80% cloths "
+                    "on static spheres (r=5 mm, xi=1 mm), 20% particle clouds (r=1 mm, xi=2 mm); 10 iterations"),
     "wires": (lambda seed: S.wires(seed=seed),
               "16,384 helical strands x 64 segments (1,064,960 verts) over a static grate, 10 iterations"),
 }
@@ -156,6 +158,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, ws, rank, desc)
+        return
+    if args.workload == "batch":
+        run_batch(args, ws, rank, local, desc)
         return
 
     import torch
@@ -328,6 +333,81 @@ def main():
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_batch(args, ws, rank, local, desc):
+    """Batched step: all scenes in one context (one graph-captured launch
+    sequence per substep), after the autotuner; compared with the same scenes
+    stepped one context at a time on the same GPU and stream."""
+    import numpy as np
+    import torch
+    from paper_2607_26901_b300 import ccfr
+
+    torch.cuda.set_device(local)
+    scenes = S.batch(seed=4 + rank)
+    x = torch.as_tensor(np.concatenate([sc.x for sc in scenes])).cuda().contiguous()
+    v = torch.as_tensor(np.concatenate([sc.v for sc in scenes])).cuda().contiguous()
+    movable = sum(sc.n_movable for sc in scenes)
+    ctx = ccfr.Context.from_scenes(scenes)
+    t0 = time.perf_counter()
+    tuning, tuned_ms = ctx.autotune(x, v, steps=1)
+    tune_s = time.perf_counter() - t0
+    for _ in range(max(args.warmup, 0)):
+        ctx.step(x, v)
+    torch.cuda.synchronize()
+    ctx.reset_stats()
+    stream = torch.cuda.current_stream()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
+        ctx.step(x, v)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    ms = evs[0].elapsed_time(evs[-1])
+    st = ctx.stats()
+    value = movable * st["iterations"] / (ms / 1e3)
+    ctx.close()
+    # plain: one context per scene, stepped one after another on the same stream
+    ctxs, xs, vs = [], [], []
+    for sc in scenes:
+        c1 = ccfr.Context.from_scene(sc)
+        c1.set_tuning(cell_factor=tuning["cell_factor"], emit_blocks_per_sm=tuning["emit_blocks_per_sm"],
+                      plane_capacity=tuning["plane_capacity"])
+        ctxs.append(c1)
+        xs.append(torch.as_tensor(sc.x).cuda().contiguous())
+        vs.append(torch.as_tensor(sc.v).cuda().contiguous())
+    for _ in range(max(args.warmup, 0)):
+        for c1, xx, vv in zip(ctxs, xs, vs):
+            c1.step(xx, vv)
+    torch.cuda.synchronize()
+    pl_steps = max(1, min(args.steps, 3))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(pl_steps):
+        for c1, xx, vv in zip(ctxs, xs, vs):
+            c1.step(xx, vv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    pms = e0.elapsed_time(e1)
+    iters = scenes[0].params["iters"]
+    plain_value = movable * iters * pl_steps / (pms / 1e3)
+    for c1 in ctxs:
+        c1.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value * ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batch", "description": desc, "scenes": len(scenes), "verts": int(x.shape[0]),
+                       "movable": movable, "tuning": tuning, "autotune_s": round(tune_s, 2),
+                       "autotune_best_ms": round(tuned_ms, 3)},
+            "plain_per_scene": {"value": plain_value, "unit": UNIT, "ms_per_step": pms / pl_steps,
+                                "launch": "512 contexts, one ccfr_step each, one stream"},
+            "batched_over_plain": value / plain_value,
+            "stats_per_iter": {k: st[k] / max(st["iterations"], 1) for k in ("planes", "halts", "violated_verts",
+                                                                            "overflow_verts")},
+        }), flush=True)
 
 
 def run_reference(args, ws, rank, desc):

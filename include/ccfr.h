@@ -217,6 +217,39 @@ ccfr_status ccfr_project_static(const float* x, float* x_io, const float* planes
                                 const float* dmin_drop, int n_verts, int capacity, const ccfr_params* params,
                                 unsigned char* halt_out, void* stream);
 
+/* A context for several independent scenes stepped together (batched step).
+ * meshes[k] / params[k] describe scene k with scene-local vertex ids; the
+ * context numbers the vertices of scene k after those of scenes 0..k-1, so x
+ * and v passed to ccfr_step hold all scenes one after another.  rest_x is
+ * required for every scene.  Pairs never cross scenes; r, xi, delta and pad
+ * are per scene, everything else (dt, gravity, iterations, projection
+ * settings, capacity, flags) must be equal across scenes.  At most 2048
+ * scenes.  Each scene's result equals its result in a context of its own. */
+ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params, int n_scenes, void* stream,
+                              ccfr_ctx** out);
+
+/* Performance knobs (no effect on results): grid cell size in mean padded
+ * primitive extents, emission blocks per SM, and plane capacity (a multiple
+ * of 32; changing it reallocates the plane lists).  0 keeps a setting. */
+typedef struct {
+    float cell_factor;
+    int emit_blocks_per_sm;
+    int plane_capacity;
+} ccfr_tuning;
+
+/* Apply tuning (synchronises the device; drops recorded step graphs). */
+ccfr_status ccfr_set_tuning(ccfr_ctx* ctx, const ccfr_tuning* t);
+ccfr_status ccfr_get_tuning(const ccfr_ctx* ctx, ccfr_tuning* t);
+
+/* Autotuner: sets the plane capacity to 1.5x the largest per-vertex plane
+ * count at x (+32), then times `steps` substeps from a scratch copy of
+ * (x, v) for every cell factor in {1, 1.5, 2, 3} and emission grid in {4, 8,
+ * 16} blocks per SM, and keeps the fastest.  x, v (device) are not modified.
+ * Allocates two scratch vectors for the duration of the call.  best receives
+ * the chosen tuning, best_ms (optional) its time per substep. */
+ccfr_status ccfr_autotune(ccfr_ctx* ctx, const float* x, const float* v, int steps, ccfr_tuning* best,
+                          double* best_ms, void* stream);
+
 /* Context geometry: n_verts, plane capacity, number of edge colours. */
 ccfr_status ccfr_get_info(const ccfr_ctx* ctx, int* n_verts, int* capacity, int* n_colors);
 

@@ -56,6 +56,13 @@ class Stats(C.Structure):
         return {k: (v if k == "aux" else int(v)) for k, v in d.items()}
 
 
+class Tuning(C.Structure):
+    _fields_ = [("cell_factor", C.c_float), ("emit_blocks_per_sm", C.c_int), ("plane_capacity", C.c_int)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -82,6 +89,10 @@ def lib():
             "ccfr_get_stats": [P, C.POINTER(Stats)],
             "ccfr_reset_stats": [P, P],
             "ccfr_project_static": [P, P, P, P, P, C.c_int, C.c_int, C.POINTER(Params), P, P],
+            "ccfr_create_batch": [C.POINTER(Mesh), C.POINTER(Params), C.c_int, P, C.POINTER(P)],
+            "ccfr_set_tuning": [P, C.POINTER(Tuning)],
+            "ccfr_get_tuning": [P, C.POINTER(Tuning)],
+            "ccfr_autotune": [P, P, P, C.c_int, C.POINTER(Tuning), C.POINTER(C.c_double), P],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -99,7 +110,7 @@ def exported_symbols() -> list[str]:
     return ["ccfr_create", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
             "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
             "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
-            "ccfr_project_static"]
+            "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune"]
 
 
 def _check(rc: int, what: str):
@@ -177,6 +188,56 @@ class Context:
                    cell_size: float = 0.0, cell_factor: float = 0.0, stream=None):
         p = make_params(scene.params, flags, plane_capacity, iters, cell_size, cell_factor)
         return cls(scene.edges, scene.tris, scene.n_verts, p, rest_x=scene.x, stream=stream)
+
+    @classmethod
+    def from_scenes(cls, scenes, flags: int = 0, plane_capacity: int | None = None, stream=None):
+        """One context for several independent scenes (ccfr_create_batch).
+        Vertices are numbered scene after scene; see `offsets`."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = len(scenes)
+        meshes = (Mesh * n)()
+        params = (Params * n)()
+        keep = []
+        for k, sc in enumerate(scenes):
+            e = torch.as_tensor(np.asarray(sc.edges, np.int32).reshape(-1, 2)).to(dev).contiguous()
+            t = torch.as_tensor(np.asarray(sc.tris, np.int32).reshape(-1, 3)).to(dev).contiguous()
+            r = torch.as_tensor(np.asarray(sc.x, np.float32)).to(dev).contiguous()
+            keep += [e, t, r]
+            meshes[k] = Mesh(sc.n_verts, int(e.shape[0]), int(t.shape[0]), e.data_ptr() if e.numel() else None,
+                             t.data_ptr() if t.numel() else None, r.data_ptr())
+            params[k] = make_params(sc.params, flags, plane_capacity)
+        h = C.c_void_p()
+        _check(lib().ccfr_create_batch(meshes, params, n, _stream(stream), C.byref(h)), "ccfr_create_batch")
+        self.h = h
+        self.params = params[0]
+        self.offsets = np.concatenate([[0], np.cumsum([sc.n_verts for sc in scenes])]).astype(np.int64)
+        self.n_verts = int(self.offsets[-1])
+        nv, cap, ncol = C.c_int(), C.c_int(), C.c_int()
+        _check(lib().ccfr_get_info(h, C.byref(nv), C.byref(cap), C.byref(ncol)), "ccfr_get_info")
+        self.capacity = cap.value
+        self.n_colors = ncol.value
+        return self
+
+    def set_tuning(self, cell_factor: float = 0.0, emit_blocks_per_sm: int = 0, plane_capacity: int = 0):
+        t = Tuning(cell_factor, emit_blocks_per_sm, plane_capacity)
+        _check(lib().ccfr_set_tuning(self.h, C.byref(t)), "ccfr_set_tuning")
+        self.capacity = self.tuning()["plane_capacity"]
+
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().ccfr_get_tuning(self.h, C.byref(t)), "ccfr_get_tuning")
+        return t.as_dict()
+
+    def autotune(self, x, v, steps: int = 1, stream=None) -> tuple[dict, float]:
+        t = Tuning()
+        ms = C.c_double()
+        _check(lib().ccfr_autotune(self.h, _ptr(x), _ptr(v), steps, C.byref(t), C.byref(ms), _stream(stream)),
+               "ccfr_autotune")
+        self.capacity = t.plane_capacity
+        return t.as_dict(), ms.value
 
     def close(self):
         if getattr(self, "h", None):

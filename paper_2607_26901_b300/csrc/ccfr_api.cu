@@ -37,6 +37,7 @@ struct ccfr_ctx {
     float4* hv = nullptr;
     unsigned long long* pair_count = nullptr;
     std::vector<void*> allocs;
+    int n_scenes = 1;
 };
 
 namespace {
@@ -124,35 +125,14 @@ const char* ccfr_status_string(ccfr_status s) {
     return "unknown status";
 }
 
-ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
-    if (!out) return CCFR_ERR_INVALID_ARG;
-    *out = nullptr;
-    if (!mesh || check_params(params) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
-    const int N = mesh->n_verts, E = mesh->n_edges, T = mesh->n_tris;
-    if (N < 0 || E < 0 || T < 0 || N > (1 << 30) || E > (1 << 30) || T > (1 << 30)) return CCFR_ERR_INVALID_ARG;
-    if ((E > 0 && !mesh->edges) || (T > 0 && !mesh->tris)) return CCFR_ERR_INVALID_ARG;
-    if (mesh->rest_x && !aligned16(mesh->rest_x)) return CCFR_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-
-    // topology to the host: validation, isolated points, edge colours
-    std::vector<int> he(2 * (size_t)E), ht(3 * (size_t)T);
-    if (E && cudaMemcpy(he.data(), mesh->edges, he.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
-        return CCFR_ERR_CUDA;
-    if (T && cudaMemcpy(ht.data(), mesh->tris, ht.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
-        return CCFR_ERR_CUDA;
-    for (int e = 0; e < E; ++e) {
-        int a = he[2 * e], b = he[2 * e + 1];
-        if (a < 0 || b >= N || a >= b) return CCFR_ERR_INVALID_ARG;
-        if (e > 0) {
-            int pa = he[2 * e - 2], pb = he[2 * e - 1];
-            if (!(pa < a || (pa == a && pb < b))) return CCFR_ERR_INVALID_ARG;
-        }
-    }
-    for (int t = 0; t < T; ++t) {
-        int a = ht[3 * t], b = ht[3 * t + 1], d = ht[3 * t + 2];
-        if (a < 0 || b < 0 || d < 0 || a >= N || b >= N || d >= N || a == b || b == d || a == d)
-            return CCFR_ERR_INVALID_ARG;
-    }
+// Build a context from host topology (validated, vertex ids in [0, N)).
+// vscene / sparams: the scene of every vertex and each scene's (r, 2r, xi,
+// pad), or empty for a single scene.
+static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int>& ht, int N,
+                               const ccfr_params* params, const float* rest_x,
+                               const std::vector<unsigned short>& vscene, const std::vector<float4>& sparams,
+                               cudaStream_t st, ccfr_ctx** out) {
+    const int E = (int)(he.size() / 2), T = (int)(ht.size() / 3);
     std::vector<char> used(N > 0 ? N : 1, 0);
     for (int e = 0; e < E; ++e) { used[he[2 * e]] = 1; used[he[2 * e + 1]] = 1; }
     std::vector<int> pts;
@@ -221,7 +201,7 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     int btot = 0;
     for (int k = 0; k < 5; ++k) {
         // the oversized-edge table is sized for a quarter of the edges (load factor <= 8 if all are oversized)
-        int want = (k == KIND_BIGE) ? nk[k] / 4 : 2 * nk[k];
+        int want = (k == KIND_BIGE) ? nk[k] / 4 : nk[k];
         unsigned M = next_pow2((unsigned)(want > 64 ? want : 64));
         d.bucket_base[k] = btot;
         d.bucket_mask[k] = (int)(M - 1);
@@ -233,6 +213,7 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     d.n_kind[1] = E;
     d.n_kind[2] = d.n_pts;
     d.cell_factor = params->cell_factor > 0.f ? params->cell_factor : 1.5f;
+    d.emit_bps = 8;
     d.big_base[0] = 0;
     d.big_base[1] = T;
     d.unit_base[0] = 0;
@@ -246,7 +227,7 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
         d.n_sm = nsm;
     }
     const int SCAN_TILE = 4096;
-    if ((btot + 1 + SCAN_TILE - 1) / SCAN_TILE > SCAN_TILE) { free_ctx(c); return CCFR_ERR_INVALID_ARG; }
+    const int n_tiles = (btot + 1 + SCAN_TILE - 1) / SCAN_TILE;
 
     size_t NK = (size_t)N * params->plane_capacity;
     bool ok = true;
@@ -281,13 +262,22 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     ok &= dalloc(c, &d.work_count, 1) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
-    ok &= dalloc(c, &c->tile_sums, SCAN_TILE) == cudaSuccess;
+    ok &= dalloc(c, &c->tile_sums, (size_t)n_tiles) == cudaSuccess;
     ok &= dalloc(c, &d.flags, 2) == cudaSuccess;
     ok &= dalloc(c, &d.stats, 1) == cudaSuccess;
     ok &= dalloc(c, &c->pair_count, 3) == cudaSuccess;
     ok &= dalloc(c, &c->hx, N) == cudaSuccess;
     ok &= dalloc(c, &c->hv, N) == cudaSuccess;
+    unsigned short* dscene = nullptr;
+    float4* dsp = nullptr;
+    if (!vscene.empty()) {
+        ok &= dalloc(c, &dscene, vscene.size()) == cudaSuccess;
+        ok &= dalloc(c, &dsp, sparams.size()) == cudaSuccess;
+    }
     if (!ok) { cudaGetLastError(); free_ctx(c); return CCFR_ERR_OOM; }
+    d.vscene = dscene;
+    d.sparams = dsp;
+    c->n_scenes = vscene.empty() ? 1 : (int)sparams.size();
     d.edges = edges;
     d.edges_col = edges_col;
     d.rest_col = rest;
@@ -302,12 +292,17 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     if (err == cudaSuccess && T) err = cudaMemcpyAsync(tris, ht.data(), ht.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess && !pts.empty())
         err = cudaMemcpyAsync(dpts, pts.data(), pts.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess && dscene) {
+        err = cudaMemcpyAsync(dscene, vscene.data(), vscene.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess)
+            err = cudaMemcpyAsync(dsp, sparams.data(), sparams.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+    }
     if (err == cudaSuccess) err = cudaMemsetAsync(d.flags, 0, 2 * sizeof(int), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.stats, 0, sizeof(DevStats), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.count, 0, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.dmin_drop, 0xFF, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
     if (err == cudaSuccess && E) {
-        if (mesh->rest_x) launch_rest_lengths(edges_col, (const float4*)mesh->rest_x, rest, E, st);
+        if (rest_x) launch_rest_lengths(edges_col, (const float4*)rest_x, rest, E, st);
         else c->rest_pending = true;
         err = cudaGetLastError();
     }
@@ -317,6 +312,122 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
     if (err != cudaSuccess) { free_ctx(c); return CCFR_ERR_CUDA; }
     *out = c;
     return CCFR_OK;
+}
+
+ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
+    if (!out) return CCFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || check_params(params) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
+    const int N = mesh->n_verts, E = mesh->n_edges, T = mesh->n_tris;
+    if (N < 0 || E < 0 || T < 0 || N > (1 << 30) || E > (1 << 30) || T > (1 << 30)) return CCFR_ERR_INVALID_ARG;
+    if ((E > 0 && !mesh->edges) || (T > 0 && !mesh->tris)) return CCFR_ERR_INVALID_ARG;
+    if (mesh->rest_x && !aligned16(mesh->rest_x)) return CCFR_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // topology to the host: validation, isolated points, edge colours
+    std::vector<int> he(2 * (size_t)E), ht(3 * (size_t)T);
+    if (E && cudaMemcpy(he.data(), mesh->edges, he.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+        return CCFR_ERR_CUDA;
+    if (T && cudaMemcpy(ht.data(), mesh->tris, ht.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+        return CCFR_ERR_CUDA;
+    for (int e = 0; e < E; ++e) {
+        int a = he[2 * e], b = he[2 * e + 1];
+        if (a < 0 || b >= N || a >= b) return CCFR_ERR_INVALID_ARG;
+        if (e > 0) {
+            int pa = he[2 * e - 2], pb = he[2 * e - 1];
+            if (!(pa < a || (pa == a && pb < b))) return CCFR_ERR_INVALID_ARG;
+        }
+    }
+    for (int t = 0; t < T; ++t) {
+        int a = ht[3 * t], b = ht[3 * t + 1], d = ht[3 * t + 2];
+        if (a < 0 || b < 0 || d < 0 || a >= N || b >= N || d >= N || a == b || b == d || a == d)
+            return CCFR_ERR_INVALID_ARG;
+    }
+    return create_impl(he, ht, N, params, mesh->rest_x, {}, {}, st, out);
+}
+
+ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params, int n_scenes, void* stream,
+                              ccfr_ctx** out) {
+    if (!out) return CCFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!meshes || !params || n_scenes < 1 || n_scenes > 2048) return CCFR_ERR_INVALID_ARG;
+    for (int k = 0; k < n_scenes; ++k) {
+        if (check_params(&params[k]) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
+        // what the scenes share: the time step, the loop and the projection settings
+        if (params[k].dt != params[0].dt || params[k].solver_iters != params[0].solver_iters ||
+            params[k].max_passes != params[0].max_passes || params[k].plane_capacity != params[0].plane_capacity ||
+            params[k].eps_retract != params[0].eps_retract || params[k].eps_dep != params[0].eps_dep ||
+            params[k].tau_feas != params[0].tau_feas || params[k].compliance != params[0].compliance ||
+            params[k].gravity[0] != params[0].gravity[0] || params[k].gravity[1] != params[0].gravity[1] ||
+            params[k].gravity[2] != params[0].gravity[2] || params[k].flags != params[0].flags)
+            return CCFR_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    long NL = 0, EL = 0, TL = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        const ccfr_mesh& m = meshes[k];
+        if (m.n_verts < 0 || m.n_edges < 0 || m.n_tris < 0) return CCFR_ERR_INVALID_ARG;
+        if ((m.n_edges > 0 && !m.edges) || (m.n_tris > 0 && !m.tris) || !m.rest_x || !aligned16(m.rest_x))
+            return CCFR_ERR_INVALID_ARG;
+        NL += m.n_verts; EL += m.n_edges; TL += m.n_tris;
+    }
+    if (NL > (1 << 30) || EL > (1 << 30) || TL > (1 << 30)) return CCFR_ERR_INVALID_ARG;
+    const int N = (int)NL;
+    std::vector<int> he(2 * (size_t)EL), ht(3 * (size_t)TL);
+    std::vector<unsigned short> vscene((size_t)N);
+    std::vector<float4> sparams((size_t)n_scenes);
+    size_t eo = 0, to = 0;
+    int vo = 0;
+    for (int k = 0; k < n_scenes; ++k) {
+        const ccfr_mesh& m = meshes[k];
+        std::vector<int> le(2 * (size_t)m.n_edges), lt(3 * (size_t)m.n_tris);
+        if (m.n_edges && cudaMemcpy(le.data(), m.edges, le.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+            return CCFR_ERR_CUDA;
+        if (m.n_tris && cudaMemcpy(lt.data(), m.tris, lt.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+            return CCFR_ERR_CUDA;
+        for (int e = 0; e < m.n_edges; ++e) {
+            int a = le[2 * e], b = le[2 * e + 1];
+            if (a < 0 || b >= m.n_verts || a >= b) return CCFR_ERR_INVALID_ARG;
+            if (e > 0 && !(le[2 * e - 2] < a || (le[2 * e - 2] == a && le[2 * e - 1] < b))) return CCFR_ERR_INVALID_ARG;
+            he[eo + 2 * e] = a + vo;
+            he[eo + 2 * e + 1] = b + vo;
+        }
+        for (int t = 0; t < m.n_tris; ++t) {
+            int a = lt[3 * t], b = lt[3 * t + 1], d = lt[3 * t + 2];
+            if (a < 0 || b < 0 || d < 0 || a >= m.n_verts || b >= m.n_verts || d >= m.n_verts || a == b || b == d ||
+                a == d)
+                return CCFR_ERR_INVALID_ARG;
+            ht[to + 3 * t] = a + vo;
+            ht[to + 3 * t + 1] = b + vo;
+            ht[to + 3 * t + 2] = d + vo;
+        }
+        for (int i = 0; i < m.n_verts; ++i) vscene[vo + i] = (unsigned short)k;
+        sparams[k] = make_float4(params[k].r, 2.f * params[k].r, params[k].xi, params[k].pad);
+        eo += 2 * (size_t)m.n_edges;
+        to += 3 * (size_t)m.n_tris;
+        vo += m.n_verts;
+    }
+    // rest shapes side by side in one device buffer (read once for the rest lengths)
+    float4* rest = nullptr;
+    if (cudaMalloc((void**)&rest, (size_t)(N > 0 ? N : 1) * sizeof(float4)) != cudaSuccess) {
+        cudaGetLastError();
+        return CCFR_ERR_OOM;
+    }
+    vo = 0;
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < n_scenes && err == cudaSuccess; ++k) {
+        if (meshes[k].n_verts)
+            err = cudaMemcpyAsync(rest + vo, meshes[k].rest_x, (size_t)meshes[k].n_verts * sizeof(float4),
+                                  cudaMemcpyDefault, st);
+        vo += meshes[k].n_verts;
+    }
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    ccfr_status s = (err == cudaSuccess)
+                        ? create_impl(he, ht, N, &params[0], (const float*)rest, vscene, sparams, st, out)
+                        : CCFR_ERR_CUDA;
+    cudaStreamSynchronize(st);
+    cudaFree(rest);
+    return s;
 }
 
 ccfr_status ccfr_destroy(ccfr_ctx* c) {
@@ -486,6 +597,125 @@ ccfr_status ccfr_get_info(const ccfr_ctx* c, int* n_verts, int* capacity, int* n
     if (n_verts) *n_verts = c->dc.n_verts;
     if (capacity) *capacity = c->dc.p.K;
     if (n_colors) *n_colors = c->n_colors;
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_set_tuning(ccfr_ctx* c, const ccfr_tuning* t) {
+    if (!c || !t) return CCFR_ERR_INVALID_ARG;
+    if (!(t->cell_factor >= 0.f) || t->cell_factor > 64.f || t->emit_blocks_per_sm < 0 || t->emit_blocks_per_sm > 64)
+        return CCFR_ERR_INVALID_ARG;
+    if (t->plane_capacity != 0 && (t->plane_capacity < 32 || t->plane_capacity % 32 || t->plane_capacity > 65536))
+        return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) return CCFR_ERR_CUDA;
+    if (t->plane_capacity && t->plane_capacity != c->dc.p.K) {
+        // the only call besides ccfr_create that allocates: new plane lists
+        size_t NK = (size_t)c->dc.n_verts * t->plane_capacity;
+        float4* planes = nullptr;
+        unsigned long long* keys = nullptr;
+        if (cudaMalloc((void**)&planes, (NK ? NK : 1) * sizeof(float4)) != cudaSuccess) {
+            cudaGetLastError();
+            return CCFR_ERR_OOM;
+        }
+        if (c->dc.keys && cudaMalloc((void**)&keys, (NK ? NK : 1) * sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(planes);
+            return CCFR_ERR_OOM;
+        }
+        for (auto& p : c->allocs) {
+            if (p == (void*)c->dc.planes) { cudaFree(p); p = planes; }
+            else if (c->dc.keys && p == (void*)c->dc.keys) { cudaFree(p); p = keys; }
+        }
+        c->dc.planes = planes;
+        if (c->dc.keys) c->dc.keys = keys;
+        c->dc.p.K = t->plane_capacity;
+        c->prm.plane_capacity = t->plane_capacity;
+        c->regions_valid = false;
+    }
+    if (t->cell_factor > 0.f) c->dc.cell_factor = t->cell_factor;
+    if (t->emit_blocks_per_sm > 0) c->dc.emit_bps = t->emit_blocks_per_sm;
+    // recorded graphs captured the old settings
+    for (auto& e : c->graphs) cudaGraphExecDestroy(e.exec);
+    c->graphs.clear();
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_get_tuning(const ccfr_ctx* c, ccfr_tuning* t) {
+    if (!c || !t) return CCFR_ERR_INVALID_ARG;
+    t->cell_factor = c->dc.cell_factor;
+    t->emit_blocks_per_sm = c->dc.emit_bps;
+    t->plane_capacity = c->dc.p.K;
+    return CCFR_OK;
+}
+
+ccfr_status ccfr_autotune(ccfr_ctx* c, const float* x, const float* v, int steps, ccfr_tuning* best, double* best_ms,
+                          void* stream) {
+    if (!c || !x || !v || !best || steps < 1 || steps > 16 || !aligned16(x) || !aligned16(v)) return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = c->dc.n_verts;
+    size_t bytes = (size_t)(N > 0 ? N : 1) * sizeof(float4);
+    // 1. plane capacity: 1.5 x the largest per-vertex count at x (counts are exact beyond the capacity)
+    ccfr_status s = ccfr_build_regions(c, x, stream);
+    if (s != CCFR_OK) return s;
+    std::vector<unsigned> cnt((size_t)N);
+    if (N && cudaMemcpyAsync(cnt.data(), c->dc.count, (size_t)N * sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
+                 cudaSuccess)
+        return CCFR_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CCFR_ERR_CUDA;
+    unsigned mx = 0;
+    for (unsigned k : cnt) mx = k > mx ? k : mx;
+    int K = (int)((mx * 3u / 2u + 32u + 31u) / 32u * 32u);
+    if (K < 64) K = 64;
+    if (K > 65536) K = 65536;
+    ccfr_tuning t{};
+    t.plane_capacity = K;
+    s = ccfr_set_tuning(c, &t);
+    if (s != CCFR_OK) return s;
+    // 2. cell size and emission grid: time `steps` substeps from a scratch copy of (x, v)
+    float4 *xs = nullptr, *vs = nullptr;
+    if (cudaMalloc((void**)&xs, bytes) != cudaSuccess || cudaMalloc((void**)&vs, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(xs);
+        return CCFR_ERR_OOM;
+    }
+    const float factors[4] = {1.0f, 1.5f, 2.0f, 3.0f};
+    const int bps[3] = {4, 8, 16};
+    double best_t = 1e300;
+    ccfr_tuning bt{1.5f, 8, K};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaError_t err = cudaSuccess;
+    for (float f : factors) {
+        for (int b : bps) {
+            ccfr_tuning cand{f, b, 0};
+            if ((s = ccfr_set_tuning(c, &cand)) != CCFR_OK) break;
+            err = cudaMemcpyAsync(xs, x, bytes, cudaMemcpyDeviceToDevice, st);
+            if (err == cudaSuccess) err = cudaMemcpyAsync(vs, v, bytes, cudaMemcpyDeviceToDevice, st);
+            if (err != cudaSuccess) break;
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < steps; ++k) enqueue_step(c, xs, vs, st);
+            cudaEventRecord(e1, st);
+            err = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+            if (err != cudaSuccess) break;
+            if (ms < best_t) { best_t = ms; bt = ccfr_tuning{f, b, K}; }
+        }
+        if (s != CCFR_OK || err != cudaSuccess) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(xs);
+    cudaFree(vs);
+    if (s != CCFR_OK) return s;
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    s = ccfr_set_tuning(c, &bt);
+    if (s != CCFR_OK) return s;
+    *best = bt;
+    if (best_ms) *best_ms = best_t / steps;
+    c->regions_valid = false;
     return CCFR_OK;
 }
 

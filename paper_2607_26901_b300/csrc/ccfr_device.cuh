@@ -110,6 +110,11 @@ struct DevCtx {
     float4* x_s;
     int* flags;                 // [0] not converged, [1] done (early exit)
     int n_sm;                   // streaming multiprocessors (persistent grids)
+    int emit_bps;               // emission blocks per SM
+    // several independent scenes in one context (batched step): the scene of
+    // every vertex and each scene's (r, 2r, xi, pad); null for a single scene
+    const unsigned short* vscene;
+    const float4* sparams;
     int4* work;                 // [n_verts] vertices queued for the heavy projection
     unsigned* work_count;       // [1]
     DevStats* stats;
@@ -159,12 +164,32 @@ __device__ __forceinline__ int cell_coord(float v, float inv_h) {
     return (int)floorf(v * inv_h);
 }
 
-__device__ __forceinline__ unsigned cell_hash(int cx, int cy, int cz) {
-    return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u);
+// Cells of different scenes are different cells: the scene enters the hash
+// and the packed tag.  The tag keeps 7 bits per axis, enough to tell apart the
+// cells one search visits (never more than 127 per axis), and 11 scene bits.
+__device__ __forceinline__ unsigned cell_hash(int cx, int cy, int cz, unsigned scene) {
+    return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u) ^
+           (scene * 2654435761u);
 }
 
-__device__ __forceinline__ unsigned cell_pack(int cx, int cy, int cz) {
-    return ((unsigned)cx & 1023u) | (((unsigned)cy & 1023u) << 10) | (((unsigned)cz & 1023u) << 20);
+__device__ __forceinline__ unsigned cell_pack(int cx, int cy, int cz, unsigned scene) {
+    return ((unsigned)cx & 127u) | (((unsigned)cy & 127u) << 7) | (((unsigned)cz & 127u) << 14) | (scene << 21);
+}
+
+__device__ __forceinline__ unsigned pack_scene(unsigned packed) { return packed >> 21; }
+
+// Per-scene parameters of the narrow phase and the clamp.
+struct SceneParams { float r, two_r, xi, pad; };
+__device__ __forceinline__ unsigned scene_of(const DevCtx& c, int v) { return c.vscene ? c.vscene[v] : 0u; }
+__device__ __forceinline__ SceneParams scene_params(const DevCtx& c, unsigned s) {
+    SceneParams q;
+    if (c.sparams) {
+        float4 t = c.sparams[s];
+        q.r = t.x; q.two_r = t.y; q.xi = t.z; q.pad = t.w;
+    } else {
+        q.r = c.p.r; q.two_r = c.p.two_r; q.xi = c.p.xi; q.pad = c.p.pad;
+    }
+    return q;
 }
 
 __device__ __forceinline__ void warp_add_u64(u64* dst, u64 v) {

@@ -35,39 +35,46 @@ __device__ __forceinline__ f3 xyz(float4 a) { return mk(a.x, a.y, a.z); }
 // Padded box of item i of the concatenated item space (triangles, edges,
 // isolated points, vertices): lo = fl32(min - pad), hi = fl32(max + pad).
 __device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restrict__ x, int i,
-                                        float lo[3], float hi[3], int& id) {
-    int kind;
+                                        float lo[3], float hi[3], int& id, unsigned& scene) {
+    int kind, v0;
     float4 a, b, d;
     if (i < c.item_base[KIND_EDGE]) {
         kind = KIND_TRI;
         id = i;
         int3 t = c.tris[id];
+        v0 = t.x;
         a = x[t.x]; b = x[t.y]; d = x[t.z];
     } else if (i < c.item_base[KIND_PT]) {
         kind = KIND_EDGE;
         id = i - c.item_base[KIND_EDGE];
         int2 e = c.edges[id];
+        v0 = e.x;
         a = x[e.x]; b = x[e.y]; d = b;
     } else if (i < c.item_base[KIND_VQ]) {
         kind = KIND_PT;
         id = c.pts[i - c.item_base[KIND_PT]];
+        v0 = id;
         a = x[id]; b = a; d = a;
     } else if (i < c.item_base[KIND_BIGE]) {
         kind = KIND_VQ;
         id = i - c.item_base[KIND_VQ];
+        v0 = id;
         a = x[id]; b = a; d = a;
     } else {
         kind = KIND_BIGE;
         id = i - c.item_base[KIND_BIGE];
         int2 e = c.edges[id];
+        v0 = e.x;
         a = x[e.x]; b = x[e.y]; d = b;
     }
-    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), c.p.pad);
-    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), c.p.pad);
-    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), c.p.pad);
-    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), c.p.pad);
-    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), c.p.pad);
-    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), c.p.pad);
+    scene = scene_of(c, v0);
+    const float pad = scene_params(c, scene).pad;
+    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), pad);
+    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), pad);
+    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), pad);
+    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), pad);
+    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), pad);
+    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), pad);
     return kind;
 }
 
@@ -83,7 +90,8 @@ __global__ void k_extent(DevCtx c, const float4* __restrict__ x) {
     if (i < c.n_items) {
         float lo[3], hi[3];
         int id;
-        int kind = item_box(c, x, i, lo, hi, id);
+        unsigned sc;
+        int kind = item_box(c, x, i, lo, hi, id, sc);
         float m = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
         // positive floats order as integers; the sum is fixed-point (nm) so it is order-independent
         if (m == m && m < 1e6f && kind < 3) {
@@ -99,12 +107,13 @@ __global__ void k_extent(DevCtx c, const float4* __restrict__ x) {
     }
 }
 
-__device__ __forceinline__ unsigned item_bucket_of(const DevCtx& c, int kind, const float lo[3], unsigned& packed) {
+__device__ __forceinline__ unsigned item_bucket_of(const DevCtx& c, int kind, const float lo[3], unsigned scene,
+                                                   unsigned& packed) {
     float h = cell_size_of(c, cell_kind(kind));
     float inv = 1.0f / h;
     int cx = cell_coord(lo[0], inv), cy = cell_coord(lo[1], inv), cz = cell_coord(lo[2], inv);
-    packed = cell_pack(cx, cy, cz);
-    return (unsigned)c.bucket_base[kind] + (cell_hash(cx, cy, cz) & (unsigned)c.bucket_mask[kind]);
+    packed = cell_pack(cx, cy, cz, scene);
+    return (unsigned)c.bucket_base[kind] + (cell_hash(cx, cy, cz, scene) & (unsigned)c.bucket_mask[kind]);
 }
 
 // Triangles and edges whose box spans more than a cell go to the oversized
@@ -115,18 +124,19 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     if (i >= c.n_items) return;
     float lo[3], hi[3];
     int id;
-    int kind = item_box(c, x, i, lo, hi, id);
+    unsigned sc;
+    int kind = item_box(c, x, i, lo, hi, id, sc);
     if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
         unsigned s = atomicAdd(&c.big_count[kind], 1u);
         unsigned o = c.big_base[kind] + s;
         c.big[o] = id;
         c.big_box[2 * o] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
-        c.big_box[2 * o + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
+        c.big_box[2 * o + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(sc));
         return;
     }
     unsigned packed;
-    unsigned b = item_bucket_of(c, kind, lo, packed);
+    unsigned b = item_bucket_of(c, kind, lo, sc, packed);
     c.item_bucket[i] = b;
     atomicAdd(&c.bucket_count[b], 1u);
 }
@@ -137,11 +147,12 @@ __global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
     if (i >= c.n_items) return;
     float lo[3], hi[3];
     int id;
-    int kind = item_box(c, x, i, lo, hi, id);
+    unsigned sc;
+    int kind = item_box(c, x, i, lo, hi, id, sc);
     if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
     unsigned packed;
-    unsigned b = item_bucket_of(c, kind, lo, packed);
+    unsigned b = item_bucket_of(c, kind, lo, sc, packed);
     unsigned pos = c.bucket_count[b] + atomicAdd(&c.bucket_fill[b], 1u);
     c.rec[2 * pos] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
     c.rec[2 * pos + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(packed));
@@ -195,19 +206,24 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_tiles(DevCtx c, unsigned*
     if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
 }
 
+// Scan of the tile sums by one block, SCAN_TILE at a time with a running carry.
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_top(DevCtx c, unsigned* tile_sums, int n_tiles) {
     if (c.flags[1]) return;
     __shared__ unsigned smem[33];
-    int base = threadIdx.x * SCAN_ITEMS;
-    unsigned vals[SCAN_ITEMS], s = 0;
-    #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) { vals[k] = (base + k < n_tiles) ? tile_sums[base + k] : 0u; s += vals[k]; }
-    unsigned total;
-    unsigned off = block_exclusive_scan(s, smem, total);
-    #pragma unroll
-    for (int k = 0; k < SCAN_ITEMS; ++k) {
-        if (base + k < n_tiles) tile_sums[base + k] = off;
-        off += vals[k];
+    unsigned carry = 0;
+    for (int chunk = 0; chunk < n_tiles; chunk += SCAN_TILE) {
+        int base = chunk + threadIdx.x * SCAN_ITEMS;
+        unsigned vals[SCAN_ITEMS], s = 0;
+        #pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) { vals[k] = (base + k < n_tiles) ? tile_sums[base + k] : 0u; s += vals[k]; }
+        unsigned total;
+        unsigned off = block_exclusive_scan(s, smem, total) + carry;
+        #pragma unroll
+        for (int k = 0; k < SCAN_ITEMS; ++k) {
+            if (base + k < n_tiles) tile_sums[base + k] = off;
+            off += vals[k];
+        }
+        carry += total;
     }
 }
 
@@ -290,6 +306,7 @@ __device__ bool closest_on_triangle(f3 a, f3 b, f3 cc, f3& q, float& wa, float& 
 // Vertex-face pair (Alg. 3): p against triangle t = (ta, tb, tc).  Local
 // coordinates centred at p.  Returns 1 if the pair is accepted (phi < 2r).
 __device__ int narrow_vf(const DevCtx& c, int p, float4 P, int t, int3 T, float4 A, float4 B, float4 C) {
+    const SceneParams sp = scene_params(c, scene_of(c, p));
     f3 o = xyz(P);
     f3 a = sub(xyz(A), o), b = sub(xyz(B), o), cc = sub(xyz(C), o);
     f3 q;
@@ -309,8 +326,8 @@ __device__ int narrow_vf(const DevCtx& c, int p, float4 P, int t, int3 T, float4
     }
     float dist = len(diff);
     if (dist == 0.f) return 0;
-    float phi = dist - c.p.xi;
-    if (!(phi < c.p.two_r)) return 0;
+    float phi = dist - sp.xi;
+    if (!(phi < sp.two_r)) return 0;
     float wf = wa * A.w + wb * B.w + wc * C.w;
     float W = P.w + wf;
     if (W == 0.f) return 0;
@@ -352,6 +369,7 @@ __device__ void closest_segments_fp64(float4 P1, float4 Q1, float4 P2, float4 Q2
 // near-parallel FP64 solve was used.
 __device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A0, float4 A1, float4 B0,
                          float4 B1, int& fp64) {
+    const SceneParams sp = scene_params(c, scene_of(c, E.x));
     f3 o = xyz(A0);
     f3 d1 = sub(xyz(A1), o), p2 = sub(xyz(B0), o), d2 = sub(xyz(B1), xyz(B0));
     // r = p1 - p2 = -p2
@@ -394,8 +412,8 @@ __device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A
     }
     float dist = len(diff);
     if (dist == 0.f) return 0;
-    float phi = dist - c.p.xi;
-    if (!(phi < c.p.two_r)) return 0;
+    float phi = dist - sp.xi;
+    if (!(phi < sp.two_r)) return 0;
     float wa = (1.f - s) * A0.w + s * A1.w;
     float wb = (1.f - t) * B0.w + t * B1.w;
     float W = wa + wb;
@@ -414,11 +432,12 @@ __device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A
 
 // Point-point pair (isolated particles).
 __device__ int narrow_pp(const DevCtx& c, int p, int q, float4 P, float4 Q) {
+    const SceneParams sp = scene_params(c, scene_of(c, p));
     f3 diff = sub(xyz(P), xyz(Q));
     float dist = len(diff);
     if (dist == 0.f) return 0;
-    float phi = dist - c.p.xi;
-    if (!(phi < c.p.two_r)) return 0;
+    float phi = dist - sp.xi;
+    if (!(phi < sp.two_r)) return 0;
     float W = P.w + Q.w;
     if (W == 0.f) return 0;
     f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
@@ -541,22 +560,24 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4
         float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
         if (act) { r0 = c.rec[2 * (s0 + lane)]; r1 = c.rec[2 * (s0 + lane) + 1]; }
         const int qid = __float_as_int(r0.w);
+        const unsigned qs = pack_scene(__float_as_uint(r1.w));
         int3 qt = make_int3(-1, -1, -1);
         if (QK == KIND_TRI && act) qt = c.tris[qid];
         const int mx = cell_coord(r0.x, inv), my = cell_coord(r0.y, inv), mz = cell_coord(r0.z, inv);
         unsigned pending = __ballot_sync(FULL, act);
         while (pending) {
-            // the queries of one cell share its neighbourhood
+            // the queries of one cell (of one scene) share its neighbourhood
             const int leader = __ffs(pending) - 1;
             const int cx = __shfl_sync(FULL, mx, leader), cy = __shfl_sync(FULL, my, leader),
                       cz = __shfl_sync(FULL, mz, leader);
-            const bool in = ((pending >> lane) & 1u) && mx == cx && my == cy && mz == cz;
+            const unsigned cs = __shfl_sync(FULL, qs, leader);
+            const bool in = ((pending >> lane) & 1u) && mx == cx && my == cy && mz == cz && qs == cs;
             pending &= ~__ballot_sync(FULL, in);
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const unsigned b = ibase + (cell_hash(cx + dx, cy + dy, cz + dz) & imask);
-                        const unsigned pk = cell_pack(cx + dx, cy + dy, cz + dz);
+                        const unsigned b = ibase + (cell_hash(cx + dx, cy + dy, cz + dz, cs) & imask);
+                        const unsigned pk = cell_pack(cx + dx, cy + dy, cz + dz, cs);
                         const unsigned t1 = c.bucket_count[b + 1];
                         for (unsigned s = c.bucket_count[b]; s < t1; ++s) {
                             const float4 i1 = c.rec[2 * s + 1];
@@ -597,22 +618,28 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4
 // edges also test the other oversized edges with a larger id.  Together with
 // the per-cell pass over the fitting primitives this visits every candidate
 // pair exactly once.
-__device__ __forceinline__ void prim_box(const DevCtx& c, const float4* __restrict__ x, int kind, int id,
-                                         float lo[3], float hi[3]) {
+__device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __restrict__ x, int kind, int id,
+                                             float lo[3], float hi[3]) {
     float4 a, b, d;
+    int v0;
     if (kind == KIND_TRI) {
         int3 t = c.tris[id];
+        v0 = t.x;
         a = x[t.x]; b = x[t.y]; d = x[t.z];
     } else {
         int2 e = c.edges[id];
+        v0 = e.x;
         a = x[e.x]; b = x[e.y]; d = b;
     }
-    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), c.p.pad);
-    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), c.p.pad);
-    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), c.p.pad);
-    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), c.p.pad);
-    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), c.p.pad);
-    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), c.p.pad);
+    const unsigned scene = scene_of(c, v0);
+    const float pad = scene_params(c, scene).pad;
+    lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), pad);
+    lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), pad);
+    lo[2] = __fsub_rn(fminf(fminf(a.z, b.z), d.z), pad);
+    hi[0] = __fadd_rn(fmaxf(fmaxf(a.x, b.x), d.x), pad);
+    hi[1] = __fadd_rn(fmaxf(fmaxf(a.y, b.y), d.y), pad);
+    hi[2] = __fadd_rn(fmaxf(fmaxf(a.z, b.z), d.z), pad);
+    return scene;
 }
 
 template <int QK, int MODE>
@@ -647,7 +674,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nbig; u += stride) {
         const int o = c.big[c.big_base[QK] + u];
         float lo[3], hi[3];
-        prim_box(c, x, QK, o, lo, hi);
+        const unsigned qs = prim_box(c, x, QK, o, lo, hi);
         int3 ot = make_int3(-1, -1, -1);
         if (QK == KIND_TRI) ot = c.tris[o];
         bool fin = isfinite(lo[0]) && isfinite(lo[1]) && isfinite(lo[2]) && isfinite(hi[0]) && isfinite(hi[1]) &&
@@ -663,7 +690,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         const unsigned t_begin = c.bucket_count[ibase], t_end = c.bucket_count[c.bucket_base[IK + 1]];
         auto test = [&](float4 i0, float4 i1) -> int2 {
             const int iid = __float_as_int(i0.w);
-            bool hit = lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
+            bool hit = pack_scene(__float_as_uint(i1.w)) == qs && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
             if (QK == KIND_TRI) {
                 if (!(hit && iid != ot.x && iid != ot.y && iid != ot.z)) return make_int2(-1, -1);
                 return make_int2(o, iid);
@@ -672,8 +699,10 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             return make_int2(min(o, iid), max(o, iid));
         };
         const float cmax = 1e9f;
+        // the packed tag tells apart at most 127 cells per axis: wider ranges test the whole table
         const bool huge = fabsf(fx0) > cmax || fabsf(fx1) > cmax || fabsf(fy0) > cmax || fabsf(fy1) > cmax ||
-                          fabsf(fz0) > cmax || fabsf(fz1) > cmax;
+                          fabsf(fz0) > cmax || fabsf(fz1) > cmax || fx1 - fx0 >= 127.f || fy1 - fy0 >= 127.f ||
+                          fz1 - fz0 >= 127.f;
         if (huge || ncell * 8.0 > (double)(t_end - t_begin)) {
             // cheaper to test the whole table
             for (unsigned s0 = t_begin; s0 < t_end; s0 += 32) {
@@ -687,8 +716,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             for (int cz = z0; cz <= z1; ++cz)
                 for (int cy = y0; cy <= y1; ++cy)
                     for (int cx = x0; cx <= x1; ++cx) {
-                        const unsigned b = ibase + (cell_hash(cx, cy, cz) & imask);
-                        const unsigned pk = cell_pack(cx, cy, cz);
+                        const unsigned b = ibase + (cell_hash(cx, cy, cz, qs) & imask);
+                        const unsigned pk = cell_pack(cx, cy, cz, qs);
                         const unsigned t1 = c.bucket_count[b + 1];
                         for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
                             const unsigned s = s0 + lane;
@@ -710,8 +739,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             for (int dz = -1; dz <= 1; ++dz)
                 for (int dy = -1; dy <= 1; ++dy)
                     for (int dx = -1; dx <= 1; ++dx) {
-                        const unsigned b = bb + (cell_hash(bx + dx, by + dy, bz + dz) & bm);
-                        const unsigned pk = cell_pack(bx + dx, by + dy, bz + dz);
+                        const unsigned b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
+                        const unsigned pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
                         const unsigned t1 = c.bucket_count[b + 1];
                         for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
                             const unsigned s = s0 + lane;
@@ -1087,7 +1116,7 @@ template <bool STEP>
 __device__ __forceinline__ void finish_vertex(const DevCtx& c, int lane, int v, float4 X, float4 XP, f3 y0, f3 y,
                                               bool halted, const float4* pl, int np, bool over, unsigned cnt,
                                               BlockCounters& bc, float4* x_out, unsigned char* halt_out) {
-    if (STEP && !halted) y = clamp_len(y, c.p.r);
+    if (STEP && !halted) y = clamp_len(y, scene_params(c, scene_of(c, v)).r);
     f3 xn = add(xyz(X), y);
     bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
     if (!halted && np > 0 && (changed || over)) {
@@ -1447,7 +1476,7 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     int nqb = c.bucket_base[KIND_VQ];
     k_make_units<<<nblk(nqb, 256), 256, 0, st>>>(c);
     if (tm) tm->mark(ST_GRID_UNITS, st);
-    const int G = c.n_sm * 8;
+    const int G = c.n_sm * (c.emit_bps > 0 ? c.emit_bps : 8);
     if (mode == MODE_PLANES) {
         if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF, st);

@@ -18,6 +18,7 @@ codimensional wires falling on a grate, and particle clouds.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
+from functools import lru_cache
 
 import numpy as np
 
@@ -64,21 +65,22 @@ def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 /
                 plane_capacity=int(plane_capacity))
 
 
+def canonical_edges(e: np.ndarray) -> np.ndarray:
+    """Unique undirected edges (min, max), sorted lexicographically."""
+    if len(e) == 0:
+        return np.zeros((0, 2), np.int32)
+    e = np.sort(np.asarray(e, np.int64).reshape(-1, 2), axis=1)
+    key = np.unique(e[:, 0] * (int(e.max()) + 1) + e[:, 1])
+    m = int(e.max()) + 1
+    return np.stack([key // m, key % m], 1).astype(np.int32)
+
+
 def edges_of_tris(tris: np.ndarray) -> np.ndarray:
     """Unique undirected edges of a triangle list, (min, max), lexicographic."""
     if len(tris) == 0:
         return np.zeros((0, 2), np.int32)
-    e = np.concatenate([tris[:, [0, 1]], tris[:, [1, 2]], tris[:, [2, 0]]], axis=0)
-    e = np.sort(e, axis=1)
-    e = np.unique(e, axis=0)
-    return e.astype(np.int32)
-
-
-def canonical_edges(e: np.ndarray) -> np.ndarray:
-    if len(e) == 0:
-        return np.zeros((0, 2), np.int32)
-    e = np.sort(np.asarray(e, np.int64), axis=1)
-    return np.unique(e, axis=0).astype(np.int32)
+    t = np.asarray(tris)
+    return canonical_edges(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]], axis=0))
 
 
 def _grid_tris(nx: int, nz: int, base: int = 0) -> np.ndarray:
@@ -104,20 +106,15 @@ def _cloth_grid(n_side: int, spacing: float, center, rng, jitter: float) -> np.n
     return p
 
 
-def uv_sphere(radius: float, slices: int, stacks: int, center=(0.0, 0.0, 0.0)):
-    """UV sphere: 2 poles + (stacks-1) rings of `slices` vertices.
-
-    slices=50, stacks=41 gives 2,002 vertices and 4,000 triangles.
-    """
-    pts = [(0.0, radius, 0.0)]
+@lru_cache(maxsize=16)
+def _unit_uv_sphere(slices: int, stacks: int):
+    pts = [(0.0, 1.0, 0.0)]
     for i in range(1, stacks):
         th = np.pi * i / stacks
         for j in range(slices):
             ph = 2.0 * np.pi * j / slices
-            pts.append((radius * np.sin(th) * np.cos(ph), radius * np.cos(th),
-                        radius * np.sin(th) * np.sin(ph)))
-    pts.append((0.0, -radius, 0.0))
-    p = np.asarray(pts) + np.asarray(center)
+            pts.append((np.sin(th) * np.cos(ph), np.cos(th), np.sin(th) * np.sin(ph)))
+    pts.append((0.0, -1.0, 0.0))
     south = len(pts) - 1
     tris = []
 
@@ -134,7 +131,20 @@ def uv_sphere(radius: float, slices: int, stacks: int, center=(0.0, 0.0, 0.0)):
             tris.append((a, d, c))
     for j in range(slices):
         tris.append((south, ring(stacks - 1, j), ring(stacks - 1, j + 1)))
-    return p, np.asarray(tris, np.int32)
+    p = np.asarray(pts)
+    t = np.asarray(tris, np.int32)
+    p.setflags(write=False)
+    t.setflags(write=False)
+    return p, t, edges_of_tris(t)
+
+
+def uv_sphere(radius: float, slices: int, stacks: int, center=(0.0, 0.0, 0.0)):
+    """UV sphere: 2 poles + (stacks-1) rings of `slices` vertices.
+
+    slices=50, stacks=41 gives 2,002 vertices and 4,000 triangles.
+    """
+    p, t, _ = _unit_uv_sphere(slices, stacks)
+    return p * radius + np.asarray(center), t.copy()
 
 
 def _assemble(name, parts_p, parts_w, parts_tris, parts_edges, params, v=None) -> Scene:
@@ -283,6 +293,37 @@ def particle_cloud(n: int, spacing: float = 3e-3, jitter: float = 4e-4, seed: in
     params = default_params(1e-3, 2e-3, iters=iters, steps=steps, plane_capacity=plane_capacity)
     return _assemble("particle_cloud", [p, sp], [np.full(len(p), 1.0 / mass), np.zeros(len(sp))],
                      [None, st], [None, edges_of_tris(st)], params)
+
+
+def batch(n_scenes: int = 512, seed: int = 4, min_verts: int = 1024, max_verts: int = 65536,
+          median_verts: int = 8192, particle_frac: float = 0.2, iters: int = 10, steps: int = 20,
+          plane_capacity: int = 256, sphere_slices: int = 50, sphere_stacks: int = 41) -> list:
+    """Independent scenes of uneven sizes for the batched step.
+
+    Sizes N ~ lognormal(ln median, ln 2) clipped to [min, max].  80% are
+    square cloths of side round(sqrt(N)) at 1 cm (+-1 mm jitter) dropped on a
+    static UV sphere of radius 0.3 x the cloth side; 20% are particle clouds of
+    N points (3 mm lattice, +-0.4 mm jitter) above a static sphere.  Cloth:
+    r = 5 mm, xi = 1 mm; particles: r = 1 mm, xi = 2 mm; 10 iterations.
+    """
+    rng = np.random.default_rng(seed)
+    sizes = np.clip(np.exp(rng.normal(np.log(median_verts), np.log(2.0), n_scenes)), min_verts, max_verts)
+    kinds = rng.uniform(size=n_scenes) < particle_frac
+    out = []
+    for k in range(n_scenes):
+        n = int(sizes[k])
+        sub = int(rng.integers(1 << 30))
+        if kinds[k]:
+            side_m = np.ceil(n ** (1.0 / 3.0)) * 3e-3
+            sc = particle_cloud(n, seed=sub, sphere_radius=max(0.02, 0.3 * side_m), iters=iters, steps=steps,
+                                plane_capacity=plane_capacity)
+        else:
+            side = max(4, int(round(np.sqrt(n))))
+            sc = cloth_on_sphere(n_side=side, radius=0.3 * side * 0.01, slices=sphere_slices, stacks=sphere_stacks,
+                                 seed=sub, iters=iters, steps=steps, plane_capacity=plane_capacity)
+        sc.name = f"batch{k}_{sc.name}"
+        out.append(sc)
+    return out
 
 
 def config(k: int, seed: int | None = None) -> Scene:
