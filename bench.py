@@ -43,6 +43,8 @@ WORKLOADS = {
                         "32x32 cloth (1,024 verts) on a static 4,000-tri sphere, 10 iterations"),
     "batch": (None, "512 independent scenes, sizes lognormal(ln 8192, ln 2) in [1k, 64k] verts: 80% cloths "
                     "on static spheres (r=5 mm, xi=1 mm), 20% particle clouds (r=1 mm, xi=2 mm); 10 iterations"),
+    "serve": (None, "Poisson step requests over the 512 batch scenes plus 4 cloths of 1024x1024 (1,048,576 verts, "
+                    "p=0.05), device-resident state, HBM-budget admission"),
     "wires": (lambda seed: S.wires(seed=seed),
               "16,384 helical strands x 64 segments (1,064,960 verts) over a static grate, 10 iterations"),
 }
@@ -135,6 +137,21 @@ def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2):
                            f"1 substep x {iters} iterations, seed {seed}"
 
 
+def max_over_ranks(v: float, dist=None, device=None) -> float:
+    """Largest value over the ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def scene_seed(workload: str, rank: int) -> int:
+    """Each rank steps its own replica of the workload (independent scenes)."""
+    return (2 if workload.startswith("cloth_stack") else 1) + rank
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -152,6 +169,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: number of step requests")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=8, help="serve: concurrent steps")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     builder, desc = WORKLOADS[args.workload]
@@ -161,6 +181,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, ws, rank, local, desc)
+        return
+    if args.workload == "serve":
+        run_serve(args, ws, rank, local, desc)
         return
 
     import torch
@@ -172,7 +195,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    sc = builder(2 + rank if args.workload.startswith("cloth_stack") else rank + 1)
+    sc = builder(scene_seed(args.workload, rank))
     iters = sc.params["iters"]
     x = torch.as_tensor(sc.x).cuda().contiguous()
     v = torch.as_tensor(sc.v).cuda().contiguous()
@@ -207,11 +230,7 @@ def main():
     if dist:
         dist.barrier()
     clocks = sampler.stop() if sampler else None
-    ms_total = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     st = ctx.stats()
     iters_run = st["iterations"] / max(args.steps, 1)
     units_per_rank = sc.n_movable * st["iterations"]
@@ -280,11 +299,7 @@ def main():
         for _ in range(ke):
             ctx.step_host(xa, va)
         t1 = time.perf_counter()
-        te = t1 - t0
-        if dist:
-            t = torch.tensor([te], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            te = float(t.item())
+        te = max_over_ranks(t1 - t0, dist, "cuda")
         st3 = ctx.stats()
         e2e = {"value": sc.n_movable * st3["iterations"] * ws / te, "unit": UNIT,
                "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": 2 * N * 16}
@@ -407,6 +422,78 @@ def run_batch(args, ws, rank, local, desc):
             "batched_over_plain": value / plain_value,
             "stats_per_iter": {k: st[k] / max(st["iterations"], 1) for k in ("planes", "halts", "violated_verts",
                                                                             "overflow_verts")},
+        }), flush=True)
+
+
+def serve_pool(seed: int = 5):
+    big = [S.cloth_on_sphere(n_side=1024, radius=0.3 * 10.24, seed=50 + k, plane_capacity=256) for k in range(4)]
+    return S.batch(seed=seed), big
+
+
+def run_serve(args, ws, rank, local, desc):
+    """Open-loop replay of a seeded Poisson trace of step requests through the
+    serving loop; latency = completion - arrival, per request."""
+    import numpy as np
+    import torch
+    from paper_2607_26901_b300 import ccfr
+
+    torch.cuda.set_device(local)
+    small, big = serve_pool(5 + rank)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    rng = np.random.default_rng(50 + rank)
+    n = args.requests
+    t_arr = np.cumsum(rng.exponential(1.0 / args.rate, n))
+    t_arr -= t_arr[0]
+    pick_big = rng.uniform(size=n) < 0.05
+    which = np.where(pick_big, rng.integers(0, len(big), n), rng.integers(0, len(small), n))
+    out = {}
+    for slots in sorted({args.slots, 1}, reverse=True):
+        sv = ccfr.Server(budget, n_slots=slots, timeout_s=300.0)
+        ids_small = [sv.add_scene(sc) for sc in small]
+        ids_big = [sv.add_scene(sc) for sc in big]
+        sid = np.where(pick_big, np.array(ids_big)[np.minimum(which, len(big) - 1)],
+                       np.array(ids_small)[np.minimum(which, len(small) - 1)])
+        for i in range(n):
+            sv.submit(int(sid[i]), float(t_arr[i]))
+        t_pre = time.perf_counter()
+        preloaded = sv.preload(0.9)
+        t_pre = time.perf_counter() - t_pre
+        t0 = time.perf_counter()
+        sv.start()
+        done = sv.wait(1800.0)
+        wall = time.perf_counter() - t0
+        res = sv.results(n)
+        info = sv.info()
+        ok = res["status"] == 0
+        lat = (res["t_done"] - res["t_arrival"])[ok] * 1e3
+        span = float(res["t_done"][ok].max() - res["t_arrival"].min()) if ok.any() else float("nan")
+        scenes_all = small + big
+        nv = np.array([scenes_all[i].n_movable for i in range(len(scenes_all))])
+        iters = small[0].params["iters"]
+        vert_updates = float(nv[sid[ok]].sum()) * iters
+        out[slots] = {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                      "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                      "mean_ms": float(lat.mean()) if len(lat) else None,
+                      "completed": int(ok.sum()), "failed": int((~ok).sum()), "done": int(done),
+                      "throughput_req_s": ok.sum() / span, "value": vert_updates / span,
+                      "span_s": span, "wall_s": wall, "admissions": info["admissions"],
+                      "evictions": info["evictions"], "peak_resident_gb": info["peak_resident_bytes"] / 1e9,
+                      "preloaded": preloaded, "preload_s": round(t_pre, 2)}
+        sv.close()
+        if slots == 1 and args.slots != 1:
+            # the single-slot run only needs to establish the sequential rate
+            pass
+    best = out[args.slots]
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": best["value"] * ws, "unit": UNIT, "n_gpus": ws, "steps": n,
+            "warmup": 0, "ms_per_step": best["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "serve", "description": desc, "requests": n, "rate_per_s": args.rate,
+                       "slots": args.slots, "hbm_budget_gb": budget / 1e9, "scenes": len(small) + len(big)},
+            "served": best, "single_slot": out.get(1),
+            "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
         }), flush=True)
 
 

@@ -250,6 +250,55 @@ ccfr_status ccfr_get_tuning(const ccfr_ctx* ctx, ccfr_tuning* t);
 ccfr_status ccfr_autotune(ccfr_ctx* ctx, const float* x, const float* v, int steps, ccfr_tuning* best,
                           double* best_ms, void* stream);
 
+/* ---------------------------------------------------------------- Serving
+ * A server takes step requests for registered scenes as they arrive, keeps
+ * admitted scenes' state on the device, admits scenes within an HBM budget
+ * (evicting idle scenes, least recently used first, to the host), and runs
+ * up to n_slots steps of different scenes at once on separate streams, so
+ * the work of requests that arrive while others run overlaps on the device.
+ * Requests of one scene run in arrival order.  Each request is one
+ * ccfr_step; a scene's results are the same whatever else is served.
+ * Waits are bounded by timeout_s (a step that does not finish in time is
+ * reported as CCFR_ERR_TIMEOUT).  The server allocates device memory when it
+ * admits a scene.  Calls are thread-safe. */
+typedef struct ccfr_server ccfr_server;
+
+typedef struct {
+    long scenes, requests, done, failed, admissions, evictions;
+    size_t resident_bytes, peak_resident_bytes, budget_bytes;
+} ccfr_server_info;
+
+ccfr_status ccfr_server_create(size_t hbm_budget_bytes, int n_slots, double timeout_s, ccfr_server** out);
+/* Register a scene (host arrays, copied; x is also the rest shape).  Only
+ * before ccfr_server_start.  CCFR_ERR_OOM if the scene alone exceeds the budget. */
+ccfr_status ccfr_server_add_scene(ccfr_server* sv, int n_verts, int n_edges, int n_tris, const int* edges,
+                                  const int* tris, const float* x, const float* v, const ccfr_params* params,
+                                  int* scene_id);
+/* Queue one step of a scene, due t_arrival seconds after ccfr_server_start
+ * (non-decreasing across calls).  May be called before or after start. */
+ccfr_status ccfr_server_submit(ccfr_server* sv, int scene_id, double t_arrival, long* request_id);
+/* Before start: admit registered scenes, in order, while the resident bytes
+ * stay within `fraction` of the budget (first requests then skip admission). */
+ccfr_status ccfr_server_preload(ccfr_server* sv, double fraction, int* n_admitted);
+ccfr_status ccfr_server_start(ccfr_server* sv);
+/* Wait (at most timeout_s) until every submitted request is done. */
+ccfr_status ccfr_server_wait(ccfr_server* sv, double timeout_s, long* n_done);
+/* Per request (first n): arrival, start and completion times (s, since
+ * start; -1 if not reached) and status (-1 pending). */
+ccfr_status ccfr_server_results(ccfr_server* sv, long n, double* t_arrival, double* t_start, double* t_done,
+                                int* status);
+/* Current state of a scene (host arrays, n_verts x 4 floats each). */
+ccfr_status ccfr_server_get_state(ccfr_server* sv, int scene_id, float* x, float* v);
+ccfr_status ccfr_server_get_info(ccfr_server* sv, ccfr_server_info* out);
+/* Device bytes a resident scene takes (context, plane lists, state), the
+ * amount the server charges against its budget. */
+ccfr_status ccfr_estimate_bytes(int n_verts, int n_edges, int n_tris, int plane_capacity, size_t* bytes);
+/* Test hook: steps of the scene are treated as never finishing (no GPU work
+ * is issued), to exercise the bounded wait. */
+ccfr_status ccfr_server_set_stall(ccfr_server* sv, int scene_id, int stall);
+ccfr_status ccfr_server_stop(ccfr_server* sv);
+ccfr_status ccfr_server_destroy(ccfr_server* sv);
+
 /* Context geometry: n_verts, plane capacity, number of edge colours. */
 ccfr_status ccfr_get_info(const ccfr_ctx* ctx, int* n_verts, int* capacity, int* n_colors);
 

@@ -15,7 +15,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 LIB = PKG / "_lib" / "libccfr.so"
-SOURCES = ["ccfr_kernels.cu", "ccfr_api.cu"]
+SOURCES = ["ccfr_kernels.cu", "ccfr_api.cu", "ccfr_server.cpp"]
 DEPS = SOURCES + ["ccfr_device.cuh", "ccfr_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

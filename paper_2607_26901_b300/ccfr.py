@@ -63,6 +63,14 @@ class Tuning(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class ServerInfo(C.Structure):
+    _fields_ = [(n, C.c_long) for n in ("scenes", "requests", "done", "failed", "admissions", "evictions")] + \
+               [(n, C.c_size_t) for n in ("resident_bytes", "peak_resident_bytes", "budget_bytes")]
+
+    def as_dict(self) -> dict:
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
 _lib = None
 
 
@@ -93,6 +101,19 @@ def lib():
             "ccfr_set_tuning": [P, C.POINTER(Tuning)],
             "ccfr_get_tuning": [P, C.POINTER(Tuning)],
             "ccfr_autotune": [P, P, P, C.c_int, C.POINTER(Tuning), C.POINTER(C.c_double), P],
+            "ccfr_server_create": [C.c_size_t, C.c_int, C.c_double, C.POINTER(P)],
+            "ccfr_server_add_scene": [P, C.c_int, C.c_int, C.c_int, P, P, P, P, C.POINTER(Params), C.POINTER(C.c_int)],
+            "ccfr_server_submit": [P, C.c_int, C.c_double, C.POINTER(C.c_long)],
+            "ccfr_server_start": [P],
+            "ccfr_server_preload": [P, C.c_double, C.POINTER(C.c_int)],
+            "ccfr_server_wait": [P, C.c_double, C.POINTER(C.c_long)],
+            "ccfr_server_results": [P, C.c_long, P, P, P, P],
+            "ccfr_server_get_state": [P, C.c_int, P, P],
+            "ccfr_server_get_info": [P, C.POINTER(ServerInfo)],
+            "ccfr_server_set_stall": [P, C.c_int, C.c_int],
+            "ccfr_server_stop": [P],
+            "ccfr_server_destroy": [P],
+            "ccfr_estimate_bytes": [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_size_t)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -110,7 +131,11 @@ def exported_symbols() -> list[str]:
     return ["ccfr_create", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
             "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
             "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
-            "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune"]
+            "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune",
+            "ccfr_server_create", "ccfr_server_add_scene", "ccfr_server_submit", "ccfr_server_start",
+            "ccfr_server_preload",
+            "ccfr_server_wait", "ccfr_server_results", "ccfr_server_get_state", "ccfr_server_get_info",
+            "ccfr_server_set_stall", "ccfr_server_stop", "ccfr_server_destroy", "ccfr_estimate_bytes"]
 
 
 def _check(rc: int, what: str):
@@ -317,3 +342,90 @@ class Context:
 
     def reset_stats(self, stream=None):
         _check(lib().ccfr_reset_stats(self.h, _stream(stream)), "ccfr_reset_stats")
+
+
+def estimate_bytes(scene, plane_capacity: int | None = None) -> int:
+    """Device bytes a resident scene takes (what the server charges)."""
+    b = C.c_size_t()
+    k = plane_capacity or scene.params.get("plane_capacity", 64)
+    _check(lib().ccfr_estimate_bytes(scene.n_verts, len(scene.edges), len(scene.tris), k, C.byref(b)),
+           "ccfr_estimate_bytes")
+    return b.value
+
+
+class Server:
+    """Serving loop (ccfr_server_*): step requests for registered scenes,
+    device-resident state, HBM-budget admission, n_slots concurrent steps."""
+
+    def __init__(self, hbm_budget_bytes: int, n_slots: int = 8, timeout_s: float = 30.0):
+        h = C.c_void_p()
+        _check(lib().ccfr_server_create(int(hbm_budget_bytes), n_slots, timeout_s, C.byref(h)), "ccfr_server_create")
+        self.h = h
+        self.n_verts = []
+
+    def add_scene(self, scene, flags: int = 0, plane_capacity: int | None = None) -> int:
+        p = make_params(scene.params, flags, plane_capacity)
+        e = np.ascontiguousarray(scene.edges, np.int32)
+        t = np.ascontiguousarray(scene.tris, np.int32)
+        x = np.ascontiguousarray(scene.x, np.float32)
+        v = np.ascontiguousarray(scene.v, np.float32)
+        sid = C.c_int()
+        ptr = lambda a: a.ctypes.data_as(C.c_void_p) if a.size else None  # noqa: E731
+        _check(lib().ccfr_server_add_scene(self.h, scene.n_verts, len(e), len(t), ptr(e), ptr(t), ptr(x), ptr(v),
+                                           C.byref(p), C.byref(sid)), "ccfr_server_add_scene")
+        self.n_verts.append(scene.n_verts)
+        return sid.value
+
+    def submit(self, scene_id: int, t_arrival: float) -> int:
+        rid = C.c_long()
+        _check(lib().ccfr_server_submit(self.h, scene_id, t_arrival, C.byref(rid)), "ccfr_server_submit")
+        return rid.value
+
+    def preload(self, fraction: float = 0.9) -> int:
+        n = C.c_int()
+        _check(lib().ccfr_server_preload(self.h, fraction, C.byref(n)), "ccfr_server_preload")
+        return n.value
+
+    def start(self):
+        _check(lib().ccfr_server_start(self.h), "ccfr_server_start")
+
+    def wait(self, timeout_s: float) -> int:
+        n = C.c_long()
+        rc = lib().ccfr_server_wait(self.h, timeout_s, C.byref(n))
+        if rc not in (0, 5):
+            _check(rc, "ccfr_server_wait")
+        return n.value
+
+    def results(self, n: int) -> dict:
+        ta, ts, td = np.zeros(n), np.zeros(n), np.zeros(n)
+        st = np.zeros(n, np.int32)
+        f = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+        _check(lib().ccfr_server_results(self.h, n, f(ta), f(ts), f(td), f(st)), "ccfr_server_results")
+        return {"t_arrival": ta, "t_start": ts, "t_done": td, "status": st}
+
+    def state(self, scene_id: int):
+        n = self.n_verts[scene_id]
+        x = np.zeros((n, 4), np.float32)
+        v = np.zeros((n, 4), np.float32)
+        _check(lib().ccfr_server_get_state(self.h, scene_id, x.ctypes.data_as(C.c_void_p),
+                                           v.ctypes.data_as(C.c_void_p)), "ccfr_server_get_state")
+        return x, v
+
+    def info(self) -> dict:
+        i = ServerInfo()
+        _check(lib().ccfr_server_get_info(self.h, C.byref(i)), "ccfr_server_get_info")
+        return i.as_dict()
+
+    def stall(self, scene_id: int, on: bool = True):
+        _check(lib().ccfr_server_set_stall(self.h, scene_id, int(on)), "ccfr_server_set_stall")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ccfr_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
