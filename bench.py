@@ -39,6 +39,8 @@ WORKLOADS = {
                     "iid U(-0.5,0.5) m/s velocities, r=2 mm, xi=1 mm, dt=1/60 s, 20 XPBD iterations"),
     "cloth_stack_128": (lambda seed: S.cloth_stack(n_side=128, seed=seed),
                         "profiling case of the stack recipe: 4 layers of 128x128 cloth (65,536 verts)"),
+    "wires_64": (lambda seed: S.wires(n_grid=64, seed=seed),
+                 "profiling case of the wires recipe: 64x64 strands (266,240 verts) over the grate"),
     "cloth_on_sphere": (lambda seed: S.cloth_on_sphere(seed=seed),
                         "32x32 cloth (1,024 verts) on a static 4,000-tri sphere, 10 iterations"),
     "batch": (None, "512 independent scenes, sizes lognormal(ln 8192, ln 2) in [1k, 64k] verts: 80% cloths "
@@ -169,6 +171,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--requests", type=int, default=10000, help="serve: number of step requests")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--slots", type=int, default=8, help="serve: concurrent steps")
@@ -201,6 +204,9 @@ def main():
     v = torch.as_tensor(sc.v).cuda().contiguous()
     ctx = ccfr.Context.from_scene(sc)
     stream = torch.cuda.current_stream()
+    tuning = None
+    if not args.no_autotune:
+        tuning, tuned_ms = ctx.autotune(x, v, steps=1, plane_capacity=ctx.capacity)
 
     for _ in range(max(args.warmup, 0)):
         ctx.step(x, v)
@@ -323,7 +329,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": args.workload, "description": desc, "verts": N, "movable": sc.n_movable,
                        "edges": E, "tris": T, "iters_per_step": iters, "iters_run_per_step": iters_run,
-                       "plane_capacity": ctx.capacity, "parallelism": f"replicas x{ws}",
+                       "plane_capacity": ctx.capacity, "parallelism": f"replicas x{ws}", "tuning": tuning,
                        "l2": "inputs larger than L2 (plane lists %.1f GB)" % (N * ctx.capacity * 16 / 1e9)},
             "roofline": roofline,
             "cpu_baseline": cpu,

@@ -241,8 +241,9 @@ typedef struct {
 ccfr_status ccfr_set_tuning(ccfr_ctx* ctx, const ccfr_tuning* t);
 ccfr_status ccfr_get_tuning(const ccfr_ctx* ctx, ccfr_tuning* t);
 
-/* Autotuner: sets the plane capacity to 1.5x the largest per-vertex plane
- * count at x (+32), then times `steps` substeps from a scratch copy of
+/* Autotuner: sets the plane capacity (best->plane_capacity on input: 0 =
+ * choose 1.5x the largest per-vertex plane count at x, +32; otherwise keep
+ * that value), then times `steps` substeps from a scratch copy of
  * (x, v) for every cell factor in {1, 1.5, 2, 3} and emission grid in {4, 8,
  * 16} blocks per SM, and keeps the fastest.  x, v (device) are not modified.
  * Allocates two scratch vectors for the duration of the call.  best receives

@@ -256,8 +256,9 @@ class Context:
         _check(lib().ccfr_get_tuning(self.h, C.byref(t)), "ccfr_get_tuning")
         return t.as_dict()
 
-    def autotune(self, x, v, steps: int = 1, stream=None) -> tuple[dict, float]:
-        t = Tuning()
+    def autotune(self, x, v, steps: int = 1, plane_capacity: int = 0, stream=None) -> tuple[dict, float]:
+        """Pick cell size and emission grid (and the capacity when plane_capacity is 0)."""
+        t = Tuning(0.0, 0, plane_capacity)
         ms = C.c_double()
         _check(lib().ccfr_autotune(self.h, _ptr(x), _ptr(v), steps, C.byref(t), C.byref(ms), _stream(stream)),
                "ccfr_autotune")

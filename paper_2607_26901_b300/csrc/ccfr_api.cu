@@ -655,19 +655,25 @@ ccfr_status ccfr_autotune(ccfr_ctx* c, const float* x, const float* v, int steps
     cudaStream_t st = (cudaStream_t)stream;
     const int N = c->dc.n_verts;
     size_t bytes = (size_t)(N > 0 ? N : 1) * sizeof(float4);
-    // 1. plane capacity: 1.5 x the largest per-vertex count at x (counts are exact beyond the capacity)
-    ccfr_status s = ccfr_build_regions(c, x, stream);
-    if (s != CCFR_OK) return s;
-    std::vector<unsigned> cnt((size_t)N);
-    if (N && cudaMemcpyAsync(cnt.data(), c->dc.count, (size_t)N * sizeof(unsigned), cudaMemcpyDeviceToHost, st) !=
-                 cudaSuccess)
-        return CCFR_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return CCFR_ERR_CUDA;
-    unsigned mx = 0;
-    for (unsigned k : cnt) mx = k > mx ? k : mx;
-    int K = (int)((mx * 3u / 2u + 32u + 31u) / 32u * 32u);
-    if (K < 64) K = 64;
-    if (K > 65536) K = 65536;
+    // 1. plane capacity: as given, or 1.5 x the largest per-vertex count at x
+    //    (counts are exact beyond the capacity)
+    int K = best->plane_capacity;
+    ccfr_status s = CCFR_OK;
+    if (K != 0 && (K < 32 || K % 32 || K > 65536)) return CCFR_ERR_INVALID_ARG;
+    if (K == 0) {
+        s = ccfr_build_regions(c, x, stream);
+        if (s != CCFR_OK) return s;
+        std::vector<unsigned> cnt((size_t)N);
+        if (N && cudaMemcpyAsync(cnt.data(), c->dc.count, (size_t)N * sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                 st) != cudaSuccess)
+            return CCFR_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return CCFR_ERR_CUDA;
+        unsigned mx = 0;
+        for (unsigned k : cnt) mx = k > mx ? k : mx;
+        K = (int)((mx * 3u / 2u + 32u + 31u) / 32u * 32u);
+        if (K < 64) K = 64;
+        if (K > 65536) K = 65536;
+    }
     ccfr_tuning t{};
     t.plane_capacity = K;
     s = ccfr_set_tuning(c, &t);

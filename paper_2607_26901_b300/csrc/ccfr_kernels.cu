@@ -1295,6 +1295,32 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                 __syncwarp();
                 if (m > SCAP || np > 65535) break;
                 if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
+                if (m <= 32) {
+                    // one candidate per lane: rank by the full order (key, plane bits, slot)
+                    Tup me = {~0ull, ~0ull, ~0ull};
+                    unsigned short jj = 0;
+                    if (lane < m) {
+                        jj = sb.idx[0][lane];
+                        const float4 P = pl[jj];
+                        me.a = ((u64)sb.key[0][lane] << 32) | f2ord(P.w);
+                        me.b = ((u64)f2ord(P.x) << 32) | f2ord(P.y);
+                        me.c = ((u64)f2ord(P.z) << 32) | (unsigned)jj;
+                    }
+                    int rank = 0;
+                    for (int t = 0; t < m; ++t) {
+                        Tup o;
+                        o.a = __shfl_sync(FULL, me.a, t);
+                        o.b = __shfl_sync(FULL, me.b, t);
+                        o.c = __shfl_sync(FULL, me.c, t);
+                        rank += tless(o, me) ? 1 : 0;
+                    }
+                    __syncwarp();
+                    if (lane < m) {
+                        sb.key[0][rank] = (unsigned)(me.a >> 32);
+                        sb.idx[0][rank] = jj;
+                    }
+                    __syncwarp();
+                } else {
                 warp_radix_sort(sb, m, lane);
                 // equal keys on distinct planes: order by the plane itself (rare; one
                 // lane).  Bitwise-identical planes act identically in any order.
@@ -1321,6 +1347,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                         }
                     }
                     __syncwarp();
+                }
                 }
                 int nvp = sorted_pass(c, lane, sb, m, pl, ypass, ynext, Dmax);
                 __syncwarp();

@@ -1,0 +1,85 @@
+"""Full-size checks, in the launch configuration bench.py times (one context
+per scene, default tuning): the 262,144-vertex cloth stack and the
+1,201,202-vertex wires.  The oracle cannot run these whole, so (a) properties
+that hold at any size are checked on every vertex, and (b) sampled vertices
+are projected by the oracle on the GPU's own planes and compared within
+1e-5 L (band cases excluded, as in the small parity tests)."""
+import numpy as np
+import pytest
+
+from paper_2607_26901_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26901_b300 import ccfr  # noqa: E402
+
+TOL_REL = 1e-5
+BAND_REL = 1e-7
+
+
+@pytest.fixture(scope="module", params=["cloth_stack", "wires"])
+def full(request):
+    sc = S.config(2) if request.param == "cloth_stack" else S.config(3)
+    x = torch.as_tensor(sc.x).cuda().contiguous()
+    v = torch.as_tensor(sc.v).cuda().contiguous()
+    ctx = ccfr.Context.from_scene(sc)
+    ctx.step(x, v)                 # one full substep in the bench configuration
+    st = ctx.stats()
+    yield sc, ctx, x, v, st
+    ctx.close()
+
+
+def test_full_step_properties(full):
+    sc, ctx, x, v, st = full
+    assert st["status"] == 0 and st["error_flags"] == 0
+    assert st["iterations"] == sc.params["iters"] and st["planes"] > 0
+    xs = x.cpu().numpy()
+    assert np.all(np.isfinite(xs))
+    static = sc.x[:, 3] == 0
+    np.testing.assert_array_equal(xs[static], sc.x[static])           # obstacles never move
+    # per-iteration step bound: a substep moves a vertex at most iters * r
+    d = np.linalg.norm(xs[:, :3].astype(np.float64) - sc.x[:, :3], axis=1)
+    assert d.max() <= sc.params["iters"] * sc.params["r"] * (1 + 1e-5)
+
+
+def test_full_regions_and_sampled_projection(full, orc):
+    sc, ctx, x, v, st = full
+    L = orc.scene_scale(x.cpu().numpy())
+    ctx.build_regions(x)
+    reg = ctx.regions()
+    count = reg["count"].cpu().numpy()
+    K = ctx.capacity
+    assert count.max() > 0
+    rng = np.random.default_rng(7)
+    mov = np.nonzero((sc.x[:, 3] > 0) & (count > 0) & (count <= K))[0]
+    sample = rng.choice(mov, size=min(400, len(mov)), replace=False)
+    planes = reg["planes"][torch.as_tensor(sample).cuda()].cpu().numpy().astype(np.float64)
+    # (a) every stored plane of the sample is a unit normal with a finite offset
+    for i, vtx in enumerate(sample):
+        p = planes[i, :count[vtx]]
+        assert np.all(np.abs(np.linalg.norm(p[:, :3], axis=1) - 1) < 1e-5)
+        assert np.all(np.isfinite(p[:, 3]))
+    # (b) GPU projection vs the oracle's Alg. 2 on the same planes, sampled vertices
+    xg = x.clone()
+    noise = torch.as_tensor(rng.normal(scale=0.6 * sc.params["r"], size=(sc.n_verts, 3)).astype(np.float32)).cuda()
+    xg[:, :3] += noise * (xg[:, 3:4] > 0)
+    xio = xg.clone()
+    ctx.project(x, xio)
+    got = xio.cpu().numpy()[sample, :3].astype(np.float64)
+    xb = x.cpu().numpy()[sample, :3].astype(np.float64)
+    xp = xg.cpu().numpy()[sample, :3].astype(np.float64)
+    offs = np.concatenate([[0], np.cumsum(count[sample])]).astype(np.int64)
+    flat = np.concatenate([planes[i, :count[vtx]] for i, vtx in enumerate(sample)])
+    keys = np.arange(len(flat), dtype=np.uint64)       # ties broken by slot, as on the GPU
+    P = orc.make_params(sc.params, band=BAND_REL * L, capacity=0)
+    out, halt, band, nviol = orc.project(xb, xp, np.ones(len(sample)), offs, flat, keys, None, P)
+    ok = band == 0
+    err = np.abs(got - out).max(axis=1)
+    assert (nviol > 0).sum() > 0
+    assert ok.mean() > 0.3 and ok.sum() >= 100
+    bad = np.nonzero(ok & (err > TOL_REL * L))[0]
+    assert len(bad) <= max(1, int(0.005 * len(sample))), [(int(sample[b]), float(err[b])) for b in bad[:5]]
