@@ -347,7 +347,7 @@ def main():
                                "proj_smem_passes": st["aux"][0] / per_iter, "proj_full_passes": st["aux"][1] / per_iter,
                                "proj_violated_planes": st["aux"][2] / per_iter, "big_tris": st["aux"][3] / per_iter,
                                "big_edges": st["aux"][4] / per_iter, "proj_retries": st["aux"][5] / per_iter,
-                               "proj_heavy_planes": planes_q},
+                               "proj_heavy_planes": planes_q, "proj_sorted_planes": st["aux"][7] / per_iter},
             "kernel_sha": kernel_sha(),
         }
         print(json.dumps(line), flush=True)

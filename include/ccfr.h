@@ -104,7 +104,8 @@ typedef struct {
                                                          planes processed, [3] oversized
                                                          triangles, [4] oversized edges,
                                                          [5] candidate-list retries, [6]
-                                                         planes of the violated vertices     */
+                                                         planes of the violated vertices,
+                                                         [7] candidate planes sorted       */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
 } ccfr_stats;

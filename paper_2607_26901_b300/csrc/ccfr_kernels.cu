@@ -774,7 +774,9 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
 // centred at the pass start x^(0), so that the auxiliary point w starts at the
 // normal itself.  Alg. 1 divides by the dependence measures beta; with nearly
 // dependent planes (beta ~ 1e-3) binary32 would lose the result's accuracy, and
-// the step runs at most three times per pass, so it is done in FP64.
+// the step runs at most three times per pass, so it is done in FP64.  The FP64
+// pipe is a small fraction of the binary32 rate, so everything around the step
+// (plane tests, retraction, bookkeeping of the iterate) stays in binary32.
 struct d3 { double x, y, z; };
 __device__ __forceinline__ d3 dk(double x, double y, double z) { d3 r; r.x = x; r.y = y; r.z = z; return r; }
 __device__ __forceinline__ d3 dsub(d3 a, d3 b) { return dk(a.x - b.x, a.y - b.y, a.z - b.z); }
@@ -796,23 +798,29 @@ __device__ __forceinline__ void ero_push(Ero& S, d3 v, d3 n, double b) {
     if (S.m < 3) { S.V[S.m] = v; S.A[S.m] = n; S.B[S.m] = b; S.m++; }
 }
 
-// One Alg. 1 step: project zt onto the intersection of the stored hyperplanes
-// and n . z = b.
+// a / b for |b| >= eps_dep: a binary32 reciprocal estimate (relative error
+// below 2^-21) refined by one Newton-Raphson step r <- r + r (1 - b r) in
+// FP64, which squares the relative error (< 2^-42); the quotient is then
+// a r.  Far cheaper on the FP64 pipe than an IEEE division, and well inside
+// the accuracy Alg. 1 needs.
+__device__ __forceinline__ double div_nr(double a, double b) {
+    double r = (double)__fdividef(1.f, (float)b);
+    r = fma(r, fma(-b, r, 1.0), r);
+    return a * r;
+}
+
+// One Alg. 1 step with |V| >= 1 stored lines: project zt onto the
+// intersection of the stored hyperplanes and n . z = b.  (The first step, onto
+// a single plane, is taken in binary32 by the caller.)  The |v| > eps_dep
+// test compares squares (no square root).
 __device__ __noinline__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double eps) {
-    if (S.m == 0) {
-        double beta0 = ddot(n, n);
-        if (fabs(beta0) < eps) return;
-        zt = daxpy((b - ddot(n, zt)) / beta0, n, zt);
-        ero_push(S, n, n, b);
-        return;
-    }
     const int m = S.m;
     const d3 n0 = S.A[0];
     const double b0 = S.B[0];
     const d3 vm = S.V[m - 1];
     double beta_u = ddot(dsub(n, n0), vm);
     if (fabs(beta_u) < eps) return;
-    d3 u = daxpy((b - ddot(n, zt)) / beta_u, vm, zt);
+    d3 u = daxpy(div_nr(b - ddot(n, zt), beta_u), vm, zt);
     d3 w = n;
     #pragma unroll
     for (int j = 1; j <= 2; ++j) {
@@ -821,27 +829,124 @@ __device__ __noinline__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double e
         double bj = (j < m) ? S.B[j] : b;
         d3 dnj = dsub(nj, n0);
         double beta_w = ddot(dnj, S.V[j - 1]);
-        if (fabs(beta_w) > eps) w = daxpy((bj - b0 - ddot(dnj, w)) / beta_w, S.V[j - 1], w);
+        if (fabs(beta_w) > eps) w = daxpy(div_nr(bj - b0 - ddot(dnj, w), beta_w), S.V[j - 1], w);
     }
     d3 vn = dsub(w, u);
-    if (dlen(vn) > eps) {
+    if (ddot(vn, vn) > eps * eps) {
         double beta_new = ddot(n0, vn);
-        zt = (fabs(beta_new) < eps) ? u : daxpy((b0 - ddot(n0, u)) / beta_new, vn, u);
+        zt = (fabs(beta_new) < eps) ? u : daxpy(div_nr(b0 - ddot(n0, u), beta_new), vn, u);
         ero_push(S, vn, n, b);
     }
 }
 
-// Sort tuple of a plane: rho at the pass input (Alg. 2 sorts once), then the
-// plane's own bits and slot, so that equal keys break ties deterministically.
-struct Tup { u64 a, b, c; };
-__device__ __forceinline__ bool tless(const Tup& x, const Tup& y) {
-    return x.a < y.a || (x.a == y.a && (x.b < y.b || (x.b == y.b && x.c < y.c)));
+__device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
+
+// One pass of Alg. 2 in progress: the pass input, the binary32 iterate y
+// (offset from the build position), the largest squared distance of y from
+// the pass input so far, the number of violated planes met and the ERO state.
+// The first Alg. 1 step of a pass (|V| = 0) is a plain orthogonal projection
+// onto one plane, with no division by a dependence measure: it runs in
+// binary32 (as accurate as the binary32 iterate it produces), and its FP64 ERO
+// entry is formed from the stored plane P0 only when a second step needs it.
+struct Walk {
+    f3 ypass, y;
+    float dmax2;
+    int nv;
+    bool lazy0;
+    float4 P0;
+    Ero S;
+};
+
+__device__ __forceinline__ void walk_begin(Walk& W, f3 ypass) {
+    W.ypass = ypass;
+    W.y = ypass;
+    W.dmax2 = 0.f;
+    W.nv = 0;
+    W.lazy0 = false;
+    W.S.m = 0;
 }
-__device__ __forceinline__ Tup make_tup(float key, float4 P, int j) {
+
+// A plane violated at the current iterate: Alg. 1 (while |V| < 3), then the
+// retraction by eps towards the build position (Sec. 3.2).  Steps with
+// |V| >= 1 work in FP64 on z = y - ypass (exact in FP64), the plane written
+// n . z = b with b = -d - n . ypass, and round their result once to binary32;
+// with |V| = 3 the iterate only retracts, in binary32.  A binary32 scaling is
+// accurate to ~u |y| here (no cancellation).
+__device__ __forceinline__ void walk_visit(Walk& W, float4 P, float eps, double eps_dep) {
+    ++W.nv;
+    if (W.S.m == 0) {
+        const f3 n = xyz(P);
+        const float beta0 = dot(n, n);
+        if (!(fabsf(beta0) < (float)eps_dep)) {
+            W.y = sub(W.y, mul(n, rho_at(W.y, P) / beta0));
+            W.P0 = P;
+            W.lazy0 = true;
+            W.S.m = 1;
+        }
+    } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
+        // (a normal equal to the first line's gives beta_u = (n - n0) . v = 0
+        // exactly, and Alg. 1 leaves the iterate unchanged: skipped)
+        const d3 yp = d_of(W.ypass);
+        if (W.lazy0) {
+            const d3 n0 = dk(W.P0.x, W.P0.y, W.P0.z);
+            W.S.V[0] = n0;
+            W.S.A[0] = n0;
+            W.S.B[0] = -(double)W.P0.w - ddot(n0, yp);
+            W.lazy0 = false;
+        }
+        const d3 nrm = dk(P.x, P.y, P.z);
+        const double bz = -(double)P.w - ddot(nrm, yp);
+        d3 zt = dsub(d_of(W.y), yp);
+        ortho_step(zt, nrm, bz, W.S, eps_dep);
+        W.y = f_of(dadd(yp, zt));
+    }
+    const float L = len(W.y);
+    W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
+    const f3 dz = sub(W.y, W.ypass);
+    W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
+}
+
+// 16-bit hash of a plane's bits: the second sort key, which splits runs of
+// equal rho keys on distinct planes (near-duplicate contacts reached through
+// several pairs) without a comparison sort.  Any fixed function of the bits
+// gives a deterministic order; this one is a multiply-xorshift mix.
+__device__ __forceinline__ unsigned plane_hash16(float4 P) {
+    unsigned h = __float_as_uint(P.x) * 0x9E3779B1u + __float_as_uint(P.y) * 0x85EBCA77u +
+                 __float_as_uint(P.z) * 0xC2B2AE3Du + __float_as_uint(P.w) * 0x27D4EB2Fu;
+    h ^= h >> 15;
+    h *= 0x2C1B3C6Du;
+    h ^= h >> 13;
+    return h & 0xFFFFu;
+}
+
+// Order of the planes in a pass of Alg. 2: the sort key (rho at the first
+// pass input; Alg. 2 sorts once), then the plane hash, the plane's own bits
+// (d, n) and its slot, so that equal keys break ties deterministically and
+// independently of the order in which the planes were stored.
+struct Tup { u64 a, b, c; unsigned d; };
+__device__ __forceinline__ bool tless(const Tup& x, const Tup& y) {
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    if (x.c != y.c) return x.c < y.c;
+    return x.d < y.d;
+}
+__device__ __forceinline__ Tup make_tup_ord(unsigned key_ord, float4 P, int j) {
     Tup t;
-    t.a = ((u64)f2ord(key) << 32) | f2ord(P.w);
-    t.b = ((u64)f2ord(P.x) << 32) | f2ord(P.y);
-    t.c = ((u64)f2ord(P.z) << 32) | (unsigned)j;
+    t.a = ((u64)key_ord << 32) | plane_hash16(P);
+    t.b = ((u64)f2ord(P.w) << 32) | f2ord(P.x);
+    t.c = ((u64)f2ord(P.y) << 32) | f2ord(P.z);
+    t.d = (unsigned)j;
+    return t;
+}
+__device__ __forceinline__ Tup make_tup(float key, float4 P, int j) { return make_tup_ord(f2ord(key), P, j); }
+__device__ __forceinline__ float4 tup_plane(const Tup& t) {
+    return make_float4(ord2f((unsigned)t.b), ord2f((unsigned)(t.c >> 32)), ord2f((unsigned)t.c),
+                       ord2f((unsigned)(t.b >> 32)));
+}
+__device__ __forceinline__ Tup tup_none() {
+    Tup t;
+    t.a = t.b = t.c = ~0ull;
+    t.d = ~0u;
     return t;
 }
 
@@ -853,7 +958,7 @@ __device__ __forceinline__ f3 clamp_len(f3 y, float lim) {
 
 struct BlockCounters {
     unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry;
-    unsigned long long planes, heavy_planes;
+    unsigned long long planes, heavy_planes, sorted;
 };
 
 // Per-warp shared memory of the projection: the candidate planes of a pass
@@ -868,7 +973,6 @@ struct SortBuf {
 };
 constexpr size_t PROJ_SMEM = PROJ_WARPS * sizeof(SortBuf);
 
-__device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
 
 __device__ __forceinline__ Tup warp_min_tup(Tup best) {
     #pragma unroll
@@ -877,6 +981,7 @@ __device__ __forceinline__ Tup warp_min_tup(Tup best) {
         t.a = __shfl_xor_sync(FULL, best.a, o);
         t.b = __shfl_xor_sync(FULL, best.b, o);
         t.c = __shfl_xor_sync(FULL, best.c, o);
+        t.d = __shfl_xor_sync(FULL, best.d, o);
         if (tless(t, best)) best = t;
     }
     return best;
@@ -894,112 +999,109 @@ __device__ __forceinline__ float warp_max(float v) {
 }
 
 // One pass of Alg. 2 from the pass input ypass: visit the planes in ascending
-// order of the sort key (rho at the first input y0, then the plane's bits and
-// slot), call Alg. 1 on each plane violated at the current iterate and
+// order of the sort key (rho at the first input y0, then the plane's own bits
+// and slot), call Alg. 1 on each plane violated at the current iterate and
 // retract by eps towards the build position.  `get(e, P, key, j)` yields
-// source entry e of n.  Returns the number of violated planes; zt receives the
-// iterate in coordinates centred at ypass and Dmax the largest |zt| reached.
+// source entry e of n.  Returns the number of violated planes; y_out receives
+// the pass result and Dmax the largest distance of the iterate from ypass.
 template <typename Get>
 __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get get, f3 ypass, f3& y_out, float& Dmax) {
-    d3 zt = dk(0.0, 0.0, 0.0);
-    const d3 yp = d_of(ypass);
-    Dmax = 0.f;
-    Ero S;
-    S.m = 0;
-    int nv = 0;
-    Tup cur = {0ull, 0ull, 0ull};
+    Walk W;
+    walk_begin(W, ypass);
+    Tup cur;
+    cur.a = cur.b = cur.c = 0ull;
+    cur.d = 0u;
+    bool first = true;
     for (int it = 0; it <= n; ++it) {
-        f3 yt = f_of(dadd(yp, zt));
-        Tup best = {~0ull, ~0ull, ~0ull};
+        Tup best = tup_none();
         for (int e = lane; e < n; e += 32) {
             float4 P;
             float key;
             int j;
             get(e, P, key, j);
-            if (rho_at(yt, P) < 0.f) {
+            if (rho_at(W.y, P) < 0.f) {
                 Tup t = make_tup(key, P, j);
-                if (tless(cur, t) && tless(t, best)) best = t;
+                if ((first || tless(cur, t)) && tless(t, best)) best = t;
             }
         }
         best = warp_min_tup(best);
-        if (best.a == ~0ull) break;
+        if (best.d == ~0u) break;
         cur = best;
-        ++nv;
-        d3 nrm = dk(ord2f((unsigned)(best.b >> 32)), ord2f((unsigned)best.b), ord2f((unsigned)(best.c >> 32)));
-        double d = ord2f((unsigned)best.a);
-        // the plane n . y = -d in coordinates centred at the pass input
-        double bz = -d - ddot(nrm, yp);
-        if (S.m < 3) ortho_step(zt, nrm, bz, S, (double)c.p.eps_dep);
-        // retraction by eps towards the build position (Sec. 3.2); a binary32
-        // scaling is accurate to ~u |y| here (no cancellation), so only the
-        // Alg. 1 step above runs in FP64
-        f3 yn = f_of(dadd(yp, zt));
-        float L = len(yn);
-        yn = (L > c.p.eps) ? mul(yn, (L - c.p.eps) / L) : mk(0.f, 0.f, 0.f);
-        zt = dsub(d_of(yn), yp);
-        Dmax = fmaxf(Dmax, len(sub(yn, ypass)));
+        first = false;
+        const float4 P = tup_plane(best);
+        walk_visit(W, P, c.p.eps, (double)c.p.eps_dep);
     }
-    y_out = f_of(dadd(yp, zt));
-    return nv;
+    y_out = W.y;
+    Dmax = sqrtf(W.dmax2);
+    return W.nv;
 }
 
-// Stable LSD radix sort (four 8-bit digits) of n (key, slot) pairs held in
-// buffer 0, by one warp; the result is in buffer 0.  Equal digits keep their
-// relative order (ranks from __match_any_sync within each 32-entry chunk).
-__device__ void warp_radix_sort(SortBuf& sb, int n, int lane) {
-    int src = 0;
+// One stable counting pass of a warp LSD radix sort over n (key, slot) pairs
+// from buffer src into buffer src ^ 1, on the 8-bit digit dig(key, slot).
+// Equal digits keep their relative order: ranks within each 32-entry chunk
+// come from the intersection of the eight bit-slice ballots.
+template <typename Dig>
+__device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src, Dig dig) {
     const unsigned lt = (1u << lane) - 1u;
-    for (int shift = 0; shift < 32; shift += 8) {
-        for (int b = lane; b < 256; b += 32) sb.hist[b] = 0u;
-        __syncwarp();
-        for (int i = lane; i < n; i += 32) atomicAdd(&sb.hist[(sb.key[src][i] >> shift) & 255u], 1u);
-        __syncwarp();
-        // exclusive scan of the 256 bins, 8 per lane
-        unsigned loc[8], tot = 0;
-        #pragma unroll
-        for (int k = 0; k < 8; ++k) { loc[k] = sb.hist[lane * 8 + k]; tot += loc[k]; }
-        unsigned inc = tot;
-        #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned t = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += t;
-        }
-        unsigned off = inc - tot;
-        __syncwarp();
-        #pragma unroll
-        for (int k = 0; k < 8; ++k) { sb.hist[lane * 8 + k] = off; off += loc[k]; }
-        __syncwarp();
-        for (int base = 0; base < n; base += 32) {
-            const int i = base + lane;
-            const bool valid = i < n;
-            const unsigned k = valid ? sb.key[src][i] : 0u;
-            const unsigned short j = valid ? sb.idx[src][i] : 0;
-            const unsigned dg = valid ? ((k >> shift) & 255u) : 256u;
-            // lanes holding the same digit: intersect the eight bit-slice ballots
-            unsigned peers = __ballot_sync(FULL, valid) ;
-            if (!valid) peers = ~peers;
-            #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const unsigned bit = __ballot_sync(FULL, (dg >> b) & 1u);
-                peers &= ((dg >> b) & 1u) ? bit : ~bit;
-            }
-            const unsigned start = valid ? sb.hist[dg] : 0u;
-            __syncwarp();
-            if (valid) {
-                const unsigned dst = start + __popc(peers & lt);
-                sb.key[src ^ 1][dst] = k;
-                sb.idx[src ^ 1][dst] = j;
-                if ((peers & lt) == 0u) sb.hist[dg] = start + __popc(peers);
-            }
-            __syncwarp();
-        }
-        src ^= 1;
+    for (int b = lane; b < 256; b += 32) sb.hist[b] = 0u;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) atomicAdd(&sb.hist[dig(sb.key[src][i], sb.idx[src][i])], 1u);
+    __syncwarp();
+    // exclusive scan of the 256 bins, 8 per lane
+    unsigned loc[8], tot = 0;
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) { loc[k] = sb.hist[lane * 8 + k]; tot += loc[k]; }
+    unsigned inc = tot;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
     }
-    // four passes: the sorted data is back in buffer 0
+    unsigned off = inc - tot;
+    __syncwarp();
+    #pragma unroll
+    for (int k = 0; k < 8; ++k) { sb.hist[lane * 8 + k] = off; off += loc[k]; }
+    __syncwarp();
+    for (int base = 0; base < n; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < n;
+        const unsigned k = valid ? sb.key[src][i] : 0u;
+        const unsigned short j = valid ? sb.idx[src][i] : 0;
+        const unsigned dg = valid ? dig(k, j) : 256u;
+        // lanes holding the same digit: intersect the eight bit-slice ballots
+        unsigned peers = __ballot_sync(FULL, valid);
+        if (!valid) peers = ~peers;
+        #pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned bit = __ballot_sync(FULL, (dg >> b) & 1u);
+            peers &= ((dg >> b) & 1u) ? bit : ~bit;
+        }
+        const unsigned start = valid ? sb.hist[dg] : 0u;
+        __syncwarp();
+        if (valid) {
+            const unsigned dst = start + __popc(peers & lt);
+            sb.key[src ^ 1][dst] = k;
+            sb.idx[src ^ 1][dst] = j;
+            if ((peers & lt) == 0u) sb.hist[dg] = start + __popc(peers);
+        }
+        __syncwarp();
+    }
 }
 
-// Plane order of Alg. 2 among equal sort keys: the plane's own bits and its
-// slot (identical planes may go in any order; distinct ones need a fixed one).
+// Stable LSD radix sort by (rho key, plane hash) of the n pairs in buffer 0,
+// which arrive in slot order: two passes on the hash, then four on the key.
+// Six passes: the sorted data is back in buffer 0, ordered by (key, hash, slot).
+__device__ void warp_radix_sort(SortBuf& sb, int n, int lane, const float4* pl) {
+    int src = 0;
+    for (int shift = 0; shift < 16; shift += 8, src ^= 1)
+        radix_pass(sb, n, lane, src, [&](unsigned, unsigned short j) { return (plane_hash16(pl[j]) >> shift) & 255u; });
+    for (int shift = 0; shift < 32; shift += 8, src ^= 1)
+        radix_pass(sb, n, lane, src, [&](unsigned k, unsigned short) { return (k >> shift) & 255u; });
+}
+
+// Plane order of Alg. 2 among equal (key, hash): the plane's own bits (d, n)
+// and its slot, as in tless (identical planes may go in any order; distinct
+// ones need a fixed one).
 __device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
     float4 A = pl[a], B = pl[b];
     unsigned x0 = f2ord(A.w), y0 = f2ord(B.w);
@@ -1014,44 +1116,31 @@ __device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
 }
 
 // One pass of Alg. 2 over the sorted candidates sb.key/idx[0][0..m): walk
-// the list in order, 32 planes per step; the first violated plane of a step
-// is handled (Alg. 1 + retraction) and the walk resumes right after it.
+// the list in order, 32 planes per chunk held one per lane; the first plane of
+// the chunk violated at the current iterate is handled (Alg. 1 + retraction)
+// and the walk resumes with the chunk's later planes, tested at the new iterate.
 __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, const float4* pl, f3 ypass,
                            f3& y_out, float& Dmax) {
-    d3 zt = dk(0.0, 0.0, 0.0);
-    const d3 yp = d_of(ypass);
-    Dmax = 0.f;
-    Ero S;
-    S.m = 0;
-    int nv = 0;
-    f3 yt = ypass;
-    int pos = 0;
-    while (pos < m) {
+    Walk W;
+    walk_begin(W, ypass);
+    for (int pos = 0; pos < m; pos += 32) {
         const int e = pos + lane;
-        float4 P = make_float4(0.f, 0.f, 0.f, 0.f);
-        bool viol = false;
-        if (e < m) {
-            P = pl[sb.idx[0][e]];
-            viol = rho_at(yt, P) < 0.f;
+        const float4 P = (e < m) ? pl[sb.idx[0][e]] : make_float4(0.f, 0.f, 0.f, 0.f);
+        int lo = 0;   // lanes below lo are already behind the walk
+        for (;;) {
+            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f;
+            const unsigned bal = __ballot_sync(FULL, viol);
+            if (!bal) break;
+            const int f = __ffs(bal) - 1;
+            const float4 Pf = make_float4(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f),
+                                          __shfl_sync(FULL, P.z, f), __shfl_sync(FULL, P.w, f));
+            walk_visit(W, Pf, c.p.eps, (double)c.p.eps_dep);
+            lo = f + 1;
         }
-        const unsigned bal = __ballot_sync(FULL, viol);
-        if (!bal) { pos += 32; continue; }
-        const int f = __ffs(bal) - 1;
-        const d3 nrm = dk(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f), __shfl_sync(FULL, P.z, f));
-        const double d = __shfl_sync(FULL, P.w, f);
-        ++nv;
-        double bz = -d - ddot(nrm, yp);
-        if (S.m < 3) ortho_step(zt, nrm, bz, S, (double)c.p.eps_dep);
-        f3 yn = f_of(dadd(yp, zt));
-        float L = len(yn);
-        yn = (L > c.p.eps) ? mul(yn, (L - c.p.eps) / L) : mk(0.f, 0.f, 0.f);
-        zt = dsub(d_of(yn), yp);
-        Dmax = fmaxf(Dmax, len(sub(yn, ypass)));
-        yt = f_of(dadd(yp, zt));
-        pos += f + 1;
     }
-    y_out = f_of(dadd(yp, zt));
-    return nv;
+    y_out = W.y;
+    Dmax = sqrtf(W.dmax2);
+    return W.nv;
 }
 
 // Minimum of rho over a vertex's planes at y, and the largest |d|; four
@@ -1157,6 +1246,7 @@ __device__ __forceinline__ void flush_block_counters(const DevCtx& c, BlockCount
         if (bc.nviol) atomicAdd(&c.stats->aux[2], (u64)bc.nviol);
         if (bc.retry) atomicAdd(&c.stats->aux[5], (u64)bc.retry);
         if (bc.heavy_planes) atomicAdd(&c.stats->aux[6], bc.heavy_planes);
+        if (bc.sorted) atomicAdd(&c.stats->aux[7], bc.sorted);
     }
 }
 
@@ -1165,6 +1255,7 @@ __device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
         bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.smem_pass = bc.glob_pass = bc.nviol = bc.retry = 0u;
         bc.planes = 0ull;
         bc.heavy_planes = 0ull;
+        bc.sorted = 0ull;
     }
     __syncthreads();
 }
@@ -1297,14 +1388,11 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                 if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
                 if (m <= 32) {
                     // one candidate per lane: rank by the full order (key, plane bits, slot)
-                    Tup me = {~0ull, ~0ull, ~0ull};
+                    Tup me = tup_none();
                     unsigned short jj = 0;
                     if (lane < m) {
                         jj = sb.idx[0][lane];
-                        const float4 P = pl[jj];
-                        me.a = ((u64)sb.key[0][lane] << 32) | f2ord(P.w);
-                        me.b = ((u64)f2ord(P.x) << 32) | f2ord(P.y);
-                        me.c = ((u64)f2ord(P.z) << 32) | (unsigned)jj;
+                        me = make_tup_ord(sb.key[0][lane], pl[jj], jj);
                     }
                     int rank = 0;
                     for (int t = 0; t < m; ++t) {
@@ -1312,6 +1400,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                         o.a = __shfl_sync(FULL, me.a, t);
                         o.b = __shfl_sync(FULL, me.b, t);
                         o.c = __shfl_sync(FULL, me.c, t);
+                        o.d = __shfl_sync(FULL, me.d, t);
                         rank += tless(o, me) ? 1 : 0;
                     }
                     __syncwarp();
@@ -1321,34 +1410,42 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                     }
                     __syncwarp();
                 } else {
-                warp_radix_sort(sb, m, lane);
-                // equal keys on distinct planes: order by the plane itself (rare; one
-                // lane).  Bitwise-identical planes act identically in any order.
+                warp_radix_sort(sb, m, lane, pl);
+                // equal (key, hash) on distinct planes (a hash collision; rare): order
+                // each such run by the plane itself (its bits, then its slot).
+                // Bitwise-identical planes act identically in any order.  Runs are
+                // disjoint: each lane sorts the runs that start at its indices.
                 bool tie = false;
                 for (int i = lane; i + 1 < m; i += 32) {
                     if (sb.key[0][i] == sb.key[0][i + 1]) {
                         const float4 A = pl[sb.idx[0][i]], B = pl[sb.idx[0][i + 1]];
-                        tie |= !(A.x == B.x && A.y == B.y && A.z == B.z && A.w == B.w);
+                        tie |= !(A.x == B.x && A.y == B.y && A.z == B.z && A.w == B.w) &&
+                               plane_hash16(A) == plane_hash16(B);
                     }
                 }
                 if (__any_sync(FULL, tie)) {
-                    if (lane == 0) {
-                        for (int i = 1; i < m; ++i) {
-                            unsigned kk = sb.key[0][i];
-                            unsigned short jj = sb.idx[0][i];
-                            int q = i - 1;
-                            while (q >= 0 && sb.key[0][q] == kk && plane_less(pl, jj, sb.idx[0][q])) {
-                                sb.key[0][q + 1] = sb.key[0][q];
+                    auto same = [&](int i, int k) {
+                        return sb.key[0][i] == sb.key[0][k] &&
+                               plane_hash16(pl[sb.idx[0][i]]) == plane_hash16(pl[sb.idx[0][k]]);
+                    };
+                    for (int i = lane; i < m; i += 32) {
+                        if ((i > 0 && same(i - 1, i)) || i + 1 >= m || !same(i, i + 1)) continue;
+                        int e = i + 2;
+                        while (e < m && same(i, e)) ++e;
+                        for (int a = i + 1; a < e; ++a) {
+                            const unsigned short jj = sb.idx[0][a];
+                            int q = a - 1;
+                            while (q >= i && plane_less(pl, jj, sb.idx[0][q])) {
                                 sb.idx[0][q + 1] = sb.idx[0][q];
                                 --q;
                             }
-                            sb.key[0][q + 1] = kk;
                             sb.idx[0][q + 1] = jj;
                         }
                     }
                     __syncwarp();
                 }
                 }
+                if (lane == 0) atomicAdd(&bc.sorted, (unsigned long long)m);
                 int nvp = sorted_pass(c, lane, sb, m, pl, ypass, ynext, Dmax);
                 __syncwarp();
                 if (Dmax <= T - margin) {
