@@ -364,11 +364,28 @@ __device__ void closest_segments_fp64(float4 P1, float4 Q1, float4 P2, float4 Q2
     else if (t > 1.0) { t = 1.0; s = fmin(fmax((b - cc) / a, 0.0), 1.0); }
 }
 
+// Near-parallel edges: closest points in FP64 and their separation rounded
+// once to binary32.  Out of line: rare, and its FP64 registers would
+// otherwise count against the occupancy of the whole emission kernel.
+__device__ __noinline__ void near_parallel_fp64(const float4* __restrict__ x, int2 E, int2 F, f3& diff, float& s,
+                                                float& t) {
+    const float4 A0 = x[E.x], A1 = x[E.y], B0 = x[F.x], B1 = x[F.y];
+    double sd, td;
+    closest_segments_fp64(A0, A1, B0, B1, sd, td);
+    double ax = (double)A0.x + sd * ((double)A1.x - A0.x), ay = (double)A0.y + sd * ((double)A1.y - A0.y),
+           az = (double)A0.z + sd * ((double)A1.z - A0.z);
+    double bx = (double)B0.x + td * ((double)B1.x - B0.x), by = (double)B0.y + td * ((double)B1.y - B0.y),
+           bz = (double)B0.z + td * ((double)B1.z - B0.z);
+    diff = mk((float)(ax - bx), (float)(ay - by), (float)(az - bz));
+    s = (float)sd;
+    t = (float)td;
+}
+
 // Edge-edge pair (Alg. 3): e = (e0, e1) against f = (f0, f1), local
 // coordinates centred at e0.  Returns 1 if accepted; *fp64 is set when the
 // near-parallel FP64 solve was used.
-__device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A0, float4 A1, float4 B0,
-                         float4 B1, int& fp64) {
+__device__ int narrow_ee(const DevCtx& c, const float4* __restrict__ x, int e, int2 E, int f, int2 F, float4 A0,
+                         float4 A1, float4 B0, float4 B1, int& fp64) {
     const SceneParams sp = scene_params(c, scene_of(c, E.x));
     f3 o = xyz(A0);
     f3 d1 = sub(xyz(A1), o), p2 = sub(xyz(B0), o), d2 = sub(xyz(B1), xyz(B0));
@@ -399,16 +416,8 @@ __device__ int narrow_ee(const DevCtx& c, int e, int2 E, int f, int2 F, float4 A
             }
         }
     } else {
-        double sd, td;
-        closest_segments_fp64(A0, A1, B0, B1, sd, td);
+        near_parallel_fp64(x, E, F, diff, s, t);
         fp64 = 1;
-        double ax = (double)A0.x + sd * ((double)A1.x - A0.x), ay = (double)A0.y + sd * ((double)A1.y - A0.y),
-               az = (double)A0.z + sd * ((double)A1.z - A0.z);
-        double bx = (double)B0.x + td * ((double)B1.x - B0.x), by = (double)B0.y + td * ((double)B1.y - B0.y),
-               bz = (double)B0.z + td * ((double)B1.z - B0.z);
-        diff = mk((float)(ax - bx), (float)(ay - by), (float)(az - bz));
-        s = (float)sd;
-        t = (float)td;
     }
     float dist = len(diff);
     if (dist == 0.f) return 0;
@@ -512,8 +521,8 @@ __device__ __forceinline__ void process_pair(const DevCtx& c, const float4* __re
         int np = narrow_vf(c, v, P, t, T, A, B, C);
         k.acc += (np > 0);
         k.planes += np;
-    } else if (QK == KIND_EDGE) {                  // (edge, edge), e < f
-        int e = pr.x, f = pr.y;
+    } else if (QK == KIND_EDGE) {                  // (edge, edge), taken as e < f
+        const int e = min(pr.x, pr.y), f = max(pr.x, pr.y);
         int2 E = c.edges[e], F = c.edges[f];
         if (F.x == E.x || F.x == E.y || F.y == E.x || F.y == E.y) return;
         float4 A0 = x[E.x], A1 = x[E.y], B0 = x[F.x], B1 = x[F.y];
@@ -521,12 +530,12 @@ __device__ __forceinline__ void process_pair(const DevCtx& c, const float4* __re
         ++k.cand;
         if (MODE == MODE_PAIRS) { write_pair(po, 1, e, f); return; }
         int fp64 = 0;
-        int np = narrow_ee(c, e, E, f, F, A0, A1, B0, B1, fp64);
+        int np = narrow_ee(c, x, e, E, f, F, A0, A1, B0, B1, fp64);
         k.acc += (np > 0);
         k.planes += np;
         k.fp64 += fp64;
-    } else {                                       // (point, point), p < q
-        int p = pr.x, q = pr.y;
+    } else {                                       // (point, point), taken as p < q
+        const int p = min(pr.x, pr.y), q = max(pr.x, pr.y);
         float4 P = x[p], Q = x[q];
         if (!(P.w > 0.f || Q.w > 0.f)) return;
         ++k.cand;
@@ -537,21 +546,78 @@ __device__ __forceinline__ void process_pair(const DevCtx& c, const float4* __re
     }
 }
 
+// The items of up to 32 cells of one table, gathered across the warp.  Lane j
+// describes cell j (has: there is one; b: its bucket; pk: its tag).  The cells'
+// item lists are concatenated and dealt out 32 per round, item k to lane
+// k % 32, so that the loads of all cells are in flight together.  f(valid, i0,
+// i1, j) runs once per round on every lane; valid lanes hold an item of cell j
+// whose tag matches (other cells that share the bucket are skipped).  The
+// cells with has must come first.
+template <typename F>
+__device__ __forceinline__ void warp_cell_items(const DevCtx& c, int lane, bool has, unsigned b, unsigned pk, F f) {
+    unsigned t0 = 0, cnt = 0;
+    if (has) {
+        t0 = c.bucket_count[b];
+        cnt = c.bucket_count[b + 1] - t0;
+    }
+    unsigned inc = cnt;
+    #pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const unsigned total = __shfl_sync(FULL, inc, 31);
+    const unsigned excl = inc - cnt;
+    for (unsigned base = 0; base < total; base += 32) {
+        const unsigned k = base + (unsigned)lane;
+        // owner: the last cell whose list starts at or before k
+        int j = 0;
+        #pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const unsigned e = __shfl_sync(FULL, excl, min(j + step, 31));
+            if (j + step <= 31 && e <= k) j += step;
+        }
+        const unsigned tj = __shfl_sync(FULL, t0, j), ej = __shfl_sync(FULL, excl, j), pj = __shfl_sync(FULL, pk, j);
+        bool valid = k < total;
+        float4 i0 = make_float4(0.f, 0.f, 0.f, 0.f), i1 = i0;
+        if (valid) {
+            const unsigned s = tj + (k - ej);
+            i0 = c.rec[2 * s];
+            i1 = c.rec[2 * s + 1];
+            valid = __float_as_uint(i1.w) == pj;
+        }
+        f(valid, i0, i1, j);
+    }
+}
+
 // QK: query table (KIND_TRI: triangles against the vertex table, KIND_EDGE,
 // KIND_PT: against their own table).  Persistent warps stride over the units.
+// A table queried against itself needs only half of the neighbourhood: the
+// query's own cell (pairs taken from the smaller id) and the 13 cells after it
+// in (z, y, x) order find every pair of cells once.  The triangle queries scan
+// all 27 cells of the vertex table.  The items of the scanned cells are
+// gathered 32 at a time (warp_cell_items), compacted into shared memory and
+// tested by every query lane against one broadcast item at a time.
 template <int QK, int MODE>
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po) {
     if (c.flags[1]) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
+    __shared__ float4 items[EMIT_WARPS][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int2* q = queue[wib];
+    float4* it = items[wib];
     int qn = 0;
     EmitCounters k{0, 0, 0, 0};
+    constexpr bool HALF = QK != KIND_TRI;
+    constexpr int NOFF = HALF ? 14 : 27;
     const int IK = (QK == KIND_TRI) ? KIND_VQ : QK;
     const float inv = 1.0f / cell_size_of(c, QK);
     const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
     const unsigned nunits = c.unit_count[QK];
     const unsigned stride = gridDim.x * EMIT_WARPS;
+    // this lane's neighbour offset (cell order (z, y, x); index 13 is the cell itself)
+    const int oi = HALF ? 13 + lane : lane;
+    const int ox = oi % 3 - 1, oy = (oi / 3) % 3 - 1, oz = oi / 9 - 1;
     for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nunits; u += stride) {
         int2 U = c.units[c.unit_base[QK] + u];
         unsigned s0 = c.bucket_count[U.x] + (unsigned)U.y, s1 = c.bucket_count[U.x + 1];
@@ -573,36 +639,46 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4
             const unsigned cs = __shfl_sync(FULL, qs, leader);
             const bool in = ((pending >> lane) & 1u) && mx == cx && my == cy && mz == cz && qs == cs;
             pending &= ~__ballot_sync(FULL, in);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const unsigned b = ibase + (cell_hash(cx + dx, cy + dy, cz + dz, cs) & imask);
-                        const unsigned pk = cell_pack(cx + dx, cy + dy, cz + dz, cs);
-                        const unsigned t1 = c.bucket_count[b + 1];
-                        for (unsigned s = c.bucket_count[b]; s < t1; ++s) {
-                            const float4 i1 = c.rec[2 * s + 1];
-                            if (__float_as_uint(i1.w) != pk) continue;
-                            const float4 i0 = c.rec[2 * s];
-                            const int iid = __float_as_int(i0.w);
-                            bool hit = in && r0.x <= i1.x && i0.x <= r1.x && r0.y <= i1.y && i0.y <= r1.y &&
-                                       r0.z <= i1.z && i0.z <= r1.z;
-                            if (QK == KIND_TRI) hit = hit && iid != qt.x && iid != qt.y && iid != qt.z;
-                            else hit = hit && iid > qid;
-                            const unsigned hb = __ballot_sync(FULL, hit);
-                            if (!hb) continue;
-                            if (hit) q[qn + __popc(hb & ((1u << lane) - 1u))] = make_int2(qid, iid);
-                            qn += __popc(hb);
-                            if (qn >= 32) {
-                                __syncwarp();
-                                process_pair<QK, MODE>(c, x, po, q[lane], k);
-                                int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
-                                __syncwarp();
-                                if (lane < qn - 32) q[lane] = rest;
-                                qn -= 32;
-                                __syncwarp();
-                            }
-                        }
+            const bool has = lane < NOFF;
+            unsigned b = 0, pk = 0;
+            if (has) {
+                b = ibase + (cell_hash(cx + ox, cy + oy, cz + oz, cs) & imask);
+                pk = cell_pack(cx + ox, cy + oy, cz + oz, cs);
+            }
+            warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
+                // compact this round's items into shared memory; w = 1 marks the query's own cell
+                const unsigned vb = __ballot_sync(FULL, valid);
+                if (valid) {
+                    const int pos = __popc(vb & ((1u << lane) - 1u));
+                    i1.w = __int_as_float(HALF && j == 0 ? 1 : 0);
+                    it[2 * pos] = i0;
+                    it[2 * pos + 1] = i1;
+                }
+                __syncwarp();
+                const int nv = __popc(vb);
+                for (int v = 0; v < nv; ++v) {
+                    const float4 a0 = it[2 * v], a1 = it[2 * v + 1];
+                    const int iid = __float_as_int(a0.w);
+                    bool hit = in && r0.x <= a1.x && a0.x <= r1.x && r0.y <= a1.y && a0.y <= r1.y && r0.z <= a1.z &&
+                               a0.z <= r1.z;
+                    if (QK == KIND_TRI) hit = hit && iid != qt.x && iid != qt.y && iid != qt.z;
+                    else hit = hit && (__float_as_int(a1.w) == 0 || iid > qid);
+                    const unsigned hb = __ballot_sync(FULL, hit);
+                    if (!hb) continue;
+                    if (hit) q[qn + __popc(hb & ((1u << lane) - 1u))] = make_int2(qid, iid);
+                    qn += __popc(hb);
+                    if (qn >= 32) {
+                        __syncwarp();
+                        process_pair<QK, MODE>(c, x, po, q[lane], k);
+                        int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
+                        __syncwarp();
+                        if (lane < qn - 32) q[lane] = rest;
+                        qn -= 32;
+                        __syncwarp();
                     }
+                }
+                __syncwarp();
+            });
         }
     }
     __syncwarp();
@@ -712,23 +788,25 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                 push(pr.x >= 0, pr);
             }
         } else {
-            const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1, z0 = (int)fz0, z1 = (int)fz1;
-            for (int cz = z0; cz <= z1; ++cz)
-                for (int cy = y0; cy <= y1; ++cy)
-                    for (int cx = x0; cx <= x1; ++cx) {
-                        const unsigned b = ibase + (cell_hash(cx, cy, cz, qs) & imask);
-                        const unsigned pk = cell_pack(cx, cy, cz, qs);
-                        const unsigned t1 = c.bucket_count[b + 1];
-                        for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
-                            const unsigned s = s0 + lane;
-                            int2 pr = make_int2(-1, -1);
-                            if (s < t1) {
-                                const float4 i1 = c.rec[2 * s + 1];
-                                if (__float_as_uint(i1.w) == pk) pr = test(c.rec[2 * s], i1);
-                            }
-                            push(pr.x >= 0, pr);
-                        }
-                    }
+            // the reachable cells, 32 per round, their items gathered across the warp
+            const int x0 = (int)fx0, y0 = (int)fy0, z0 = (int)fz0;
+            const int nx = (int)fx1 - x0 + 1, ny = (int)fy1 - y0 + 1, nz = (int)fz1 - z0 + 1;
+            const int nc = nx * ny * nz;
+            for (int c0 = 0; c0 < nc; c0 += 32) {
+                const int ci = c0 + lane;
+                const bool has = ci < nc;
+                unsigned b = 0, pk = 0;
+                if (has) {
+                    const int cx = x0 + ci % nx, cy = y0 + (ci / nx) % ny, cz = z0 + ci / (nx * ny);
+                    b = ibase + (cell_hash(cx, cy, cz, qs) & imask);
+                    pk = cell_pack(cx, cy, cz, qs);
+                }
+                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
+                    int2 pr = make_int2(-1, -1);
+                    if (valid) pr = test(i0, i1);
+                    push(pr.x >= 0, pr);
+                });
+            }
         }
         if (QK == KIND_EDGE) {
             // oversized-oversized pairs, found from the smaller id in the table of
@@ -736,28 +814,23 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
             const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
             const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
-            for (int dz = -1; dz <= 1; ++dz)
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const unsigned b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
-                        const unsigned pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
-                        const unsigned t1 = c.bucket_count[b + 1];
-                        for (unsigned s0 = c.bucket_count[b]; s0 < t1; s0 += 32) {
-                            const unsigned s = s0 + lane;
-                            int2 pr = make_int2(-1, -1);
-                            if (s < t1) {
-                                const float4 i1 = c.rec[2 * s + 1];
-                                if (__float_as_uint(i1.w) == pk) {
-                                    const float4 i0 = c.rec[2 * s];
-                                    const int o2 = __float_as_int(i0.w);
-                                    if (o2 > o && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] &&
-                                        lo[2] <= i1.z && i0.z <= hi[2])
-                                        pr = make_int2(o, o2);
-                                }
-                            }
-                            push(pr.x >= 0, pr);
-                        }
-                    }
+            const bool has = lane < 27;
+            unsigned b = 0, pk = 0;
+            if (has) {
+                const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+                b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
+                pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
+            }
+            warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
+                int2 pr = make_int2(-1, -1);
+                if (valid) {
+                    const int o2 = __float_as_int(i0.w);
+                    if (o2 > o && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z &&
+                        i0.z <= hi[2])
+                        pr = make_int2(o, o2);
+                }
+                push(pr.x >= 0, pr);
+            });
         }
     }
     __syncwarp();
