@@ -257,7 +257,9 @@ def main():
     planes_stored = st["planes"] / per_iter
     n_pts = len(S.isolated_points(sc.x, sc.edges))
     # algorithmic bytes per launch (one launch per iteration), per kernel
-    n_q = st["violated_verts"] / per_iter          # vertices queued for the heavy projection
+    n_s = st["aux"][8] / per_iter                  # violated vertices with short plane lists
+    planes_s = st["aux"][9] / per_iter             # their planes
+    n_q = st["violated_verts"] / per_iter - n_s    # violated vertices with long lists
     planes_q = st["aux"][6] / per_iter             # their planes
     alg = {
         "emit_vf": 16 * N + 12 * T + 32 * T + 16 * planes_vf + 4 * N,
@@ -265,6 +267,7 @@ def main():
         "emit_pp": 16 * n_pts + 32 * n_pts + 16 * planes_vv,
         "project": 52 * N + 16 * planes_stored,
         "project_heavy": 52 * n_q + 16 * planes_q,
+        "project_short": 52 * n_s + 16 * planes_s,
         "xpbd": 8 * E + 4 * E + 4 * E * 2 + 2 * 16 * N,
         "grid_scatter": 16 * N + 8 * E + 12 * T + 32 * (T + E + n_pts),
     }
@@ -311,8 +314,8 @@ def main():
                "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": 2 * N * 16}
 
     n_emit = (2 if T > 0 else 0) + (2 if E > 0 else 0) + (1 if n_pts > 1 else 0)
-    # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours, 2 project, iter_end
-    launches_per_iter = 1 + 1 + 1 + 3 + 1 + 1 + n_emit + ctx.n_colors + 2 + 1  # noqa: E501
+    # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours, 3 project, iter_end
+    launches_per_iter = 1 + 1 + 1 + 3 + 1 + 1 + n_emit + ctx.n_colors + 3 + 1  # noqa: E501
     gpu_launches = args.steps * (2 + iters * launches_per_iter)
 
     cpu = None
@@ -347,7 +350,8 @@ def main():
                                "proj_smem_passes": st["aux"][0] / per_iter, "proj_full_passes": st["aux"][1] / per_iter,
                                "proj_violated_planes": st["aux"][2] / per_iter, "big_tris": st["aux"][3] / per_iter,
                                "big_edges": st["aux"][4] / per_iter, "proj_retries": st["aux"][5] / per_iter,
-                               "proj_heavy_planes": planes_q, "proj_sorted_planes": st["aux"][7] / per_iter},
+                               "proj_heavy_planes": planes_q, "proj_sorted_planes": st["aux"][7] / per_iter,
+                               "proj_short_verts": n_s, "proj_short_planes": planes_s},
             "kernel_sha": kernel_sha(),
         }
         print(json.dumps(line), flush=True)

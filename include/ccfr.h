@@ -98,14 +98,19 @@ typedef struct {
     unsigned long long feas_halts;                    /* halts caused by the final check */
     unsigned long long iterations;                    /* solver iterations executed     */
     unsigned long long steps;                         /* ccfr_step calls                */
-    unsigned long long aux[8];                        /* diagnostics: [0] projection passes
-                                                         run from shared memory, [1] passes
-                                                         over the full list, [2] violated
-                                                         planes processed, [3] oversized
-                                                         triangles, [4] oversized edges,
-                                                         [5] candidate-list retries, [6]
-                                                         planes of the violated vertices,
-                                                         [7] candidate planes sorted       */
+    unsigned long long aux[16];                       /* diagnostics: [0] projection passes
+                                                         over a sorted list in shared memory
+                                                         (long lists), [1] passes over the
+                                                         full list (short lists, one thread
+                                                         per vertex, and lists beyond shared
+                                                         memory), [2] violated planes
+                                                         processed, [3] oversized triangles,
+                                                         [4] oversized edges, [5] candidate-
+                                                         list retries, [6] planes of the
+                                                         violated vertices with long lists,
+                                                         [7] candidate planes sorted, [8]
+                                                         violated vertices with short lists,
+                                                         [9] their planes, [10..15] zero   */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
 } ccfr_stats;
@@ -148,13 +153,14 @@ ccfr_status ccfr_project(ccfr_ctx* ctx, const float* x, float* x_io, unsigned ch
 ccfr_status ccfr_step(ccfr_ctx* ctx, float* x, float* v, void* stream);
 
 /* Number of stages reported by ccfr_step_timed. */
-#define CCFR_N_STAGES 15
+#define CCFR_N_STAGES 16
 
 /* ccfr_step launched kernel by kernel with CUDA events between the stages
  * (prediction, grid extent, grid count, grid scan, grid scatter, vertex-face
  * narrow phase, edge-edge narrow phase, point-point narrow phase, XPBD sweep,
  * projection scan, bookkeeping, work units, oversized vertex-face and
- * edge-edge passes, projection of the violated vertices): the per-stage split of the paper's timing table
+ * edge-edge passes, projection of the violated vertices with long and with
+ * short plane lists): the per-stage split of the paper's timing table
  * (Table 1: broad, narrow, resolution, XPBD).  stage_ms (host, n_stages >=
  * CCFR_N_STAGES doubles) receives milliseconds summed over the iterations.
  * Synchronises `stream`. */

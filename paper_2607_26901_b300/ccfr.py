@@ -47,7 +47,7 @@ class Stats(C.Structure):
                 ("cand_vf", "cand_ee", "cand_vv", "pairs_vf", "pairs_ee", "pairs_vv", "planes_vf", "planes_ee",
                  "planes_vv", "planes",
                  "overflow_verts", "violated_verts", "halts", "ee_fp64", "feas_fp64", "feas_halts",
-                 "iterations", "steps")] + [("aux", C.c_ulonglong * 8), ("max_planes", C.c_uint),
+                 "iterations", "steps")] + [("aux", C.c_ulonglong * 16), ("max_planes", C.c_uint),
                                             ("error_flags", C.c_uint)]
 
     def as_dict(self) -> dict:
@@ -288,7 +288,7 @@ class Context:
 
     def step_timed(self, x, v, stream=None) -> dict:
         """One step launched kernel by kernel; returns {stage: ms}."""
-        n = 15
+        n = 16
         out = (C.c_double * n)()
         _check(lib().ccfr_step_timed(self.h, _ptr(x), _ptr(v), out, n, _stream(stream)), "ccfr_step_timed")
         return {lib().ccfr_stage_name(i).decode(): out[i] for i in range(n)}

@@ -105,7 +105,8 @@ void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer
 
 const char* kStageNames[N_STAGES] = {"predict", "grid_extent", "grid_count", "grid_scan", "grid_scatter",
                                      "emit_vf", "emit_ee", "emit_pp", "xpbd", "project", "misc",
-                                     "grid_units", "emit_vf_big", "emit_ee_big", "project_heavy"};
+                                     "grid_units", "emit_vf_big", "emit_ee_big", "project_heavy",
+                                     "project_short"};
 
 }  // namespace
 
@@ -259,7 +260,7 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.big, (size_t)T + E) == cudaSuccess;
     ok &= dalloc(c, &d.big_box, 2 * ((size_t)T + E)) == cudaSuccess;
     ok &= dalloc(c, &d.work, (size_t)N) == cudaSuccess;
-    ok &= dalloc(c, &d.work_count, 1) == cudaSuccess;
+    ok &= dalloc(c, &d.work_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
     ok &= dalloc(c, &c->tile_sums, (size_t)n_tiles) == cudaSuccess;
@@ -744,7 +745,7 @@ ccfr_status ccfr_get_stats(ccfr_ctx* c, ccfr_stats* out) {
     out->feas_halts = s.feas_halts;
     out->iterations = s.iterations;
     out->steps = s.steps;
-    for (int i = 0; i < 8; ++i) out->aux[i] = s.aux[i];
+    for (int i = 0; i < 16; ++i) out->aux[i] = s.aux[i];
     out->max_planes = s.max_planes;
     out->error_flags = s.error_flags;
     return (s.error_flags & ERR_NONFINITE) ? CCFR_ERR_NONFINITE : CCFR_OK;

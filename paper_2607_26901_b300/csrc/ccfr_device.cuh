@@ -54,7 +54,7 @@ struct DevStats {
     u64 feas_halts;
     u64 iterations;
     u64 steps;
-    u64 aux[8];
+    u64 aux[16];
     unsigned max_planes;
     unsigned error_flags;
 };
@@ -115,8 +115,9 @@ struct DevCtx {
     // every vertex and each scene's (r, 2r, xi, pad); null for a single scene
     const unsigned short* vscene;
     const float4* sparams;
-    int4* work;                 // [n_verts] vertices queued for the heavy projection
-    unsigned* work_count;       // [1]
+    int4* work;                 // [n_verts] vertices queued for the second projection kernels:
+                                //   long plane lists from the front, short ones from the back
+    unsigned* work_count;       // [2] queue lengths: long lists, short lists
     DevStats* stats;
 };
 

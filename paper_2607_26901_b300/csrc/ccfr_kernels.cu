@@ -15,6 +15,7 @@
 //   XPBD          k_predict, k_xpbd_color, k_update (Alg. 4)
 #include "ccfr_device.cuh"
 #include "ccfr_internal.h"
+#include "ccfr_df.cuh"
 
 namespace ccfr {
 
@@ -843,72 +844,123 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
 
 // -------------------------------------------------------------- Alg. 1/2
 
-// Plesnik's ERO-line state (Alg. 1), kept in FP64 and in coordinates
-// centred at the pass start x^(0), so that the auxiliary point w starts at the
-// normal itself.  Alg. 1 divides by the dependence measures beta; with nearly
-// dependent planes (beta ~ 1e-3) binary32 would lose the result's accuracy, and
-// the step runs at most three times per pass, so it is done in FP64.  The FP64
-// pipe is a small fraction of the binary32 rate, so everything around the step
-// (plane tests, retraction, bookkeeping of the iterate) stays in binary32.
-struct d3 { double x, y, z; };
-__device__ __forceinline__ d3 dk(double x, double y, double z) { d3 r; r.x = x; r.y = y; r.z = z; return r; }
-__device__ __forceinline__ d3 dsub(d3 a, d3 b) { return dk(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ d3 dadd(d3 a, d3 b) { return dk(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ d3 dmul(d3 a, double s) { return dk(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ d3 daxpy(double s, d3 a, d3 b) { return dk(fma(s, a.x, b.x), fma(s, a.y, b.y), fma(s, a.z, b.z)); }
-__device__ __forceinline__ double ddot(d3 a, d3 b) { return fma(a.x, b.x, fma(a.y, b.y, a.z * b.z)); }
-__device__ __forceinline__ double dlen(d3 a) { return sqrt(ddot(a, a)); }
-__device__ __forceinline__ d3 d_of(f3 a) { return dk(a.x, a.y, a.z); }
-__device__ __forceinline__ f3 f_of(d3 a) { return mk((float)a.x, (float)a.y, (float)a.z); }
-
-struct Ero {
-    int m;
-    d3 V[3], A[3];
-    double B[3];
+// Plesnik's ERO-line state (Alg. 1), in coordinates centred at the pass
+// start x^(0), so that the auxiliary point w starts at the normal itself.
+// Alg. 1 divides by the dependence measures beta; with nearly dependent planes
+// (beta ~ 1e-3, e.g. two normals 0.05 rad apart) binary32 would lose the
+// result's accuracy, so the steps run in an extended precision R:
+//   double: FP64, for the warp kernels, where the step is one warp-uniform
+//     computation (few instructions; the FP64 pipe, a small fraction of the
+//     binary32 rate on this part, is far from saturated);
+//   dfl: double-float (two binary32 words, about 48 significant bits;
+//     ccfr_df.cuh), for the one-thread-per-vertex kernel, where 32 steps run
+//     side by side and FP64 would saturate its pipe.
+// The stored normals A are binary32 values (the planes' own); V and B are R.
+template <typename R> struct XP;
+template <> struct XP<double> {
+    static __device__ __forceinline__ double make(float a) { return (double)a; }
+    static __device__ __forceinline__ double diff(float a, float b) { return (double)a - (double)b; }  // exact
+    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
+    static __device__ __forceinline__ double sub(double a, double b) { return a - b; }
+    static __device__ __forceinline__ double neg(double a) { return -a; }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return ::fma(a, b, c); }
+    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
+    // a / b for |b| >= eps_dep: a binary32 reciprocal estimate (relative error
+    // below 2^-21) refined by one Newton-Raphson step r <- r + r (1 - b r),
+    // which squares the relative error (< 2^-42); the quotient is then a r.
+    // Far cheaper on the FP64 pipe than an IEEE division.
+    static __device__ __forceinline__ double div(double a, double b) {
+        double r = (double)__fdividef(1.f, (float)b);
+        r = ::fma(r, ::fma(-b, r, 1.0), r);
+        return a * r;
+    }
+    static __device__ __forceinline__ bool abs_lt(double a, float e) { return fabs(a) < (double)e; }
+    static __device__ __forceinline__ bool abs_gt(double a, float e) { return fabs(a) > (double)e; }
+    static __device__ __forceinline__ bool gt(double a, float e) { return a > (double)e; }
+    static __device__ __forceinline__ float to_float(double a) { return (float)a; }
+};
+template <> struct XP<dfl> {
+    static __device__ __forceinline__ dfl make(float a) { return df_make(a); }
+    static __device__ __forceinline__ dfl diff(float a, float b) { return two_sum(a, -b); }  // exact
+    static __device__ __forceinline__ dfl add(dfl a, dfl b) { return df_add(a, b); }
+    static __device__ __forceinline__ dfl sub(dfl a, dfl b) { return df_sub(a, b); }
+    static __device__ __forceinline__ dfl neg(dfl a) { return df_neg(a); }
+    static __device__ __forceinline__ dfl fma(dfl a, dfl b, dfl c) { return df_fma(a, b, c); }
+    static __device__ __forceinline__ dfl mul(dfl a, dfl b) { return df_mul(a, b); }
+    static __device__ __forceinline__ dfl div(dfl a, dfl b) { return df_div(a, b); }
+    static __device__ __forceinline__ bool abs_lt(dfl a, float e) { return fabsf(a.hi) < e; }
+    static __device__ __forceinline__ bool abs_gt(dfl a, float e) { return fabsf(a.hi) > e; }
+    static __device__ __forceinline__ bool gt(dfl a, float e) { return a.hi > e; }
+    static __device__ __forceinline__ float to_float(dfl a) { return df_to_float(a); }
 };
 
-__device__ __forceinline__ void ero_push(Ero& S, d3 v, d3 n, double b) {
-    if (S.m < 3) { S.V[S.m] = v; S.A[S.m] = n; S.B[S.m] = b; S.m++; }
+template <typename R> struct V3 { R x, y, z; };
+template <typename R> __device__ __forceinline__ V3<R> v3(R x, R y, R z) { V3<R> r; r.x = x; r.y = y; r.z = z; return r; }
+template <typename R> __device__ __forceinline__ V3<R> v3_of(f3 a) {
+    return v3<R>(XP<R>::make(a.x), XP<R>::make(a.y), XP<R>::make(a.z));
+}
+// a - b of binary32 vectors, exact in R
+template <typename R> __device__ __forceinline__ V3<R> v3_diff(f3 a, f3 b) {
+    return v3<R>(XP<R>::diff(a.x, b.x), XP<R>::diff(a.y, b.y), XP<R>::diff(a.z, b.z));
+}
+template <typename R> __device__ __forceinline__ V3<R> v3_add(V3<R> a, V3<R> b) {
+    return v3<R>(XP<R>::add(a.x, b.x), XP<R>::add(a.y, b.y), XP<R>::add(a.z, b.z));
+}
+template <typename R> __device__ __forceinline__ V3<R> v3_sub(V3<R> a, V3<R> b) {
+    return v3<R>(XP<R>::sub(a.x, b.x), XP<R>::sub(a.y, b.y), XP<R>::sub(a.z, b.z));
+}
+template <typename R> __device__ __forceinline__ R v3_dot(V3<R> a, V3<R> b) {
+    return XP<R>::fma(a.x, b.x, XP<R>::fma(a.y, b.y, XP<R>::mul(a.z, b.z)));
+}
+// s a + b
+template <typename R> __device__ __forceinline__ V3<R> v3_axpy(R s, V3<R> a, V3<R> b) {
+    return v3<R>(XP<R>::fma(s, a.x, b.x), XP<R>::fma(s, a.y, b.y), XP<R>::fma(s, a.z, b.z));
 }
 
-// a / b for |b| >= eps_dep: a binary32 reciprocal estimate (relative error
-// below 2^-21) refined by one Newton-Raphson step r <- r + r (1 - b r) in
-// FP64, which squares the relative error (< 2^-42); the quotient is then
-// a r.  Far cheaper on the FP64 pipe than an IEEE division, and well inside
-// the accuracy Alg. 1 needs.
-__device__ __forceinline__ double div_nr(double a, double b) {
-    double r = (double)__fdividef(1.f, (float)b);
-    r = fma(r, fma(-b, r, 1.0), r);
-    return a * r;
-}
+template <typename R> struct Ero {
+    int m;
+    V3<R> V[3];
+    f3 A[3];
+    R B[3];
+};
 
 // One Alg. 1 step with |V| >= 1 stored lines: project zt onto the
 // intersection of the stored hyperplanes and n . z = b.  (The first step, onto
 // a single plane, is taken in binary32 by the caller.)  The |v| > eps_dep
 // test compares squares (no square root).
-__device__ __noinline__ void ortho_step(d3& zt, d3 n, double b, Ero& S, double eps) {
+template <typename R>
+__device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float eps) {
+    using X = XP<R>;
     const int m = S.m;
-    const d3 n0 = S.A[0];
-    const double b0 = S.B[0];
-    const d3 vm = S.V[m - 1];
-    double beta_u = ddot(dsub(n, n0), vm);
-    if (fabs(beta_u) < eps) return;
-    d3 u = daxpy(div_nr(b - ddot(n, zt), beta_u), vm, zt);
-    d3 w = n;
+    const f3 n0 = S.A[0];
+    const R b0 = S.B[0];
+    const V3<R> vm = S.V[m - 1];
+    const R beta_u = v3_dot(v3_diff<R>(n, n0), vm);
+    if (X::abs_lt(beta_u, eps)) return;
+    const V3<R> nd = v3_of<R>(n);
+    const V3<R> u = v3_axpy(X::div(X::sub(b, v3_dot(nd, zt)), beta_u), vm, zt);
+    V3<R> w = nd;
     #pragma unroll
     for (int j = 1; j <= 2; ++j) {
         if (j > m) break;
-        d3 nj = (j < m) ? S.A[j] : n;
-        double bj = (j < m) ? S.B[j] : b;
-        d3 dnj = dsub(nj, n0);
-        double beta_w = ddot(dnj, S.V[j - 1]);
-        if (fabs(beta_w) > eps) w = daxpy(div_nr(bj - b0 - ddot(dnj, w), beta_w), S.V[j - 1], w);
+        const f3 nj = (j < m) ? S.A[j] : n;
+        const R bj = (j < m) ? S.B[j] : b;
+        const V3<R> dnj = v3_diff<R>(nj, n0);
+        const R beta_w = v3_dot(dnj, S.V[j - 1]);
+        if (X::abs_gt(beta_w, eps))
+            w = v3_axpy(X::div(X::sub(X::sub(bj, b0), v3_dot(dnj, w)), beta_w), S.V[j - 1], w);
     }
-    d3 vn = dsub(w, u);
-    if (ddot(vn, vn) > eps * eps) {
-        double beta_new = ddot(n0, vn);
-        zt = (fabs(beta_new) < eps) ? u : daxpy(div_nr(b0 - ddot(n0, u), beta_new), vn, u);
-        ero_push(S, vn, n, b);
+    const V3<R> vn = v3_sub(w, u);
+    if (X::gt(v3_dot(vn, vn), eps * eps)) {
+        const V3<R> n0d = v3_of<R>(n0);
+        const R beta_new = v3_dot(n0d, vn);
+        zt = X::abs_lt(beta_new, eps) ? u : v3_axpy(X::div(X::sub(b0, v3_dot(n0d, u)), beta_new), vn, u);
+        if (S.m < 3) {
+            S.V[S.m] = vn;
+            S.A[S.m] = n;
+            S.B[S.m] = b;
+            S.m++;
+        }
     }
 }
 
@@ -919,18 +971,18 @@ __device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, 
 // the pass input so far, the number of violated planes met and the ERO state.
 // The first Alg. 1 step of a pass (|V| = 0) is a plain orthogonal projection
 // onto one plane, with no division by a dependence measure: it runs in
-// binary32 (as accurate as the binary32 iterate it produces), and its FP64 ERO
+// binary32 (as accurate as the binary32 iterate it produces), and its ERO
 // entry is formed from the stored plane P0 only when a second step needs it.
-struct Walk {
+template <typename R> struct Walk {
     f3 ypass, y;
     float dmax2;
     int nv;
     bool lazy0;
     float4 P0;
-    Ero S;
+    Ero<R> S;
 };
 
-__device__ __forceinline__ void walk_begin(Walk& W, f3 ypass) {
+template <typename R> __device__ __forceinline__ void walk_begin(Walk<R>& W, f3 ypass) {
     W.ypass = ypass;
     W.y = ypass;
     W.dmax2 = 0.f;
@@ -939,18 +991,22 @@ __device__ __forceinline__ void walk_begin(Walk& W, f3 ypass) {
     W.S.m = 0;
 }
 
+// b = -d - n . ypass of the plane n . z = b in coordinates centred at ypass
+template <typename R> __device__ __forceinline__ R plane_b(float4 P, const V3<R>& yp) {
+    return XP<R>::neg(XP<R>::add(XP<R>::make(P.w), v3_dot(v3_of<R>(xyz(P)), yp)));
+}
+
 // A plane violated at the current iterate: Alg. 1 (while |V| < 3), then the
 // retraction by eps towards the build position (Sec. 3.2).  Steps with
-// |V| >= 1 work in FP64 on z = y - ypass (exact in FP64), the plane written
-// n . z = b with b = -d - n . ypass, and round their result once to binary32;
-// with |V| = 3 the iterate only retracts, in binary32.  A binary32 scaling is
-// accurate to ~u |y| here (no cancellation).
-__device__ __forceinline__ void walk_visit(Walk& W, float4 P, float eps, double eps_dep) {
+// |V| >= 1 work in R on z = y - ypass (exact) and round their result once to
+// binary32; with |V| = 3 the iterate only retracts, in binary32.  A binary32
+// scaling is accurate to ~u |y| here (no cancellation).
+template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, float4 P, float eps, float eps_dep) {
     ++W.nv;
     if (W.S.m == 0) {
         const f3 n = xyz(P);
         const float beta0 = dot(n, n);
-        if (!(fabsf(beta0) < (float)eps_dep)) {
+        if (!(fabsf(beta0) < eps_dep)) {
             W.y = sub(W.y, mul(n, rho_at(W.y, P) / beta0));
             W.P0 = P;
             W.lazy0 = true;
@@ -959,19 +1015,17 @@ __device__ __forceinline__ void walk_visit(Walk& W, float4 P, float eps, double 
     } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
         // (a normal equal to the first line's gives beta_u = (n - n0) . v = 0
         // exactly, and Alg. 1 leaves the iterate unchanged: skipped)
-        const d3 yp = d_of(W.ypass);
+        const V3<R> yp = v3_of<R>(W.ypass);
         if (W.lazy0) {
-            const d3 n0 = dk(W.P0.x, W.P0.y, W.P0.z);
-            W.S.V[0] = n0;
-            W.S.A[0] = n0;
-            W.S.B[0] = -(double)W.P0.w - ddot(n0, yp);
+            W.S.A[0] = xyz(W.P0);
+            W.S.V[0] = v3_of<R>(xyz(W.P0));
+            W.S.B[0] = plane_b<R>(W.P0, yp);
             W.lazy0 = false;
         }
-        const d3 nrm = dk(P.x, P.y, P.z);
-        const double bz = -(double)P.w - ddot(nrm, yp);
-        d3 zt = dsub(d_of(W.y), yp);
-        ortho_step(zt, nrm, bz, W.S, eps_dep);
-        W.y = f_of(dadd(yp, zt));
+        V3<R> zt = v3_diff<R>(W.y, W.ypass);
+        ortho_step<R>(zt, xyz(P), plane_b<R>(P, yp), W.S, eps_dep);
+        const V3<R> yn = v3_add(yp, zt);
+        W.y = mk(XP<R>::to_float(yn.x), XP<R>::to_float(yn.y), XP<R>::to_float(yn.z));
     }
     const float L = len(W.y);
     W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
@@ -1031,7 +1085,8 @@ __device__ __forceinline__ f3 clamp_len(f3 y, float lim) {
 
 struct BlockCounters {
     unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry;
-    unsigned long long planes, heavy_planes, sorted;
+    unsigned long long planes, heavy_planes, sorted, short_planes;
+    unsigned short_verts;
 };
 
 // Per-warp shared memory of the projection: the candidate planes of a pass
@@ -1079,7 +1134,7 @@ __device__ __forceinline__ float warp_max(float v) {
 // the pass result and Dmax the largest distance of the iterate from ypass.
 template <typename Get>
 __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get get, f3 ypass, f3& y_out, float& Dmax) {
-    Walk W;
+    Walk<double> W;
     walk_begin(W, ypass);
     Tup cur;
     cur.a = cur.b = cur.c = 0ull;
@@ -1102,7 +1157,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
         cur = best;
         first = false;
         const float4 P = tup_plane(best);
-        walk_visit(W, P, c.p.eps, (double)c.p.eps_dep);
+        walk_visit(W, P, c.p.eps, c.p.eps_dep);
     }
     y_out = W.y;
     Dmax = sqrtf(W.dmax2);
@@ -1194,7 +1249,7 @@ __device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
 // and the walk resumes with the chunk's later planes, tested at the new iterate.
 __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, const float4* pl, f3 ypass,
                            f3& y_out, float& Dmax) {
-    Walk W;
+    Walk<double> W;
     walk_begin(W, ypass);
     for (int pos = 0; pos < m; pos += 32) {
         const int e = pos + lane;
@@ -1207,7 +1262,7 @@ __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, 
             const int f = __ffs(bal) - 1;
             const float4 Pf = make_float4(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f),
                                           __shfl_sync(FULL, P.z, f), __shfl_sync(FULL, P.w, f));
-            walk_visit(W, Pf, c.p.eps, (double)c.p.eps_dep);
+            walk_visit(W, Pf, c.p.eps, c.p.eps_dep);
             lo = f + 1;
         }
     }
@@ -1241,18 +1296,21 @@ __device__ __forceinline__ void scan_min_rho(const float4* pl, int np, f3 y, int
 // Final feasibility check on the stored binary32 position xn: every plane
 // must hold within tau plus the binary32 rounding of the position; a
 // rounding-error filter decides most planes, FP64 the rest.  Returns true
-// when the position fails (the vertex then halts).
+// when the position fails (the vertex then halts).  THREAD: one thread checks
+// all planes; otherwise the warp's lanes share them.
+template <bool THREAD>
 __device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4* pl, int np, float4 X, f3 xn,
                                                   int lane, bool& used_fp64) {
     const float U = 5.9604645e-8f;
+    const int j_start = THREAD ? 0 : lane, j_step = THREAD ? 1 : 32;
     f3 dl = sub(xn, xyz(X));
     float tau = c.p.tau + 2.f * U * (fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z));
     bool fail = false, undecided = false;
-    for (int j0 = lane; j0 < np; j0 += 128) {
+    for (int j0 = j_start; j0 < np; j0 += 4 * j_step) {
         float4 P[4];
         #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            int j = j0 + 32 * k;
+            int j = j0 + j_step * k;
             P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 1.f);
         }
         #pragma unroll
@@ -1268,30 +1326,36 @@ __device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4*
             if (rd < -(double)tau) fail = true;
         }
     }
+    if (THREAD) {
+        used_fp64 = undecided;
+        return fail;
+    }
     used_fp64 = __any_sync(FULL, undecided);
     return __any_sync(FULL, fail);
 }
 
 // Common end of a vertex: max-step clamp (STEP), final check, write-back,
-// convergence flag and counters.
-template <bool STEP>
+// convergence flag and counters.  THREAD: the vertex belongs to one thread;
+// otherwise to the whole warp (lane 0 writes).
+template <bool STEP, bool THREAD>
 __device__ __forceinline__ void finish_vertex(const DevCtx& c, int lane, int v, float4 X, float4 XP, f3 y0, f3 y,
                                               bool halted, const float4* pl, int np, bool over, unsigned cnt,
                                               BlockCounters& bc, float4* x_out, unsigned char* halt_out) {
+    const bool leader = THREAD || lane == 0;
     if (STEP && !halted) y = clamp_len(y, scene_params(c, scene_of(c, v)).r);
     f3 xn = add(xyz(X), y);
     bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
     if (!halted && np > 0 && (changed || over)) {
         bool f64 = false;
-        if (final_check_fails(c, pl, np, X, xn, lane, f64)) {
+        if (final_check_fails<THREAD>(c, pl, np, X, xn, lane, f64)) {
             halted = true;
             y = mk(0.f, 0.f, 0.f);
             xn = xyz(X);
-            if (lane == 0) atomicAdd(&bc.fhalt, 1u);
+            if (leader) atomicAdd(&bc.fhalt, 1u);
         }
-        if (f64 && lane == 0) atomicAdd(&bc.f64, 1u);
+        if (f64 && leader) atomicAdd(&bc.f64, 1u);
     }
-    if (lane == 0) {
+    if (leader) {
         if (halted) atomicAdd(&bc.halt, 1u);
         if (cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
         if (STEP) {
@@ -1320,6 +1384,8 @@ __device__ __forceinline__ void flush_block_counters(const DevCtx& c, BlockCount
         if (bc.retry) atomicAdd(&c.stats->aux[5], (u64)bc.retry);
         if (bc.heavy_planes) atomicAdd(&c.stats->aux[6], bc.heavy_planes);
         if (bc.sorted) atomicAdd(&c.stats->aux[7], bc.sorted);
+        if (bc.short_verts) atomicAdd(&c.stats->aux[8], (u64)bc.short_verts);
+        if (bc.short_planes) atomicAdd(&c.stats->aux[9], bc.short_planes);
     }
 }
 
@@ -1329,14 +1395,21 @@ __device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
         bc.planes = 0ull;
         bc.heavy_planes = 0ull;
         bc.sorted = 0ull;
+        bc.short_planes = 0ull;
+        bc.short_verts = 0u;
     }
     __syncthreads();
 }
 
+// Plane lists up to this length are projected one thread per vertex
+// (k_project_short); longer ones one warp per vertex (k_project_heavy).
+constexpr int SHORT_LIST = 32;
+
 // Projection, first kernel: one warp per vertex.  Vertices whose planes all
 // hold at the candidate (rho_k(x') >= 0: Alg. 2 returns x' after its first
 // pass), vertices without planes, and overflowed vertices are finished here;
-// the others are queued for k_project_heavy.  STEP = true: x_b is the
+// the others are queued for k_project_short or k_project_heavy by the length
+// of their plane list.  STEP = true: x_b is the
 // collision-free iterate x_c (read and overwritten), candidates come from
 // x_in (the XPBD iterate), and the step is clamped to r.
 template <bool STEP>
@@ -1372,13 +1445,19 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
                 if (mn < 0.f) {
                     queued = true;
                     if (lane == 0) {
-                        unsigned w = atomicAdd(c.work_count, 1u);
-                        c.work[w] = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
+                        const int4 wk = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
+                        if (np <= SHORT_LIST) {
+                            const unsigned w = atomicAdd(&c.work_count[1], 1u);
+                            c.work[c.n_verts - 1 - (int)w] = wk;
+                        } else {
+                            const unsigned w = atomicAdd(&c.work_count[0], 1u);
+                            c.work[w] = wk;
+                        }
                         atomicAdd(&bc.viol, 1u);
                     }
                 }
             }
-            if (!queued) finish_vertex<STEP>(c, lane, v, X, XP, y0, y, false, pl, np, over, cnt, bc, x_out, halt_out);
+            if (!queued) finish_vertex<STEP, false>(c, lane, v, X, XP, y0, y, false, pl, np, over, cnt, bc, x_out, halt_out);
         } else if (!STEP && lane == 0 && halt_out) {
             halt_out[v] = 0;
         }
@@ -1406,7 +1485,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
     const int lane = threadIdx.x & 31;
     SortBuf& sb = reinterpret_cast<SortBuf*>(proj_smem)[threadIdx.x >> 5];
     const float U = 5.9604645e-8f;   // unit roundoff of binary32
-    const unsigned nwork = *c.work_count;
+    const unsigned nwork = c.work_count[0];
     const unsigned stride = gridDim.x * PROJ_WARPS;
     for (unsigned wi = blockIdx.x * PROJ_WARPS + (threadIdx.x >> 5); wi < nwork; wi += stride) {
         const int4 wk = c.work[wi];
@@ -1538,8 +1617,72 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
             ypass = ynext;
         }
         const bool halted = !conv;
-        finish_vertex<STEP>(c, lane, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, false, cnt, bc,
+        finish_vertex<STEP, false>(c, lane, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, false, cnt, bc,
                             x_out, halt_out);
+    }
+    flush_block_counters(c, bc);
+}
+
+// Projection, second kernel for short plane lists: one thread per queued
+// vertex (persistent threads over the back of the queue).  Each pass of Alg. 2
+// visits, over and over, the first plane in the pass order (sort key rho at
+// the first input, then hash, plane bits and slot: the order of the warp
+// kernel) that comes after the last one visited and is violated at the
+// current iterate: the same walk as over the sorted list, without storing it.
+template <bool STEP>
+__global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x_b, const float4* x_in,
+                                                        float4* x_out, unsigned char* halt_out) {
+    if (STEP && c.flags[1]) return;
+    __shared__ BlockCounters bc;
+    zero_block_counters(bc);
+    const unsigned nwork = c.work_count[1];
+    for (unsigned wi = blockIdx.x * blockDim.x + threadIdx.x; wi < nwork; wi += gridDim.x * blockDim.x) {
+        const int4 wk = c.work[c.n_verts - 1 - (int)wi];
+        const int v = wk.x;
+        const float mn = __int_as_float(wk.y);
+        const float4 X = x_b[v];
+        const float4 XP = x_in[v];
+        const f3 y0 = sub(xyz(XP), xyz(X));
+        const unsigned cnt = c.count[v];
+        const int np = (int)min(cnt, (unsigned)c.p.K);
+        const float4* pl = c.planes + (size_t)v * c.p.K;
+        atomicAdd(&bc.short_planes, (unsigned long long)np);
+        atomicAdd(&bc.short_verts, 1u);
+        f3 ypass = y0;
+        bool conv = false;
+        for (int pass = 0; pass <= c.p.max_passes; ++pass) {
+            float mnb = mn;
+            if (pass > 0) {
+                mnb = 3.4e38f;
+                for (int j = 0; j < np; ++j) mnb = fminf(mnb, rho_at(ypass, pl[j]));
+            }
+            if (mnb >= 0.f) { conv = true; break; }
+            if (pass == c.p.max_passes) break;
+            Walk<dfl> W;
+            walk_begin(W, ypass);
+            Tup cur = tup_none();
+            bool first = true;
+            for (;;) {
+                Tup best = tup_none();
+                for (int j = 0; j < np; ++j) {
+                    const float4 P = pl[j];
+                    if (rho_at(W.y, P) < 0.f) {
+                        const Tup t = make_tup(rho_at(y0, P), P, j);
+                        if ((first || tless(cur, t)) && tless(t, best)) best = t;
+                    }
+                }
+                if (best.d == ~0u) break;
+                cur = best;
+                first = false;
+                walk_visit(W, tup_plane(best), c.p.eps, c.p.eps_dep);
+            }
+            atomicAdd(&bc.glob_pass, 1u);
+            atomicAdd(&bc.nviol, (unsigned)W.nv);
+            ypass = W.y;
+        }
+        const bool halted = !conv;
+        finish_vertex<STEP, true>(c, 0, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, false, cnt,
+                                  bc, x_out, halt_out);
     }
     flush_block_counters(c, bc);
 }
@@ -1698,11 +1841,19 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     }
 }
 
+// persistent blocks of k_project_short per SM (128 threads each): as many as
+// are resident at once, found by configure_kernels
+static int g_short_blocks_per_sm = 4;
+#define SHORT_BLOCKS_PER_SM g_short_blocks_per_sm
+
 cudaError_t configure_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_project_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)PROJ_SMEM);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_project_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJ_SMEM);
+    int nb = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_short<true>, 128, 0);
+    if (e == cudaSuccess && nb > 0) g_short_blocks_per_sm = nb;
     return e;
 }
 
@@ -1713,10 +1864,11 @@ void launch_clear_regions(const DevCtx& c, cudaStream_t st) {
 
 void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st) {
     long threads = (long)c.n_verts * 32;
-    cudaMemsetAsync(c.work_count, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) {
         k_project<false><<<nblk(threads, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
         k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
+        k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, xb, xio, xio, halt);
     }
 }
 
@@ -1736,11 +1888,13 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
     }
     if (tm) tm->mark(ST_XPBD, st);
     long threads = (long)c.n_verts * 32;
-    cudaMemsetAsync(c.work_count, 0, sizeof(unsigned), st);
+    cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) k_project<true><<<nblk(threads, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
     if (threads > 0) k_project_heavy<true><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_HEAVY, st);
+    if (threads > 0) k_project_short<true><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, x, c.x_s, x, nullptr);
+    if (tm) tm->mark(ST_PROJECT_SHORT, st);
     k_iter_end<<<1, 1, 0, st>>>(c, early_exit);
 }
 
@@ -1784,8 +1938,8 @@ constexpr int STATIC_MAX_VERTS = 1 << 18;   // 262,144 vertices
 struct StaticScratch {
     DevStats stats;
     int flags[2];
-    unsigned work_count;
-    unsigned pad_[13];
+    unsigned work_count[2];
+    unsigned pad_[12];
     int4 work[STATIC_MAX_VERTS];
     unsigned dmin[STATIC_MAX_VERTS];
 };
@@ -1875,12 +2029,14 @@ extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const fl
     c.flags = sc->flags;
     c.stats = &sc->stats;
     c.work = sc->work;
-    c.work_count = &sc->work_count;
+    c.work_count = sc->work_count;
     c.n_sm = su->n_sm;
     k_static_dmin<<<nblk(n_verts, 256), 256, 0, s>>>(dmin_drop, sc->dmin, n_verts);
     long threads = (long)n_verts * 32;
     k_project<false><<<nblk(threads, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
     k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                          (float4*)x_io, halt_out);
+    k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, s>>>(c, (const float4*)x, (float4*)x_io,
+                                                                       (float4*)x_io, halt_out);
     return (cudaGetLastError() == cudaSuccess) ? CCFR_OK : CCFR_ERR_CUDA;
 }
