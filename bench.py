@@ -351,7 +351,10 @@ def main():
                                "proj_violated_planes": st["aux"][2] / per_iter, "big_tris": st["aux"][3] / per_iter,
                                "big_edges": st["aux"][4] / per_iter, "proj_retries": st["aux"][5] / per_iter,
                                "proj_heavy_planes": planes_q, "proj_sorted_planes": st["aux"][7] / per_iter,
-                               "proj_short_verts": n_s, "proj_short_planes": planes_s},
+                               "proj_short_verts": n_s, "proj_short_planes": planes_s,
+                               "big_cells": st["aux"][10] / per_iter, "big_table_scans": st["aux"][11] / per_iter,
+                               "big_items": st["aux"][12] / per_iter, "bige_items": st["aux"][13] / per_iter,
+                               "big_cand": st["aux"][14] / per_iter},
             "kernel_sha": kernel_sha(),
         }
         print(json.dumps(line), flush=True)

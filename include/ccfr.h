@@ -110,7 +110,13 @@ typedef struct {
                                                          violated vertices with long lists,
                                                          [7] candidate planes sorted, [8]
                                                          violated vertices with short lists,
-                                                         [9] their planes, [10..15] zero   */
+                                                         [9] their planes, [10] grid cells
+                                                         scanned for oversized primitives,
+                                                         [11] their whole-table scans, [12]
+                                                         items they tested, [13] oversized-
+                                                         edge items tested by oversized
+                                                         edges, [14] candidates found by
+                                                         oversized primitives, [15] zero   */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
 } ccfr_stats;

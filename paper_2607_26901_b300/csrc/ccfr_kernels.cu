@@ -600,7 +600,9 @@ __device__ __forceinline__ void warp_cell_items(const DevCtx& c, int lane, bool 
 // gathered 32 at a time (warp_cell_items), compacted into shared memory and
 // tested by every query lane against one broadcast item at a time.
 template <int QK, int MODE>
-__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po) {
+// three blocks per SM: the edge-edge narrow phase would otherwise take enough
+// registers to leave room for two
+__global__ void __launch_bounds__(EMIT_WARPS * 32, 3) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po) {
     if (c.flags[1]) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
     __shared__ float4 items[EMIT_WARPS][64];
@@ -731,6 +733,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     const float inv = 1.0f / cell_size_of(c, QK);
     const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
     const unsigned nbig = c.big_count[QK];
+    u64 big_cells = 0, big_scans = 0, big_items = 0, bige_items = 0;   // diagnostics
     const unsigned stride = gridDim.x * EMIT_WARPS;
     // append a hit to the warp queue; process 32 queued pairs at a time
     auto push = [&](bool hit, int2 pr) {
@@ -780,6 +783,10 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         const bool huge = fabsf(fx0) > cmax || fabsf(fx1) > cmax || fabsf(fy0) > cmax || fabsf(fy1) > cmax ||
                           fabsf(fz0) > cmax || fabsf(fz1) > cmax || fx1 - fx0 >= 127.f || fy1 - fy0 >= 127.f ||
                           fz1 - fz0 >= 127.f;
+        if (lane == 0) {
+            big_cells += (huge || ncell * 8.0 > (double)(t_end - t_begin)) ? 0ull : (u64)ncell;
+            big_scans += (huge || ncell * 8.0 > (double)(t_end - t_begin)) ? 1ull : 0ull;
+        }
         if (huge || ncell * 8.0 > (double)(t_end - t_begin)) {
             // cheaper to test the whole table
             for (unsigned s0 = t_begin; s0 < t_end; s0 += 32) {
@@ -805,6 +812,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                 warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                     int2 pr = make_int2(-1, -1);
                     if (valid) pr = test(i0, i1);
+                    big_items += valid ? 1ull : 0ull;
                     push(pr.x >= 0, pr);
                 });
             }
@@ -824,6 +832,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             }
             warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                 int2 pr = make_int2(-1, -1);
+                bige_items += valid ? 1ull : 0ull;
                 if (valid) {
                     const int o2 = __float_as_int(i0.w);
                     if (o2 > o && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z &&
@@ -840,6 +849,11 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     warp_add_u64(&c.stats->pairs[QK], k.acc);
     warp_add_u64(&c.stats->planes_kind[QK], k.planes);
     if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+    warp_add_u64(&c.stats->aux[10], big_cells);
+    warp_add_u64(&c.stats->aux[11], big_scans);
+    warp_add_u64(&c.stats->aux[12], big_items);
+    warp_add_u64(&c.stats->aux[13], bige_items);
+    warp_add_u64(&c.stats->aux[14], k.cand);
 }
 
 // -------------------------------------------------------------- Alg. 1/2
