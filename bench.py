@@ -444,8 +444,15 @@ def serve_pool(seed: int = 5):
 
 
 def run_serve(args, ws, rank, local, desc):
-    """Open-loop replay of a seeded Poisson trace of step requests through the
-    serving loop; latency = completion - arrival, per request."""
+    """Open-loop replay of seeded Poisson traces of step requests through the
+    serving loop; latency = completion - arrival, per request.
+
+    1. The configured trace (args.rate, args.requests) with args.slots slots.
+       When the arrival rate exceeds what the GPU can serve, the queue grows
+       for the whole trace and latency is mostly waiting; the run gives the
+       saturated service rate mu (completed requests / span).
+    2. A trace at 0.7 mu (a sustainable load), with args.slots slots and with
+       one slot, for latencies that measure the service itself."""
     import numpy as np
     import torch
     from paper_2607_26901_b300 import ccfr
@@ -454,14 +461,20 @@ def run_serve(args, ws, rank, local, desc):
     small, big = serve_pool(5 + rank)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
-    rng = np.random.default_rng(50 + rank)
-    n = args.requests
-    t_arr = np.cumsum(rng.exponential(1.0 / args.rate, n))
-    t_arr -= t_arr[0]
-    pick_big = rng.uniform(size=n) < 0.05
-    which = np.where(pick_big, rng.integers(0, len(big), n), rng.integers(0, len(small), n))
-    out = {}
-    for slots in sorted({args.slots, 1}, reverse=True):
+    scenes_all = small + big
+    nv = np.array([sc.n_movable for sc in scenes_all])
+    iters = small[0].params["iters"]
+
+    def trace(n, rate, seed):
+        rng = np.random.default_rng(seed)
+        t_arr = np.cumsum(rng.exponential(1.0 / rate, n))
+        t_arr -= t_arr[0]
+        pick_big = rng.uniform(size=n) < 0.05
+        which = np.where(pick_big, rng.integers(0, len(big), n), rng.integers(0, len(small), n))
+        return t_arr, pick_big, which
+
+    def serve(slots, t_arr, pick_big, which):
+        n = len(t_arr)
         sv = ccfr.Server(budget, n_slots=slots, timeout_s=300.0)
         ids_small = [sv.add_scene(sc) for sc in small]
         ids_big = [sv.add_scene(sc) for sc in big]
@@ -478,35 +491,40 @@ def run_serve(args, ws, rank, local, desc):
         wall = time.perf_counter() - t0
         res = sv.results(n)
         info = sv.info()
+        sv.close()
         ok = res["status"] == 0
         lat = (res["t_done"] - res["t_arrival"])[ok] * 1e3
         span = float(res["t_done"][ok].max() - res["t_arrival"].min()) if ok.any() else float("nan")
-        scenes_all = small + big
-        nv = np.array([scenes_all[i].n_movable for i in range(len(scenes_all))])
-        iters = small[0].params["iters"]
         vert_updates = float(nv[sid[ok]].sum()) * iters
-        out[slots] = {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
-                      "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
-                      "mean_ms": float(lat.mean()) if len(lat) else None,
-                      "completed": int(ok.sum()), "failed": int((~ok).sum()), "done": int(done),
-                      "throughput_req_s": ok.sum() / span, "value": vert_updates / span,
-                      "span_s": span, "wall_s": wall, "admissions": info["admissions"],
-                      "evictions": info["evictions"], "peak_resident_gb": info["peak_resident_bytes"] / 1e9,
-                      "preloaded": preloaded, "preload_s": round(t_pre, 2)}
-        sv.close()
-        if slots == 1 and args.slots != 1:
-            # the single-slot run only needs to establish the sequential rate
-            pass
-    best = out[args.slots]
+        return {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
+                "mean_ms": float(lat.mean()) if len(lat) else None,
+                "completed": int(ok.sum()), "failed": int((~ok).sum()), "done": int(done),
+                "throughput_req_s": ok.sum() / span, "value": vert_updates / span,
+                "span_s": span, "wall_s": wall, "admissions": info["admissions"],
+                "evictions": info["evictions"], "peak_resident_gb": info["peak_resident_bytes"] / 1e9,
+                "preloaded": preloaded, "preload_s": round(t_pre, 2)}
+
+    cfg = serve(args.slots, *trace(args.requests, args.rate, 50 + rank))
+    mu = cfg["throughput_req_s"]
+    rate_sub = 0.7 * mu
+    n_sub = min(args.requests, 2000)
+    tr = trace(n_sub, rate_sub, 60 + rank)
+    sub = {"rate_per_s": rate_sub, "requests": n_sub, f"slots{args.slots}": serve(args.slots, *tr)}
+    if args.slots != 1:
+        sub["slots1"] = serve(1, *tr)
     if rank == 0:
+        best = sub[f"slots{args.slots}"]
         print(json.dumps({
-            "metric": METRIC, "value": best["value"] * ws, "unit": UNIT, "n_gpus": ws, "steps": n,
-            "warmup": 0, "ms_per_step": best["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": cfg["value"] * ws, "unit": UNIT, "n_gpus": ws, "steps": args.requests,
+            "warmup": 0, "ms_per_step": cfg["mean_ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "serve", "description": desc, "requests": n, "rate_per_s": args.rate,
-                       "slots": args.slots, "hbm_budget_gb": budget / 1e9, "scenes": len(small) + len(big)},
-            "served": best, "single_slot": out.get(1),
+            "config": {"workload": "serve", "description": desc, "requests": args.requests, "rate_per_s": args.rate,
+                       "slots": args.slots, "hbm_budget_gb": budget / 1e9, "scenes": len(scenes_all)},
+            "served_at_config_rate": cfg, "sub_saturation": sub,
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
+            "latency_note": "p50/p99 at 0.7 x the saturated service rate (the configured rate exceeds it; "
+                            "there latency is queueing, see served_at_config_rate)",
         }), flush=True)
 
 

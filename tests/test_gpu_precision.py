@@ -1,0 +1,159 @@
+"""Error of the GPU path against the FP64 oracle, per workload configuration.
+
+The GPU computes in binary32, with FP64 only for near-parallel edge-edge
+closest points and the undecided planes of the final feasibility check, and
+Alg. 1 in an extended precision (FP64 or double-float).  Each case reports the
+largest and the median position error |x_gpu - x_oracle|_inf relative to the
+scene scale L, over the vertices outside the oracle's decision bands (inputs
+within 1e-7 L of a threshold, where either branch is correct), and asserts the
+1e-5 L bar.  With CCFR_PRECISION_REPORT set, one JSON line per case is
+appended to that file.
+
+Cases: the 1,024-vertex cloth over the sphere (full substep, 10 iterations);
+the cloth stack and the wires at sizes the oracle steps in seconds (full
+substeps) and at full size (oracle projection of sampled vertices on the
+GPU's own planes); a batch of uneven scenes (each scene's full substep).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2607_26901_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26901_b300 import ccfr  # noqa: E402
+from tests.helpers import dev_scene  # noqa: E402
+
+TOL_REL = 1e-5
+BAND_REL = 1e-7
+
+
+def report(case, err_rel, n_cmp, n_band, extra=None):
+    line = {"case": case, "max_err_rel": float(np.max(err_rel)) if len(err_rel) else 0.0,
+            "p99_err_rel": float(np.percentile(err_rel, 99)) if len(err_rel) else 0.0,
+            "median_err_rel": float(np.median(err_rel)) if len(err_rel) else 0.0,
+            "frac_within": float(np.mean(err_rel <= TOL_REL)) if len(err_rel) else 1.0,
+            "compared": int(n_cmp), "band_excluded": int(n_band)}
+    if extra:
+        line.update(extra)
+    print("PRECISION", json.dumps(line))
+    path = os.environ.get("CCFR_PRECISION_REPORT")
+    if path:
+        with open(path, "a") as f:
+            f.write(json.dumps(line) + "\n")
+    return line
+
+
+def oracle_capacity(orc, sc, margin=1.5):
+    P = orc.make_params(sc.params, capacity=1 << 20)
+    R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, P)
+    k = int(np.diff(R["offs"]).max() * margin) + 8
+    return max(32, (k + 31) // 32 * 32)          # the library takes multiples of 32
+
+
+def full_step_error(orc, sc, case, iters=None):
+    iters = sc.params["iters"] if iters is None else iters
+    L = orc.scene_scale(sc.x)
+    K = oracle_capacity(orc, sc)
+    P = orc.make_params(sc.params, band=BAND_REL * L, iters=iters, capacity=K)
+    x3 = sc.x[:, :3].astype(np.float64)
+    rest = orc.rest_lengths(x3, sc.edges)
+    xo, vo, info, vband = orc.step(x3, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, rest, P)
+    x, v = dev_scene(sc)
+    ctx = ccfr.Context.from_scene(sc, plane_capacity=K, iters=iters)
+    ctx.step(x, v)
+    st = ctx.stats()
+    ctx.close()
+    assert st["status"] == 0 and st["iterations"] == iters
+    got = x.cpu().numpy()[:, :3].astype(np.float64)
+    ok = vband == 0
+    err = np.abs(got - xo).max(axis=1)[ok] / L
+    line = report(case, err, ok.sum(), (~ok).sum(), {"verts": sc.n_verts, "iters": iters})
+    return line
+
+
+def test_precision_cloth_on_sphere(orc):
+    line = full_step_error(orc, S.config(1), "cloth_on_sphere 32x32, full substep")
+    assert line["max_err_rel"] <= TOL_REL
+
+
+def test_precision_small_stack_one_iteration(orc):
+    sc = S.cloth_stack(n_side=24, layers=4, seed=2, plane_capacity=1024)
+    line = full_step_error(orc, sc, "cloth_stack 4x24x24, one iteration", iters=1)
+    assert line["max_err_rel"] <= TOL_REL
+
+
+def test_precision_small_stack_full_substep(orc):
+    """20 iterations of the chaotic stack: a decision taken differently in
+    binary32 and in FP64 (a violation test, a halt, the order of
+    near-duplicate planes whose binary32 sort keys tie) changes that vertex's
+    later iterates by up to the step bound.  The median stays at the
+    rounding level; the bar is met by at least 99% of the vertices."""
+    sc = S.cloth_stack(n_side=24, layers=4, seed=2, plane_capacity=1024)
+    line = full_step_error(orc, sc, "cloth_stack 4x24x24, full substep")
+    assert line["frac_within"] >= 0.99 and line["median_err_rel"] <= 1e-7
+
+
+def test_precision_small_wires(orc):
+    sc = S.wires(n_grid=6, n_seg=32, seed=3)
+    line = full_step_error(orc, sc, "wires 6x6x32, full substep")
+    assert line["max_err_rel"] <= TOL_REL
+
+
+def test_precision_batch(orc):
+    scenes = S.batch(n_scenes=5, seed=11, min_verts=100, max_verts=700, median_verts=300, sphere_slices=16,
+                     sphere_stacks=10, plane_capacity=512)
+    worst = 0.0
+    for k, sc in enumerate(scenes):
+        line = full_step_error(orc, sc, f"batch scene {k} ({sc.name}, {sc.n_verts} verts), full substep")
+        worst = max(worst, line["max_err_rel"])
+    assert worst <= TOL_REL
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_precision_full_size_sampled_projection(orc, cfg):
+    """Full-size stack and wires after one substep: the oracle projects 300
+    sampled vertices on the GPU's planes from a perturbed candidate."""
+    sc = S.config(cfg)
+    x = torch.as_tensor(sc.x).cuda().contiguous()
+    v = torch.as_tensor(sc.v).cuda().contiguous()
+    ctx = ccfr.Context.from_scene(sc)
+    ctx.step(x, v)
+    L = orc.scene_scale(x.cpu().numpy())
+    ctx.build_regions(x)
+    reg = ctx.regions()
+    count = reg["count"].cpu().numpy()
+    K = ctx.capacity
+    rng = np.random.default_rng(17)
+    mov = np.nonzero((sc.x[:, 3] > 0) & (count > 0) & (count <= K))[0]
+    sample = rng.choice(mov, size=min(300, len(mov)), replace=False)
+    planes = reg["planes"][torch.as_tensor(sample).cuda()].cpu().numpy().astype(np.float64)
+    xg = x.clone()
+    noise = torch.as_tensor(rng.normal(scale=0.6 * sc.params["r"], size=(sc.n_verts, 3)).astype(np.float32)).cuda()
+    xg[:, :3] += noise * (xg[:, 3:4] > 0)
+    xio = xg.clone()
+    ctx.project(x, xio)
+    got = xio.cpu().numpy()[sample, :3].astype(np.float64)
+    xb = x.cpu().numpy()[sample, :3].astype(np.float64)
+    xp = xg.cpu().numpy()[sample, :3].astype(np.float64)
+    offs = np.concatenate([[0], np.cumsum(count[sample])]).astype(np.int64)
+    flat = np.concatenate([planes[i, :count[vtx]] for i, vtx in enumerate(sample)])
+    keys = np.arange(len(flat), dtype=np.uint64)
+    P = orc.make_params(sc.params, band=BAND_REL * L, capacity=0)
+    out, halt, band, nviol = orc.project(xb, xp, np.ones(len(sample)), offs, flat, keys, None, P)
+    ctx.close()
+    ok = band == 0
+    err = np.abs(got - out).max(axis=1)[ok] / L
+    name = "cloth_stack 4x256x256" if cfg == 2 else "wires 128x128x64"
+    line = report(f"{name}, sampled projection after one substep", err, ok.sum(), (~ok).sum(),
+                  {"verts": sc.n_verts, "sample": int(len(sample))})
+    # the oracle breaks equal sort keys by slot here; a handful of vertices whose
+    # walks meet equal keys on distinct planes may differ beyond the bar
+    assert np.mean(err <= TOL_REL) >= 0.995
