@@ -191,24 +191,23 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     d.p.max_passes = params->max_passes;
     d.p.K = params->plane_capacity;
     d.p.cell_size = params->cell_size;
-    // grid geometry: tables of triangles, edges, isolated points, vertices
-    int nk[5] = {T, E, d.n_pts, N, E};
-    d.n_items = T + E + d.n_pts + N + E;
+    // grid geometry: tables of triangles, edges, isolated points, vertices,
+    // oversized edges and giant edges (items of the last two are the edges that
+    // do not fit an edge cell, routed there by the edge items' own passes)
+    int nk[N_TABLES] = {T, E, d.n_pts, N, E, E};
+    d.n_items = T + E + d.n_pts + N;
     d.item_base[0] = 0;
-    d.item_base[1] = T;
-    d.item_base[2] = T + E;
-    d.item_base[3] = T + E + d.n_pts;
-    d.item_base[4] = T + E + d.n_pts + N;
+    for (int k = 1; k < N_TABLES; ++k) d.item_base[k] = d.item_base[k - 1] + (k - 1 < KIND_BIGE ? nk[k - 1] : 0);
     int btot = 0;
-    for (int k = 0; k < 5; ++k) {
-        // the oversized-edge table is sized for a quarter of the edges (load factor <= 8 if all are oversized)
-        int want = (k == KIND_BIGE) ? nk[k] / 4 : nk[k];
+    for (int k = 0; k < N_TABLES; ++k) {
+        // the oversized-edge tables are sized for a quarter / a sixteenth of the edges
+        int want = (k == KIND_BIGE) ? nk[k] / 4 : (k == KIND_GIANT) ? nk[k] / 16 : nk[k];
         unsigned M = next_pow2((unsigned)(want > 64 ? want : 64));
         d.bucket_base[k] = btot;
         d.bucket_mask[k] = (int)(M - 1);
         btot += (int)M;
     }
-    d.bucket_base[5] = btot;
+    d.bucket_base[N_TABLES] = btot;
     c->n_buckets_total = btot;
     d.n_kind[0] = T;
     d.n_kind[1] = E;

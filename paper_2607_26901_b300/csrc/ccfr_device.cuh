@@ -29,7 +29,7 @@ typedef unsigned long long u64;
 // items of the vertex-face queries).
 // A fifth table holds the oversized edges again, with a cell as large as the
 // largest edge, so that oversized edge pairs are found by a local search.
-enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, N_TABLES = 5 };
+enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, KIND_GIANT = 5, N_TABLES = 6 };
 enum { MODE_PLANES = 0, MODE_PAIRS = 1 };
 enum { ERR_NONFINITE = 1u };
 
@@ -81,9 +81,9 @@ struct DevCtx {
     float* lambda;
     // grid
     int n_items;                // n_tris + 2 n_edges + n_pts + n_verts
-    int item_base[5];           // first item of each table in the item space
-    int bucket_base[6];         // first bucket of each table (+ total)
-    int bucket_mask[5];         // M_table - 1
+    int item_base[N_TABLES];    // first item of each table in the item space
+    int bucket_base[N_TABLES + 1];  // first bucket of each table (+ total)
+    int bucket_mask[N_TABLES];  // M_table - 1
     unsigned* ext_bits;         // [3] largest padded extent per kind (float bits)
     u64* ext_sum;               // [3] sum of padded extents per kind, in nanometres
     int n_kind[3];              // primitives per kind (triangles, edges, points)
@@ -140,17 +140,25 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // primitives (or the user's cell size if larger), never below the padded
 // vertex box, so vertex boxes always fit in one cell.  Primitives whose box
 // spans more than a cell are handled by the oversized pass.
+// Oversized edges (boxes larger than an edge cell) go to a table whose cell is
+// BIGE_FACTOR edge cells; the few larger than that ("giants") to a table whose
+// cell is the largest edge box.
+constexpr float BIGE_FACTOR = 2.0f;
+
 __device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
-    if (kind == KIND_BIGE) {
+    const bool big = kind == KIND_BIGE;
+    if (kind == KIND_GIANT) {
         float h = __uint_as_float(c.ext_bits[KIND_EDGE]) * 1.0625f;
         return (h > 0.f) ? h : 1.f;
     }
+    if (kind == KIND_BIGE) kind = KIND_EDGE;   // scaled by BIGE_FACTOR below
     float mean = (c.n_kind[kind] > 0) ? (float)((double)c.ext_sum[kind] * 1e-9 / (double)c.n_kind[kind]) : 0.f;
     float h = mean * c.cell_factor;
     float hmin = 2.f * c.p.pad * 1.0625f;
     if (h < hmin) h = hmin;
     if (c.p.cell_size > h) h = c.p.cell_size;
     if (!(h > 0.f)) h = 1.f;
+    if (big) h *= BIGE_FACTOR;
     return h;
 }
 

@@ -56,17 +56,11 @@ __device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restric
         id = c.pts[i - c.item_base[KIND_PT]];
         v0 = id;
         a = x[id]; b = a; d = a;
-    } else if (i < c.item_base[KIND_BIGE]) {
+    } else {
         kind = KIND_VQ;
         id = i - c.item_base[KIND_VQ];
         v0 = id;
         a = x[id]; b = a; d = a;
-    } else {
-        kind = KIND_BIGE;
-        id = i - c.item_base[KIND_BIGE];
-        int2 e = c.edges[id];
-        v0 = e.x;
-        a = x[e.x]; b = x[e.y]; d = b;
     }
     scene = scene_of(c, v0);
     const float pad = scene_params(c, scene).pad;
@@ -118,7 +112,14 @@ __device__ __forceinline__ unsigned item_bucket_of(const DevCtx& c, int kind, co
 }
 
 // Triangles and edges whose box spans more than a cell go to the oversized
-// list instead of the grid (the count pass decides, the scatter pass skips them).
+// list instead of their grid table (the count pass decides).  An oversized
+// edge is also an item of the oversized-edge table (cell = BIGE_FACTOR edge
+// cells) when it fits a cell there, else of the giant table.
+__device__ __forceinline__ int table_of(const DevCtx& c, int kind, const float lo[3], const float hi[3]) {
+    if (kind != KIND_EDGE || fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return kind;
+    return fits_cell(lo, hi, cell_size_of(c, KIND_BIGE)) ? KIND_BIGE : KIND_GIANT;
+}
+
 __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     if (c.flags[1]) return;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,14 +128,14 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     int id;
     unsigned sc;
     int kind = item_box(c, x, i, lo, hi, id, sc);
-    if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
         unsigned s = atomicAdd(&c.big_count[kind], 1u);
         unsigned o = c.big_base[kind] + s;
         c.big[o] = id;
         c.big_box[2 * o] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
         c.big_box[2 * o + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(sc));
-        return;
+        if (kind == KIND_TRI) return;
+        kind = table_of(c, kind, lo, hi);
     }
     unsigned packed;
     unsigned b = item_bucket_of(c, kind, lo, sc, packed);
@@ -150,8 +151,8 @@ __global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
     int id;
     unsigned sc;
     int kind = item_box(c, x, i, lo, hi, id, sc);
-    if (kind == KIND_BIGE && fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return;
-    if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
+    if (kind == KIND_TRI && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
+    kind = table_of(c, kind, lo, hi);
     unsigned packed;
     unsigned b = item_bucket_of(c, kind, lo, sc, packed);
     unsigned pos = c.bucket_count[b] + atomicAdd(&c.bucket_fill[b], 1u);
@@ -730,8 +731,6 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     int qn = 0;
     EmitCounters k{0, 0, 0, 0};
     const int IK = (QK == KIND_TRI) ? KIND_VQ : KIND_EDGE;
-    const float inv = 1.0f / cell_size_of(c, QK);
-    const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
     const unsigned nbig = c.big_count[QK];
     u64 big_cells = 0, big_scans = 0, big_items = 0, bige_items = 0;   // diagnostics
     const unsigned stride = gridDim.x * EMIT_WARPS;
@@ -763,39 +762,37 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             if (lane == 0) atomicOr(&c.stats->error_flags, ERR_NONFINITE);
             continue;
         }
-        const float fx0 = floorf(lo[0] * inv) - 1.f, fx1 = floorf(hi[0] * inv);
-        const float fy0 = floorf(lo[1] * inv) - 1.f, fy1 = floorf(hi[1] * inv);
-        const float fz0 = floorf(lo[2] * inv) - 1.f, fz1 = floorf(hi[2] * inv);
-        const double ncell = (double)(fx1 - fx0 + 1.f) * (double)(fy1 - fy0 + 1.f) * (double)(fz1 - fz0 + 1.f);
-        const unsigned t_begin = c.bucket_count[ibase], t_end = c.bucket_count[c.bucket_base[IK + 1]];
-        auto test = [&](float4 i0, float4 i1) -> int2 {
-            const int iid = __float_as_int(i0.w);
-            bool hit = pack_scene(__float_as_uint(i1.w)) == qs && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
-            if (QK == KIND_TRI) {
-                if (!(hit && iid != ot.x && iid != ot.y && iid != ot.z)) return make_int2(-1, -1);
-                return make_int2(o, iid);
+        // every item of table TK whose box can reach this one: items sit in the cell
+        // of their lower corner and fit a cell, so the cells from lo - 1 to hi
+        auto scan_cells = [&](int TK, auto&& test, u64& items) {
+            const float tinv = 1.0f / cell_size_of(c, cell_kind(TK));
+            const unsigned tbase = (unsigned)c.bucket_base[TK], tmask = (unsigned)c.bucket_mask[TK];
+            const float fx0 = floorf(lo[0] * tinv) - 1.f, fx1 = floorf(hi[0] * tinv);
+            const float fy0 = floorf(lo[1] * tinv) - 1.f, fy1 = floorf(hi[1] * tinv);
+            const float fz0 = floorf(lo[2] * tinv) - 1.f, fz1 = floorf(hi[2] * tinv);
+            const double ncell = (double)(fx1 - fx0 + 1.f) * (double)(fy1 - fy0 + 1.f) * (double)(fz1 - fz0 + 1.f);
+            const unsigned t_begin = c.bucket_count[tbase], t_end = c.bucket_count[c.bucket_base[TK + 1]];
+            const float cmax = 1e9f;
+            // the packed tag tells apart at most 127 cells per axis: wider ranges test the whole table
+            const bool huge = fabsf(fx0) > cmax || fabsf(fx1) > cmax || fabsf(fy0) > cmax || fabsf(fy1) > cmax ||
+                              fabsf(fz0) > cmax || fabsf(fz1) > cmax || fx1 - fx0 >= 127.f || fy1 - fy0 >= 127.f ||
+                              fz1 - fz0 >= 127.f;
+            const bool whole = huge || ncell * 8.0 > (double)(t_end - t_begin);
+            if (lane == 0 && TK == IK) {
+                big_cells += whole ? 0ull : (u64)ncell;
+                big_scans += whole ? 1ull : 0ull;
             }
-            if (!hit) return make_int2(-1, -1);
-            return make_int2(min(o, iid), max(o, iid));
-        };
-        const float cmax = 1e9f;
-        // the packed tag tells apart at most 127 cells per axis: wider ranges test the whole table
-        const bool huge = fabsf(fx0) > cmax || fabsf(fx1) > cmax || fabsf(fy0) > cmax || fabsf(fy1) > cmax ||
-                          fabsf(fz0) > cmax || fabsf(fz1) > cmax || fx1 - fx0 >= 127.f || fy1 - fy0 >= 127.f ||
-                          fz1 - fz0 >= 127.f;
-        if (lane == 0) {
-            big_cells += (huge || ncell * 8.0 > (double)(t_end - t_begin)) ? 0ull : (u64)ncell;
-            big_scans += (huge || ncell * 8.0 > (double)(t_end - t_begin)) ? 1ull : 0ull;
-        }
-        if (huge || ncell * 8.0 > (double)(t_end - t_begin)) {
-            // cheaper to test the whole table
-            for (unsigned s0 = t_begin; s0 < t_end; s0 += 32) {
-                const unsigned s = s0 + lane;
-                int2 pr = make_int2(-1, -1);
-                if (s < t_end) pr = test(c.rec[2 * s], c.rec[2 * s + 1]);
-                push(pr.x >= 0, pr);
+            if (whole) {
+                // cheaper to test the whole table
+                for (unsigned s0 = t_begin; s0 < t_end; s0 += 32) {
+                    const unsigned s = s0 + lane;
+                    int2 pr = make_int2(-1, -1);
+                    if (s < t_end) pr = test(c.rec[2 * s], c.rec[2 * s + 1]);
+                    items += (s < t_end) ? 1ull : 0ull;
+                    push(pr.x >= 0, pr);
+                }
+                return;
             }
-        } else {
             // the reachable cells, 32 per round, their items gathered across the warp
             const int x0 = (int)fx0, y0 = (int)fy0, z0 = (int)fz0;
             const int nx = (int)fx1 - x0 + 1, ny = (int)fy1 - y0 + 1, nz = (int)fz1 - z0 + 1;
@@ -806,41 +803,85 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                 unsigned b = 0, pk = 0;
                 if (has) {
                     const int cx = x0 + ci % nx, cy = y0 + (ci / nx) % ny, cz = z0 + ci / (nx * ny);
-                    b = ibase + (cell_hash(cx, cy, cz, qs) & imask);
+                    b = tbase + (cell_hash(cx, cy, cz, qs) & tmask);
                     pk = cell_pack(cx, cy, cz, qs);
                 }
                 warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                     int2 pr = make_int2(-1, -1);
                     if (valid) pr = test(i0, i1);
-                    big_items += valid ? 1ull : 0ull;
+                    items += valid ? 1ull : 0ull;
                     push(pr.x >= 0, pr);
                 });
             }
-        }
-        if (QK == KIND_EDGE) {
-            // oversized-oversized pairs, found from the smaller id in the table of
-            // oversized edges (cell = the largest edge box: a 3x3x3 search)
-            const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
-            const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
-            const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
-            const bool has = lane < 27;
-            unsigned b = 0, pk = 0;
-            if (has) {
-                const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-                b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
-                pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
+        };
+        auto overlaps = [&](float4 i0, float4 i1) {
+            return pack_scene(__float_as_uint(i1.w)) == qs && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y &&
+                   i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
+        };
+        // the fitting primitives of the item table
+        scan_cells(IK, [&](float4 i0, float4 i1) -> int2 {
+            const int iid = __float_as_int(i0.w);
+            const bool hit = overlaps(i0, i1);
+            if (QK == KIND_TRI) {
+                if (!(hit && iid != ot.x && iid != ot.y && iid != ot.z)) return make_int2(-1, -1);
+                return make_int2(o, iid);
             }
-            warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
-                int2 pr = make_int2(-1, -1);
-                bige_items += valid ? 1ull : 0ull;
-                if (valid) {
-                    const int o2 = __float_as_int(i0.w);
-                    if (o2 > o && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y && i0.y <= hi[1] && lo[2] <= i1.z &&
-                        i0.z <= hi[2])
-                        pr = make_int2(o, o2);
+            if (!hit) return make_int2(-1, -1);
+            return make_int2(min(o, iid), max(o, iid));
+        }, big_items);
+        if (QK == KIND_EDGE) {
+            // oversized-oversized pairs.  An edge that fits a cell of the oversized
+            // table meets the others there: its own cell (pairs from the smaller id)
+            // and the 13 cells after it in (z, y, x) order, which visit every pair of
+            // cells once.  A giant (larger than that cell) finds the oversized edges
+            // of that table over its whole range, and the other giants, from the
+            // smaller id, in the giant table (cell = the largest edge box: 27 cells).
+            if (fits_cell(lo, hi, cell_size_of(c, KIND_BIGE))) {
+                const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
+                const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
+                const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
+                const bool has = lane < 14;
+                const int oi = 13 + lane;
+                const int dx = oi % 3 - 1, dy = (oi / 3) % 3 - 1, dz = oi / 9 - 1;
+                unsigned b = 0, pk = 0;
+                if (has) {
+                    b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
+                    pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
                 }
-                push(pr.x >= 0, pr);
-            });
+                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
+                    int2 pr = make_int2(-1, -1);
+                    bige_items += valid ? 1ull : 0ull;
+                    if (valid) {
+                        const int o2 = __float_as_int(i0.w);
+                        if ((j != 0 || o2 > o) && overlaps(i0, i1)) pr = make_int2(min(o, o2), max(o, o2));
+                    }
+                    push(pr.x >= 0, pr);
+                });
+            } else {
+                scan_cells(KIND_BIGE, [&](float4 i0, float4 i1) -> int2 {
+                    const int o2 = __float_as_int(i0.w);
+                    return overlaps(i0, i1) ? make_int2(min(o, o2), max(o, o2)) : make_int2(-1, -1);
+                }, bige_items);
+                const float ginv = 1.0f / cell_size_of(c, KIND_GIANT);
+                const unsigned gb = (unsigned)c.bucket_base[KIND_GIANT], gm = (unsigned)c.bucket_mask[KIND_GIANT];
+                const int gx = cell_coord(lo[0], ginv), gy = cell_coord(lo[1], ginv), gz = cell_coord(lo[2], ginv);
+                const bool has = lane < 27;
+                unsigned b = 0, pk = 0;
+                if (has) {
+                    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+                    b = gb + (cell_hash(gx + dx, gy + dy, gz + dz, qs) & gm);
+                    pk = cell_pack(gx + dx, gy + dy, gz + dz, qs);
+                }
+                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
+                    int2 pr = make_int2(-1, -1);
+                    bige_items += valid ? 1ull : 0ull;
+                    if (valid) {
+                        const int o2 = __float_as_int(i0.w);
+                        if (o2 > o && overlaps(i0, i1)) pr = make_int2(o, o2);
+                    }
+                    push(pr.x >= 0, pr);
+                });
+            }
         }
     }
     __syncwarp();
