@@ -1460,13 +1460,28 @@ __device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
 // (k_project_short); longer ones one warp per vertex (k_project_heavy).
 constexpr int SHORT_LIST = 32;
 
-// Projection, first kernel: one warp per vertex.  Vertices whose planes all
-// hold at the candidate (rho_k(x') >= 0: Alg. 2 returns x' after its first
-// pass), vertices without planes, and overflowed vertices are finished here;
-// the others are queued for k_project_short or k_project_heavy by the length
-// of their plane list.  STEP = true: x_b is the
-// collision-free iterate x_c (read and overwritten), candidates come from
-// x_in (the XPBD iterate), and the step is clamped to r.
+// Projection, first kernel.  Vertices whose planes all hold at the candidate
+// (rho_k(x') >= 0: Alg. 2 returns x' after its first pass), vertices without
+// planes, and overflowed vertices are finished here; the others are queued
+// for k_project_short or k_project_heavy by the length of their plane list.
+// One thread per vertex: a short list is scanned by its own thread; long and
+// overflowed lists are taken by the whole warp, one vertex after another.
+// STEP = true: x_b is the collision-free iterate x_c (read and overwritten),
+// candidates come from x_in (the XPBD iterate), and the step is clamped to r.
+template <bool STEP>
+__device__ __forceinline__ void queue_violated(const DevCtx& c, int v, int np, float mn, float dabs,
+                                               BlockCounters& bc) {
+    const int4 wk = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
+    if (np <= SHORT_LIST) {
+        const unsigned w = atomicAdd(&c.work_count[1], 1u);
+        c.work[c.n_verts - 1 - (int)w] = wk;
+    } else {
+        const unsigned w = atomicAdd(&c.work_count[0], 1u);
+        c.work[w] = wk;
+    }
+    atomicAdd(&bc.viol, 1u);
+}
+
 template <bool STEP>
 __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, const float4* x_in, float4* x_out,
                                                   unsigned char* halt_out) {
@@ -1474,48 +1489,66 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
     __shared__ BlockCounters bc;
     zero_block_counters(bc);
     const int lane = threadIdx.x & 31;
-    const int v = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    bool warp_job = false;
     if (v < c.n_verts) {
         const float4 X = x_b[v];
         const float4 XP = x_in[v];
         if (X.w > 0.f) {
-            const f3 y0 = sub(xyz(XP), xyz(X));
             const unsigned cnt = c.count[v];
             const int np = (int)min(cnt, (unsigned)c.p.K);
-            const bool over = cnt > (unsigned)c.p.K;
-            const float4* pl = c.planes + (size_t)v * c.p.K;
-            f3 y = y0;
-            bool queued = false;
-            if (over) {
-                // more planes than slots: bound the step by the smallest d of all planes
-                unsigned code = c.dmin_drop[v];
-                float dmin = (code == 0xFFFFFFFFu) ? 3.4e38f : ord2f(code);
-                float mn, dabs;
-                scan_min_rho(pl, np, mk(0.f, 0.f, 0.f), lane, mn, dabs);   // rho at x is d
-                y = clamp_len(y0, fmaxf(fminf(dmin, mn), 0.f));
-                if (lane == 0) atomicAdd(&bc.over, 1u);
-            } else if (np > 0) {
-                float mn, dabs;
-                scan_min_rho(pl, np, y0, lane, mn, dabs);
-                if (mn < 0.f) {
-                    queued = true;
-                    if (lane == 0) {
-                        const int4 wk = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
-                        if (np <= SHORT_LIST) {
-                            const unsigned w = atomicAdd(&c.work_count[1], 1u);
-                            c.work[c.n_verts - 1 - (int)w] = wk;
-                        } else {
-                            const unsigned w = atomicAdd(&c.work_count[0], 1u);
-                            c.work[w] = wk;
-                        }
-                        atomicAdd(&bc.viol, 1u);
-                    }
+            if (cnt > (unsigned)c.p.K || np > SHORT_LIST) {
+                warp_job = true;
+            } else {
+                const f3 y0 = sub(xyz(XP), xyz(X));
+                const float4* pl = c.planes + (size_t)v * c.p.K;
+                float mn = 3.4e38f, dabs = 0.f;
+                for (int j = 0; j < np; ++j) {
+                    const float4 P = pl[j];
+                    mn = fminf(mn, rho_at(y0, P));
+                    dabs = fmaxf(dabs, fabsf(P.w));
                 }
+                if (np > 0 && mn < 0.f)
+                    queue_violated<STEP>(c, v, np, mn, dabs, bc);
+                else
+                    finish_vertex<STEP, true>(c, 0, v, X, XP, y0, y0, false, pl, np, false, cnt, bc, x_out, halt_out);
             }
-            if (!queued) finish_vertex<STEP, false>(c, lane, v, X, XP, y0, y, false, pl, np, over, cnt, bc, x_out, halt_out);
-        } else if (!STEP && lane == 0 && halt_out) {
+        } else if (!STEP && halt_out) {
             halt_out[v] = 0;
         }
+    }
+    // long and overflowed lists: the warp takes them one at a time
+    unsigned pend = __ballot_sync(FULL, warp_job);
+    while (pend) {
+        const int l = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const int u = v - lane + l;
+        const float4 X = x_b[u];
+        const float4 XP = x_in[u];
+        const f3 y0 = sub(xyz(XP), xyz(X));
+        const unsigned cnt = c.count[u];
+        const int np = (int)min(cnt, (unsigned)c.p.K);
+        const bool over = cnt > (unsigned)c.p.K;
+        const float4* pl = c.planes + (size_t)u * c.p.K;
+        f3 y = y0;
+        bool queued = false;
+        if (over) {
+            // more planes than slots: bound the step by the smallest d of all planes
+            unsigned code = c.dmin_drop[u];
+            float dmin = (code == 0xFFFFFFFFu) ? 3.4e38f : ord2f(code);
+            float mn, dabs;
+            scan_min_rho(pl, np, mk(0.f, 0.f, 0.f), lane, mn, dabs);   // rho at x is d
+            y = clamp_len(y0, fmaxf(fminf(dmin, mn), 0.f));
+            if (lane == 0) atomicAdd(&bc.over, 1u);
+        } else {
+            float mn, dabs;
+            scan_min_rho(pl, np, y0, lane, mn, dabs);
+            if (mn < 0.f) {
+                queued = true;
+                if (lane == 0) queue_violated<STEP>(c, u, np, mn, dabs, bc);
+            }
+        }
+        if (!queued) finish_vertex<STEP, false>(c, lane, u, X, XP, y0, y, false, pl, np, over, cnt, bc, x_out, halt_out);
     }
     flush_block_counters(c, bc);
 }
@@ -1921,7 +1954,7 @@ void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned cha
     long threads = (long)c.n_verts * 32;
     cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) {
-        k_project<false><<<nblk(threads, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
+        k_project<false><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
         k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
         k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, xb, xio, xio, halt);
     }
@@ -1944,7 +1977,7 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
     if (tm) tm->mark(ST_XPBD, st);
     long threads = (long)c.n_verts * 32;
     cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
-    if (threads > 0) k_project<true><<<nblk(threads, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
+    if (threads > 0) k_project<true><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
     if (threads > 0) k_project_heavy<true><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_HEAVY, st);
@@ -2087,8 +2120,7 @@ extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const fl
     c.work_count = sc->work_count;
     c.n_sm = su->n_sm;
     k_static_dmin<<<nblk(n_verts, 256), 256, 0, s>>>(dmin_drop, sc->dmin, n_verts);
-    long threads = (long)n_verts * 32;
-    k_project<false><<<nblk(threads, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
+    k_project<false><<<nblk(n_verts, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
     k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                          (float4*)x_io, halt_out);
     k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, s>>>(c, (const float4*)x, (float4*)x_io,
