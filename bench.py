@@ -394,6 +394,10 @@ def run_batch(args, ws, rank, local, desc):
     ms = evs[0].elapsed_time(evs[-1])
     st = ctx.stats()
     value = movable * st["iterations"] / (ms / 1e3)
+    stage = {}
+    for _ in range(2):
+        for kname, kms in ctx.step_timed(x, v).items():
+            stage[kname] = stage.get(kname, 0.0) + kms / 2
     ctx.close()
     # plain: one context per scene, stepped one after another on the same stream
     ctxs, xs, vs = [], [], []
@@ -433,8 +437,14 @@ def run_batch(args, ws, rank, local, desc):
             "plain_per_scene": {"value": plain_value, "unit": UNIT, "ms_per_step": pms / pl_steps,
                                 "launch": "512 contexts, one ccfr_step each, one stream"},
             "batched_over_plain": value / plain_value,
+            "stage_ms_per_step": {k: round(v_, 4) for k, v_ in stage.items()},
             "stats_per_iter": {k: st[k] / max(st["iterations"], 1) for k in ("planes", "halts", "violated_verts",
-                                                                            "overflow_verts")},
+                                                                            "overflow_verts", "pairs_vf",
+                                                                            "pairs_ee", "pairs_vv")},
+            "max_planes": st["max_planes"],
+            "oversized_per_iter": {name: st["aux"][i] / max(st["iterations"], 1) for name, i in
+                                   (("big_tris", 3), ("big_edges", 4), ("big_cells", 10), ("big_table_scans", 11),
+                                    ("big_items", 12), ("bige_items", 13), ("big_cand", 14))},
         }), flush=True)
 
 

@@ -241,9 +241,11 @@ ccfr_status ccfr_project_static(const float* x, float* x_io, const float* planes
 ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params, int n_scenes, void* stream,
                               ccfr_ctx** out);
 
-/* Performance knobs (no effect on results): grid cell size in mean padded
- * primitive extents, emission blocks per SM, and plane capacity (a multiple
- * of 32; changing it reallocates the plane lists).  0 keeps a setting. */
+/* Performance knobs: grid cell size in mean padded primitive extents and
+ * emission blocks per SM (no effect on results), and plane capacity (a
+ * multiple of 32; changing it reallocates the plane lists; results change
+ * only for vertices that receive more planes than the capacity, whose step
+ * is then bounded by the overflow rule).  0 keeps a setting. */
 typedef struct {
     float cell_factor;
     int emit_blocks_per_sm;

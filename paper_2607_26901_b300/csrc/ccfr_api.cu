@@ -194,14 +194,14 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     // grid geometry: tables of triangles, edges, isolated points, vertices,
     // oversized edges and giant edges (items of the last two are the edges that
     // do not fit an edge cell, routed there by the edge items' own passes)
-    int nk[N_TABLES] = {T, E, d.n_pts, N, E, E};
+    int nk[N_TABLES] = {T, E, d.n_pts, N, E, E, E};
     d.n_items = T + E + d.n_pts + N;
     d.item_base[0] = 0;
     for (int k = 1; k < N_TABLES; ++k) d.item_base[k] = d.item_base[k - 1] + (k - 1 < KIND_BIGE ? nk[k - 1] : 0);
     int btot = 0;
     for (int k = 0; k < N_TABLES; ++k) {
         // the oversized-edge tables are sized for a quarter / a sixteenth of the edges
-        int want = (k == KIND_BIGE) ? nk[k] / 4 : (k == KIND_GIANT) ? nk[k] / 16 : nk[k];
+        int want = (k == KIND_BIGE || k == KIND_BIGS) ? nk[k] / 4 : (k == KIND_GIANT) ? nk[k] / 16 : nk[k];
         unsigned M = next_pow2((unsigned)(want > 64 ? want : 64));
         d.bucket_base[k] = btot;
         d.bucket_mask[k] = (int)(M - 1);

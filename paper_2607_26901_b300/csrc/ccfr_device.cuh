@@ -29,7 +29,11 @@ typedef unsigned long long u64;
 // items of the vertex-face queries).
 // A fifth table holds the oversized edges again, with a cell as large as the
 // largest edge, so that oversized edge pairs are found by a local search.
-enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, KIND_GIANT = 5, N_TABLES = 6 };
+// Grid tables: triangles, edges, isolated points, vertices (queried by
+// triangles), oversized moving edges, oversized static edges (every vertex
+// immobile), and giant edges.
+enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, KIND_BIGS = 5, KIND_GIANT = 6,
+       N_TABLES = 7 };
 enum { MODE_PLANES = 0, MODE_PAIRS = 1 };
 enum { ERR_NONFINITE = 1u };
 
@@ -146,12 +150,12 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 constexpr float BIGE_FACTOR = 2.0f;
 
 __device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
-    const bool big = kind == KIND_BIGE;
+    const bool big = kind == KIND_BIGE || kind == KIND_BIGS;
     if (kind == KIND_GIANT) {
         float h = __uint_as_float(c.ext_bits[KIND_EDGE]) * 1.0625f;
         return (h > 0.f) ? h : 1.f;
     }
-    if (kind == KIND_BIGE) kind = KIND_EDGE;   // scaled by BIGE_FACTOR below
+    if (big) kind = KIND_EDGE;   // scaled by BIGE_FACTOR below
     float mean = (c.n_kind[kind] > 0) ? (float)((double)c.ext_sum[kind] * 1e-9 / (double)c.n_kind[kind]) : 0.f;
     float h = mean * c.cell_factor;
     float hmin = 2.f * c.p.pad * 1.0625f;

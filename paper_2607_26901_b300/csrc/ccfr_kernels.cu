@@ -36,7 +36,7 @@ __device__ __forceinline__ f3 xyz(float4 a) { return mk(a.x, a.y, a.z); }
 // Padded box of item i of the concatenated item space (triangles, edges,
 // isolated points, vertices): lo = fl32(min - pad), hi = fl32(max + pad).
 __device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restrict__ x, int i,
-                                        float lo[3], float hi[3], int& id, unsigned& scene) {
+                                        float lo[3], float hi[3], int& id, unsigned& scene, bool* immobile = nullptr) {
     int kind, v0;
     float4 a, b, d;
     if (i < c.item_base[KIND_EDGE]) {
@@ -63,6 +63,7 @@ __device__ __forceinline__ int item_box(const DevCtx& c, const float4* __restric
         a = x[id]; b = a; d = a;
     }
     scene = scene_of(c, v0);
+    if (immobile) *immobile = !(a.w > 0.f || b.w > 0.f || d.w > 0.f);
     const float pad = scene_params(c, scene).pad;
     lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), pad);
     lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), pad);
@@ -113,11 +114,14 @@ __device__ __forceinline__ unsigned item_bucket_of(const DevCtx& c, int kind, co
 
 // Triangles and edges whose box spans more than a cell go to the oversized
 // list instead of their grid table (the count pass decides).  An oversized
-// edge is also an item of the oversized-edge table (cell = BIGE_FACTOR edge
-// cells) when it fits a cell there, else of the giant table.
-__device__ __forceinline__ int table_of(const DevCtx& c, int kind, const float lo[3], const float hi[3]) {
+// edge is also an item of an oversized-edge table (cell = BIGE_FACTOR edge
+// cells; one for moving and one for immobile edges) when it fits a cell
+// there, else of the giant table.
+__device__ __forceinline__ int table_of(const DevCtx& c, int kind, const float lo[3], const float hi[3],
+                                        bool immobile) {
     if (kind != KIND_EDGE || fits_cell(lo, hi, cell_size_of(c, KIND_EDGE))) return kind;
-    return fits_cell(lo, hi, cell_size_of(c, KIND_BIGE)) ? KIND_BIGE : KIND_GIANT;
+    if (!fits_cell(lo, hi, cell_size_of(c, KIND_BIGE))) return KIND_GIANT;
+    return immobile ? KIND_BIGS : KIND_BIGE;
 }
 
 __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
@@ -127,7 +131,8 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     float lo[3], hi[3];
     int id;
     unsigned sc;
-    int kind = item_box(c, x, i, lo, hi, id, sc);
+    bool immobile;
+    int kind = item_box(c, x, i, lo, hi, id, sc, &immobile);
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
         unsigned s = atomicAdd(&c.big_count[kind], 1u);
         unsigned o = c.big_base[kind] + s;
@@ -135,7 +140,7 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
         c.big_box[2 * o] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
         c.big_box[2 * o + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(sc));
         if (kind == KIND_TRI) return;
-        kind = table_of(c, kind, lo, hi);
+        kind = table_of(c, kind, lo, hi, immobile);
     }
     unsigned packed;
     unsigned b = item_bucket_of(c, kind, lo, sc, packed);
@@ -150,12 +155,15 @@ __global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
     float lo[3], hi[3];
     int id;
     unsigned sc;
-    int kind = item_box(c, x, i, lo, hi, id, sc);
+    bool immobile;
+    int kind = item_box(c, x, i, lo, hi, id, sc, &immobile);
     if (kind == KIND_TRI && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
-    kind = table_of(c, kind, lo, hi);
+    kind = table_of(c, kind, lo, hi, immobile);
     unsigned packed;
     unsigned b = item_bucket_of(c, kind, lo, sc, packed);
     unsigned pos = c.bucket_count[b] + atomicAdd(&c.bucket_fill[b], 1u);
+    // giant-table records carry the immobile flag in the id's top bit
+    if (kind == KIND_GIANT && immobile) id |= (int)0x80000000u;
     c.rec[2 * pos] = make_float4(lo[0], lo[1], lo[2], __int_as_float(id));
     c.rec[2 * pos + 1] = make_float4(hi[0], hi[1], hi[2], __uint_as_float(packed));
 }
@@ -699,7 +707,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32, 3) k_emit(DevCtx c, const flo
 // the per-cell pass over the fitting primitives this visits every candidate
 // pair exactly once.
 __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __restrict__ x, int kind, int id,
-                                             float lo[3], float hi[3]) {
+                                             float lo[3], float hi[3], bool& immobile) {
     float4 a, b, d;
     int v0;
     if (kind == KIND_TRI) {
@@ -712,6 +720,7 @@ __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __re
         a = x[e.x]; b = x[e.y]; d = b;
     }
     const unsigned scene = scene_of(c, v0);
+    immobile = !(a.w > 0.f || b.w > 0.f || d.w > 0.f);
     const float pad = scene_params(c, scene).pad;
     lo[0] = __fsub_rn(fminf(fminf(a.x, b.x), d.x), pad);
     lo[1] = __fsub_rn(fminf(fminf(a.y, b.y), d.y), pad);
@@ -753,7 +762,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nbig; u += stride) {
         const int o = c.big[c.big_base[QK] + u];
         float lo[3], hi[3];
-        const unsigned qs = prim_box(c, x, QK, o, lo, hi);
+        bool qimm;
+        const unsigned qs = prim_box(c, x, QK, o, lo, hi, qimm);
         int3 ot = make_int3(-1, -1, -1);
         if (QK == KIND_TRI) ot = c.tris[o];
         bool fin = isfinite(lo[0]) && isfinite(lo[1]) && isfinite(lo[2]) && isfinite(hi[0]) && isfinite(hi[1]) &&
@@ -830,57 +840,73 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             return make_int2(min(o, iid), max(o, iid));
         }, big_items);
         if (QK == KIND_EDGE) {
-            // oversized-oversized pairs.  An edge that fits a cell of the oversized
-            // table meets the others there: its own cell (pairs from the smaller id)
-            // and the 13 cells after it in (z, y, x) order, which visit every pair of
-            // cells once.  A giant (larger than that cell) finds the oversized edges
-            // of that table over its whole range, and the other giants, from the
-            // smaller id, in the giant table (cell = the largest edge box: 27 cells).
-            if (fits_cell(lo, hi, cell_size_of(c, KIND_BIGE))) {
-                const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
-                const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
-                const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
-                const bool has = lane < 14;
-                const int oi = 13 + lane;
-                const int dx = oi % 3 - 1, dy = (oi / 3) % 3 - 1, dz = oi / 9 - 1;
-                unsigned b = 0, pk = 0;
-                if (has) {
-                    b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
-                    pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
-                }
-                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
-                    int2 pr = make_int2(-1, -1);
-                    bige_items += valid ? 1ull : 0ull;
-                    if (valid) {
-                        const int o2 = __float_as_int(i0.w);
-                        if ((j != 0 || o2 > o) && overlaps(i0, i1)) pr = make_int2(min(o, o2), max(o, o2));
-                    }
-                    push(pr.x >= 0, pr);
-                });
-            } else {
-                scan_cells(KIND_BIGE, [&](float4 i0, float4 i1) -> int2 {
-                    const int o2 = __float_as_int(i0.w);
-                    return overlaps(i0, i1) ? make_int2(min(o, o2), max(o, o2)) : make_int2(-1, -1);
-                }, bige_items);
-                const float ginv = 1.0f / cell_size_of(c, KIND_GIANT);
-                const unsigned gb = (unsigned)c.bucket_base[KIND_GIANT], gm = (unsigned)c.bucket_mask[KIND_GIANT];
-                const int gx = cell_coord(lo[0], ginv), gy = cell_coord(lo[1], ginv), gz = cell_coord(lo[2], ginv);
+            // Oversized-oversized pairs; a pair of two immobile edges is never a
+            // candidate, so immobile edges only get found.  An edge that fits a
+            // cell of the oversized tables (cell = BIGE_FACTOR edge cells) meets
+            // the moving ones in their table: its own cell (pairs from the smaller
+            // id) and the 13 cells after it in (z, y, x) order, which visit every
+            // pair of cells once; and the immobile ones in theirs (27 cells).  A
+            // giant (larger than that cell) finds the edges of those tables over
+            // its whole range (an immobile giant only the moving ones), and a
+            // moving giant the other giants in the giant table (cell = the largest
+            // edge box: 27 cells): the immobile ones, and the moving ones from the
+            // smaller id.
+            auto cells27 = [&](int TK, auto&& accept) {
+                const float tinv = 1.0f / cell_size_of(c, TK);
+                const unsigned tb = (unsigned)c.bucket_base[TK], tm = (unsigned)c.bucket_mask[TK];
+                const int bx = cell_coord(lo[0], tinv), by = cell_coord(lo[1], tinv), bz = cell_coord(lo[2], tinv);
                 const bool has = lane < 27;
                 unsigned b = 0, pk = 0;
                 if (has) {
                     const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
-                    b = gb + (cell_hash(gx + dx, gy + dy, gz + dz, qs) & gm);
-                    pk = cell_pack(gx + dx, gy + dy, gz + dz, qs);
+                    b = tb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & tm);
+                    pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
                 }
                 warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                     int2 pr = make_int2(-1, -1);
                     bige_items += valid ? 1ull : 0ull;
-                    if (valid) {
-                        const int o2 = __float_as_int(i0.w);
-                        if (o2 > o && overlaps(i0, i1)) pr = make_int2(o, o2);
-                    }
+                    if (valid && overlaps(i0, i1)) pr = accept((unsigned)__float_as_int(i0.w));
                     push(pr.x >= 0, pr);
                 });
+            };
+            if (fits_cell(lo, hi, cell_size_of(c, KIND_BIGE))) {
+                if (!qimm) {
+                    const float binv = 1.0f / cell_size_of(c, KIND_BIGE);
+                    const unsigned bb = (unsigned)c.bucket_base[KIND_BIGE], bm = (unsigned)c.bucket_mask[KIND_BIGE];
+                    const int bx = cell_coord(lo[0], binv), by = cell_coord(lo[1], binv), bz = cell_coord(lo[2], binv);
+                    const bool has = lane < 14;
+                    const int oi = 13 + lane;
+                    const int dx = oi % 3 - 1, dy = (oi / 3) % 3 - 1, dz = oi / 9 - 1;
+                    unsigned b = 0, pk = 0;
+                    if (has) {
+                        b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
+                        pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
+                    }
+                    warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
+                        int2 pr = make_int2(-1, -1);
+                        bige_items += valid ? 1ull : 0ull;
+                        if (valid) {
+                            const int o2 = __float_as_int(i0.w);
+                            if ((j != 0 || o2 > o) && overlaps(i0, i1)) pr = make_int2(min(o, o2), max(o, o2));
+                        }
+                        push(pr.x >= 0, pr);
+                    });
+                    cells27(KIND_BIGS, [&](unsigned id2) { const int o2 = (int)id2; return make_int2(min(o, o2), max(o, o2)); });
+                }
+            } else {
+                auto any_pair = [&](float4 i0, float4 i1) -> int2 {
+                    const int o2 = __float_as_int(i0.w);
+                    return overlaps(i0, i1) ? make_int2(min(o, o2), max(o, o2)) : make_int2(-1, -1);
+                };
+                scan_cells(KIND_BIGE, any_pair, bige_items);
+                if (!qimm) {
+                    scan_cells(KIND_BIGS, any_pair, bige_items);
+                    cells27(KIND_GIANT, [&](unsigned id2) {
+                        const int o2 = (int)(id2 & 0x7FFFFFFFu);
+                        const bool imm2 = (id2 >> 31) != 0u;
+                        return (imm2 || o2 > o) ? make_int2(min(o, o2), max(o, o2)) : make_int2(-1, -1);
+                    });
+                }
             }
         }
     }
