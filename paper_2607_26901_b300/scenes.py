@@ -194,15 +194,37 @@ def cloth_on_sphere(n_side: int = 32, spacing: float = 0.01, jitter: float = 1e-
                      [ct, st], [edges_of_tris(ct), edges_of_tris(st)], params)
 
 
+def smooth_velocity(p: np.ndarray, speed: float, rng, n_waves: int = 4,
+                    wavelengths=(0.25, 1.0)) -> np.ndarray:
+    """Seeded smooth velocity field: per component a sum of n_waves sinusoids
+    sin(k . p + phase) with random directions, wavelengths uniform in the given
+    range (metres) and random phases and amplitudes, scaled so that the largest
+    magnitude of each component over the points is `speed`."""
+    v = np.zeros((len(p), 3))
+    for c in range(3):
+        acc = np.zeros(len(p))
+        for _ in range(n_waves):
+            d = rng.normal(size=3)
+            d /= np.linalg.norm(d)
+            k = 2.0 * np.pi / rng.uniform(*wavelengths) * d
+            acc += rng.uniform(0.5, 1.0) * np.sin(p @ k + rng.uniform(0.0, 2.0 * np.pi))
+        m = np.abs(acc).max()
+        v[:, c] = acc * (speed / m if m > 0 else 0.0)
+    return v
+
+
 def cloth_stack(n_side: int = 256, layers: int = 4, spacing: float = 4e-3,
                 gap: float = 2e-3, speed: float = 0.5, seed: int = 2, jitter: float = 0.0,
                 iters: int = 20, steps: int = 100, cloth_mass: float = 1e-3,
-                r: float = 2e-3, xi: float = 1e-3, plane_capacity: int = 1024) -> Scene:
+                r: float = 2e-3, xi: float = 1e-3, plane_capacity: int = 1024,
+                velocity: str = "iid") -> Scene:
     """Self-colliding stack of parallel cloth layers.
 
     Defaults: 4 layers of 256x256 vertices at 4 mm, 2 mm apart in y, every
     velocity component drawn iid from U(-speed, speed); r = 2 mm, xi = 1 mm,
-    20 iterations, no obstacle.
+    20 iterations, no obstacle.  velocity="smooth": the field of
+    smooth_velocity (4 sinusoids per component, wavelengths 0.25-1 m, scaled
+    to +-speed) instead of iid draws.
     """
     rng = np.random.default_rng(seed)
     ps, ts, es = [], [], []
@@ -213,7 +235,12 @@ def cloth_stack(n_side: int = 256, layers: int = 4, spacing: float = 4e-3,
         ts.append(t)
         es.append(edges_of_tris(t))
     n = sum(len(p) for p in ps)
-    vel = rng.uniform(-speed, speed, size=(n, 3))
+    if velocity == "smooth":
+        vel = smooth_velocity(np.concatenate(ps), speed, rng)
+    elif velocity == "iid":
+        vel = rng.uniform(-speed, speed, size=(n, 3))
+    else:
+        raise ValueError(f"velocity must be 'iid' or 'smooth', not {velocity!r}")
     params = default_params(r, xi, iters=iters, steps=steps, plane_capacity=plane_capacity)
     return _assemble("cloth_stack", ps, [np.full(len(p), 1.0 / cloth_mass) for p in ps],
                      ts, es, params, v=vel)
