@@ -69,6 +69,9 @@ typedef struct {
     int capacity;        /* plane capacity K per vertex, 0 = unbounded */
     int early_exit;      /* stop iterating once converged (R13) */
     double dt, g[3], compliance;
+    double k_resp;       /* response stiffness k (Sec. 3.3) */
+    double delta_v;      /* smooth transition width of the occlusion factor */
+    double mu_s, mu_k;   /* static and kinetic friction coefficients */
 } orc_params;
 
 /* ---------------------------------------------------------------- helpers */
@@ -756,6 +759,106 @@ typedef struct {
     int any_band;
 } orc_step_info;
 
+/* ------------------------------------------------------ response (Sec. 3.3)
+ *
+ * Soft repulsion and friction on a vertex's contacts, applied after the XPBD
+ * sweep and before the projection (Alg. 4, applyResponse; readings F1-F7).
+ * A contact c of vertex v is one of its planes: normal n_c and the pair's gap
+ * phi_c = dist - xi at the build position x.
+ *  F1  the signed distance along the contact normal at the iterate y, with
+ *      the other side held at its build position: g_c(y) = phi_c + n_c.(y - x);
+ *  F7  active contacts: g_c < delta, at most RESP_CAP of them, the innermost
+ *      by (g, pair key);
+ *  F2  visibility weight w_c = prod over the other active contacts j of
+ *      (1 - S((g_c - g_j) / delta_v)), S the cubic smoothstep 3t^2 - 2t^3
+ *      clamped to [0, 1]; gaps and weights at the iterate before the response;
+ *  F3  the energy (k/2) w_c max(0, delta - g_c)^2 as the XPBD constraint
+ *      C = max(0, delta - g_c(y)) with compliance 1/(k w_c), a fresh
+ *      multiplier every iteration (the contacts are rebuilt every iteration):
+ *      y += w C / (w + 1/(k w_c dt^2)) n_c, w the vertex's inverse mass;
+ *  F4  Gauss-Seidel over the active contacts in ascending (g, key) order;
+ *  F5  friction (position-based, after the repulsion): for each contact in
+ *      the same order whose repulsion moved y by depth > 0, t = the tangential
+ *      part of the vertex's displacement since the substep start; |t| <
+ *      mu_s depth: t is removed (static), else it is shortened by
+ *      min(mu_k depth, |t|) (kinetic);
+ *  F6  overflowed vertices (R16) get no response.
+ * *band is set when a decision falls within `band` of its threshold (an
+ * activation, a friction mode, the order of two distinct contacts). */
+#define RESP_CAP 32
+
+typedef struct { double g; u64 key; long k; } resp_entry;
+
+static int cmp_resp(const void *a, const void *b) {
+    const resp_entry *p = (const resp_entry *)a, *q = (const resp_entry *)b;
+    if (p->g != q->g) return p->g < q->g ? -1 : 1;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return 0;
+}
+
+static double smoothstep01(double t) {
+    if (t <= 0.0) return 0.0;
+    if (t >= 1.0) return 1.0;
+    return t * t * (3.0 - 2.0 * t);
+}
+
+void orc_response(double *y, const double *x, const double *xn, const double *planes4, const double *phi,
+                  const u64 *keys, long np, double w, const orc_params *P, int *band) {
+    if (!(P->delta > 0.0) || !(w > 0.0) || np <= 0) return;
+    resp_entry *all = (resp_entry *)malloc(sizeof(resp_entry) * np);
+    long nall = 0;
+    for (long k = 0; k < np; ++k) {
+        double d[3];
+        sub3(y, x, d);
+        double g = phi[k] + dot3(planes4 + 4 * k, d);
+        if (band && fabs(g - P->delta) <= P->band) *band = 1;
+        if (g < P->delta) { all[nall].g = g; all[nall].key = keys[k]; all[nall].k = k; nall++; }
+    }
+    qsort(all, nall, sizeof(resp_entry), cmp_resp);
+    int na = nall < RESP_CAP ? (int)nall : RESP_CAP;
+    if (band && nall > RESP_CAP && all[RESP_CAP].g - all[RESP_CAP - 1].g <= P->band) *band = 1;
+    for (int a = 1; a < na; ++a) {
+        const double *p0 = planes4 + 4 * all[a - 1].k, *p1 = planes4 + 4 * all[a].k;
+        int same = p0[0] == p1[0] && p0[1] == p1[1] && p0[2] == p1[2] && phi[all[a - 1].k] == phi[all[a].k];
+        if (band && !same && all[a].g - all[a - 1].g <= P->band) *band = 1;
+    }
+    double wt[RESP_CAP], depth[RESP_CAP];
+    for (int a = 0; a < na; ++a) {
+        double v = 1.0;
+        for (int b = 0; b < na; ++b)
+            if (b != a) v *= 1.0 - smoothstep01((all[a].g - all[b].g) / P->delta_v);
+        wt[a] = v;
+    }
+    for (int a = 0; a < na; ++a) {
+        const double *n = planes4 + 4 * all[a].k;
+        double d[3];
+        sub3(y, x, d);
+        double C = P->delta - (phi[all[a].k] + dot3(n, d));
+        depth[a] = 0.0;
+        if (!(C > 0.0) || !(wt[a] > 0.0)) continue;
+        double at = 1.0 / (P->k_resp * wt[a] * P->dt * P->dt);
+        double corr = w * C / (w + at);
+        for (int i = 0; i < 3; ++i) y[i] += corr * n[i];
+        depth[a] = corr;
+    }
+    if (P->mu_s > 0.0 || P->mu_k > 0.0) {
+        for (int a = 0; a < na; ++a) {
+            if (!(depth[a] > 0.0)) continue;
+            const double *n = planes4 + 4 * all[a].k;
+            double d[3], t[3];
+            sub3(y, xn, d);
+            double dn = dot3(d, n);
+            for (int i = 0; i < 3; ++i) t[i] = d[i] - dn * n[i];
+            double tl = norm3(t);
+            if (!(tl > 0.0)) continue;
+            if (band && fabs(tl - P->mu_s * depth[a]) <= P->band) *band = 1;
+            double f = (tl < P->mu_s * depth[a]) ? 1.0 : (P->mu_k * depth[a] / tl < 1.0 ? P->mu_k * depth[a] / tl : 1.0);
+            for (int i = 0; i < 3; ++i) y[i] -= f * t[i];
+        }
+    }
+    free(all);
+}
+
 /* One substep of Alg. 4 with the readings R12-R16.  x3, v3 are updated in
  * place (FP64).  x4w supplies inverse masses; rest[e] the rest lengths.
  * vband (optional, per vertex) collects band flags over all iterations. */
@@ -804,6 +907,27 @@ int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, 
                     xs[3 * b + k] -= w[b] * dl * dd[k] / L;
                 }
                 lambda[e] += dl;
+            }
+        }
+        /* contact response on every movable vertex, then the projection */
+        if (P->delta > 0.0) {
+            for (int v = 0; v < n; ++v) {
+                if (!(w[v] > 0) || isfinite(R->dlimit[v])) continue;
+                long o = R->offs[v], np = R->offs[v + 1] - R->offs[v];
+                if (np <= 0) continue;
+                double *planes4 = (double *)malloc(sizeof(double) * 4 * np);
+                double *phi = (double *)malloc(sizeof(double) * np);
+                u64 *keys = (u64 *)malloc(sizeof(u64) * np);
+                for (long k = 0; k < np; ++k) {
+                    for (int a = 0; a < 3; ++a) planes4[4 * k + a] = R->p[o + k].n[a];
+                    planes4[4 * k + 3] = R->p[o + k].d;
+                    phi[k] = R->p[o + k].phi;
+                    keys[k] = R->p[o + k].key;
+                }
+                int bd = 0;
+                orc_response(xs + 3 * v, xc + 3 * v, xn + 3 * v, planes4, phi, keys, np, w[v], P, &bd);
+                if (bd) bflag[v] = 1;
+                free(planes4); free(phi); free(keys);
             }
         }
         memcpy(pre, xs, N3);

@@ -31,6 +31,7 @@ class OrcParams(C.Structure):
         ("band", C.c_double),
         ("n_max", C.c_int), ("iters", C.c_int), ("capacity", C.c_int), ("early_exit", C.c_int),
         ("dt", C.c_double), ("g", C.c_double * 3), ("compliance", C.c_double),
+        ("k_resp", C.c_double), ("delta_v", C.c_double), ("mu_s", C.c_double), ("mu_k", C.c_double),
     ]
 
 
@@ -82,6 +83,8 @@ def lib():
         _lib.orc_count_edge_triangle_intersections.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int]
         _lib.orc_closest_point_triangle.argtypes = [P, P, P, P, P, P]
         _lib.orc_closest_segments.argtypes = [P, P, P, P, P, P]
+        _lib.orc_response.argtypes = [P, P, P, P, P, P, C.c_long, C.c_double, C.POINTER(OrcParams),
+                                      C.POINTER(C.c_int)]
     return _lib
 
 
@@ -109,6 +112,9 @@ def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
     o.dt = p["dt"]
     o.g[0], o.g[1], o.g[2] = g
     o.compliance = p.get("compliance", 0.0)
+    o.k_resp = p.get("k_resp", 0.0)
+    o.delta_v = p.get("delta_v", 0.0)
+    o.mu_s, o.mu_k = p.get("mu_s", 0.0), p.get("mu_k", 0.0)
     return o
 
 
@@ -186,6 +192,22 @@ def ortho_sequence(x0, normals, b, eps_dep=1e-12):
     out = np.zeros(3)
     L.orc_ortho_sequence(_p(x0), _p(normals), _p(b), len(b), C.c_double(eps_dep), _p(out))
     return out
+
+
+def response(y, x, xn, planes4, phi, keys, w, params: OrcParams):
+    """Contact response (Sec. 3.3, readings F1-F7) of one vertex at iterate y
+    with build position x and substep start xn.  Returns (y', band)."""
+    L = lib()
+    y = np.array(y, dtype=np.float64).copy()
+    x = _c(x, np.float64)
+    xn = _c(xn, np.float64)
+    planes4 = _c(planes4, np.float64).reshape(-1, 4)
+    phi = _c(phi, np.float64)
+    keys = _c(keys, np.uint64)
+    band = C.c_int(0)
+    L.orc_response(_p(y), _p(x), _p(xn), _p(planes4), _p(phi), _p(keys), len(phi), C.c_double(w),
+                   C.byref(params), C.byref(band))
+    return y, band.value
 
 
 def edge_colors(edges, n):

@@ -46,7 +46,9 @@ class Scene:
 
 
 def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 / 60.0,
-                   iters: int = 10, steps: int = 20, plane_capacity: int = 64) -> dict:
+                   iters: int = 10, steps: int = 20, plane_capacity: int = 64,
+                   k_resp: float = 0.0, delta_v: float | None = None, mu_s: float = 0.0,
+                   mu_k: float = 0.0) -> dict:
     """Parameter set of one scene.
 
     r, xi, delta follow the paper's parameter table (Table 3); eps is the
@@ -54,7 +56,10 @@ def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 /
     dependence tolerance of Alg. 1, n_max the pass budget of Alg. 2, and
     tau_feas the tolerance of the final feasibility check.  ``pad`` is the
     AABB enlargement r + xi/2 + delta/2 of Sec. 4.1, rounded once to binary32
-    so that every consumer evaluates the same candidate predicate.
+    so that every consumer evaluates the same candidate predicate.  The
+    contact response of Sec. 3.3 acts when delta > 0: stiffness k_resp,
+    occlusion transition width delta_v (default delta / 2), friction
+    coefficients mu_s, mu_k.
     """
     pad = np.float32(np.float32(r) + np.float32(0.5) * np.float32(xi)
                      + np.float32(0.5) * np.float32(delta))
@@ -62,7 +67,8 @@ def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 /
                 eps=1e-6, eps_dep=1e-6, tau_feas=1e-7, n_max=1,
                 dt=float(dt), iters=int(iters), steps=int(steps),
                 gravity=(0.0, -9.81, 0.0), compliance=0.0,
-                plane_capacity=int(plane_capacity))
+                plane_capacity=int(plane_capacity), k_resp=float(k_resp),
+                delta_v=float(0.5 * delta if delta_v is None else delta_v), mu_s=float(mu_s), mu_k=float(mu_k))
 
 
 def canonical_edges(e: np.ndarray) -> np.ndarray:
@@ -403,14 +409,20 @@ def two_particles(dist: float = 0.01, speed: float = 1.0, xi: float = 2e-3, r: f
 
 
 def particle_over_floor(height: float = 0.004, size: float = 0.05, r: float = 1e-3,
-                        xi: float = 1e-3, iters: int = 10, steps: int = 30) -> Scene:
-    """One particle above a static two-triangle floor at y = 0."""
+                        xi: float = 1e-3, iters: int = 10, steps: int = 30, delta: float = 0.0,
+                        k_resp: float = 0.0, mu_s: float = 0.0, mu_k: float = 0.0,
+                        v0=(0.0, 0.0, 0.0)) -> Scene:
+    """One particle (mass 1 g) above a static two-triangle floor at y = 0,
+    optionally with the contact response and an initial velocity."""
     q = np.array([[0.02, height, -0.01]])
     f = np.array([[-size, 0, -size], [size, 0, -size], [size, 0, size], [-size, 0, size]])
-    params = default_params(r, xi, iters=iters, steps=steps)
+    params = default_params(r, xi, iters=iters, steps=steps, delta=delta, k_resp=k_resp, mu_s=mu_s,
+                            mu_k=mu_k)
+    vel = np.zeros((5, 3))
+    vel[0] = v0
     return _assemble("particle_over_floor", [q, f], [np.full(1, 1e3), np.zeros(4)],
                      [None, np.array([[0, 1, 2], [0, 2, 3]])],
-                     [None, edges_of_tris(np.array([[0, 1, 2], [0, 2, 3]]))], params)
+                     [None, edges_of_tris(np.array([[0, 1, 2], [0, 2, 3]]))], params, v=vel)
 
 
 def card_stack(n_cards: int = 52, xi: float = 1e-3, size: float = 0.06, gap_factor: float = 1.5,
