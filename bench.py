@@ -41,6 +41,10 @@ WORKLOADS = {
                            "self-colliding stack, smooth-field variant: 4 layers of 256x256 cloth (262,144 verts) "
                            "2 mm apart, velocities a seeded sum of 4 sinusoids per component (wavelengths 0.25-1 m) "
                            "scaled to +-0.5 m/s, r=2 mm, xi=1 mm, dt=1/60 s, 20 XPBD iterations"),
+    "cloth_stack_response": (lambda seed: S.with_response(S.cloth_stack(seed=seed), delta=5e-4, k_resp=2.0,
+                                                          mu_s=0.3, mu_k=0.2),
+                             "self-colliding stack with the contact response of Sec. 3.3 on: repulsion range "
+                             "0.5 mm, k = 2 N/m, occlusion width 0.25 mm, friction mu_s 0.3 / mu_k 0.2"),
     "cloth_stack_128": (lambda seed: S.cloth_stack(n_side=128, seed=seed),
                         "profiling case of the stack recipe: 4 layers of 128x128 cloth (65,536 verts)"),
     "wires_64": (lambda seed: S.wires(n_grid=64, seed=seed),

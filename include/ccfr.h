@@ -70,6 +70,14 @@ typedef struct {
     float gravity[3];
     float compliance;     /* XPBD compliance of the edge-distance constraints             */
     unsigned flags;       /* CCFR_FLAG_*                                                   */
+    /* Contact response and friction (Sec. 3.3), active when delta > 0: the
+     * energy (k/2) w_c max(0, delta - g_c)^2 per contact as an XPBD constraint
+     * of compliance 1/(k w_c), w_c the smooth occlusion weight of transition
+     * width delta_v, then position-based static / kinetic friction.  Needs 4
+     * more bytes per plane slot (each plane's gap). */
+    float response_stiffness;  /* k (>= 0)                                                */
+    float delta_v;        /* occlusion transition width (> 0 when delta > 0)             */
+    float mu_s, mu_k;     /* static and kinetic friction coefficients (>= 0)             */
 } ccfr_params;
 
 /* Topology of one scene.  All arrays are device pointers, read at ccfr_create
@@ -159,14 +167,14 @@ ccfr_status ccfr_project(ccfr_ctx* ctx, const float* x, float* x_io, unsigned ch
 ccfr_status ccfr_step(ccfr_ctx* ctx, float* x, float* v, void* stream);
 
 /* Number of stages reported by ccfr_step_timed. */
-#define CCFR_N_STAGES 16
+#define CCFR_N_STAGES 17
 
 /* ccfr_step launched kernel by kernel with CUDA events between the stages
  * (prediction, grid extent, grid count, grid scan, grid scatter, vertex-face
  * narrow phase, edge-edge narrow phase, point-point narrow phase, XPBD sweep,
  * projection scan, bookkeeping, work units, oversized vertex-face and
  * edge-edge passes, projection of the violated vertices with long and with
- * short plane lists): the per-stage split of the paper's timing table
+ * short plane lists, contact response): the per-stage split of the paper's timing table
  * (Table 1: broad, narrow, resolution, XPBD).  stage_ms (host, n_stages >=
  * CCFR_N_STAGES doubles) receives milliseconds summed over the iterations.
  * Synchronises `stream`. */

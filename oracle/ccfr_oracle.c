@@ -816,11 +816,13 @@ void orc_response(double *y, const double *x, const double *xn, const double *pl
     }
     qsort(all, nall, sizeof(resp_entry), cmp_resp);
     int na = nall < RESP_CAP ? (int)nall : RESP_CAP;
-    if (band && nall > RESP_CAP && all[RESP_CAP].g - all[RESP_CAP - 1].g <= P->band) *band = 1;
-    for (int a = 1; a < na; ++a) {
+    /* near-tied gaps decide an order; two contacts whose normals agree to
+     * 1e-4 commute to within 1e-4 of a correction (<= delta), far below any
+     * tolerance, so only near-ties of distinctly oriented contacts are bands */
+    for (int a = 1; a < (nall > RESP_CAP ? RESP_CAP + 1 : na); ++a) {
         const double *p0 = planes4 + 4 * all[a - 1].k, *p1 = planes4 + 4 * all[a].k;
-        int same = p0[0] == p1[0] && p0[1] == p1[1] && p0[2] == p1[2] && phi[all[a - 1].k] == phi[all[a].k];
-        if (band && !same && all[a].g - all[a - 1].g <= P->band) *band = 1;
+        double dn = fmax(fabs(p0[0] - p1[0]), fmax(fabs(p0[1] - p1[1]), fabs(p0[2] - p1[2])));
+        if (band && dn > 1e-4 && all[a].g - all[a - 1].g <= P->band) *band = 1;
     }
     double wt[RESP_CAP], depth[RESP_CAP];
     for (int a = 0; a < na; ++a) {

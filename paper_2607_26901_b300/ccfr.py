@@ -34,7 +34,8 @@ class Params(C.Structure):
                 ("eps_retract", C.c_float), ("eps_dep", C.c_float), ("tau_feas", C.c_float),
                 ("max_passes", C.c_int), ("solver_iters", C.c_int), ("plane_capacity", C.c_int),
                 ("cell_size", C.c_float), ("cell_factor", C.c_float), ("dt", C.c_float), ("gravity", C.c_float * 3),
-                ("compliance", C.c_float), ("flags", C.c_uint)]
+                ("compliance", C.c_float), ("flags", C.c_uint),
+                ("response_stiffness", C.c_float), ("delta_v", C.c_float), ("mu_s", C.c_float), ("mu_k", C.c_float)]
 
 
 class Mesh(C.Structure):
@@ -158,6 +159,9 @@ def make_params(p: dict, flags: int = 0, plane_capacity: int | None = None,
     o.gravity[0], o.gravity[1], o.gravity[2] = g
     o.compliance = p.get("compliance", 0.0)
     o.flags = flags
+    o.response_stiffness = p.get("k_resp", 0.0)
+    o.delta_v = p.get("delta_v", 0.0)
+    o.mu_s, o.mu_k = p.get("mu_s", 0.0), p.get("mu_k", 0.0)
     return o
 
 
@@ -288,7 +292,7 @@ class Context:
 
     def step_timed(self, x, v, stream=None) -> dict:
         """One step launched kernel by kernel; returns {stage: ms}."""
-        n = 16
+        n = 17
         out = (C.c_double * n)()
         _check(lib().ccfr_step_timed(self.h, _ptr(x), _ptr(v), out, n, _stream(stream)), "ccfr_step_timed")
         return {lib().ccfr_stage_name(i).decode(): out[i] for i in range(n)}

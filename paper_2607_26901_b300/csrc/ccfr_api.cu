@@ -86,6 +86,9 @@ ccfr_status check_params(const ccfr_params* p) {
     if (p->plane_capacity < 32 || p->plane_capacity % 32 != 0 || p->plane_capacity > 65536) return CCFR_ERR_INVALID_ARG;
     if (!(p->cell_size >= 0.f) || !(p->dt > 0.f) || !(p->compliance >= 0.f)) return CCFR_ERR_INVALID_ARG;
     if (!(p->cell_factor >= 0.f) || p->cell_factor > 64.f) return CCFR_ERR_INVALID_ARG;
+    if (!(p->response_stiffness >= 0.f) || !(p->mu_s >= 0.f) || !(p->mu_k >= 0.f) || !(p->delta_v >= 0.f))
+        return CCFR_ERR_INVALID_ARG;
+    if (p->delta > 0.f && !(p->delta_v > 0.f)) return CCFR_ERR_INVALID_ARG;
     return CCFR_OK;
 }
 
@@ -106,7 +109,7 @@ void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer
 const char* kStageNames[N_STAGES] = {"predict", "grid_extent", "grid_count", "grid_scan", "grid_scatter",
                                      "emit_vf", "emit_ee", "emit_pp", "xpbd", "project", "misc",
                                      "grid_units", "emit_vf_big", "emit_ee_big", "project_heavy",
-                                     "project_short"};
+                                     "project_short", "response"};
 
 }  // namespace
 
@@ -191,6 +194,11 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     d.p.max_passes = params->max_passes;
     d.p.K = params->plane_capacity;
     d.p.cell_size = params->cell_size;
+    d.p.delta = params->delta;
+    d.p.k_resp = params->response_stiffness;
+    d.p.delta_v = params->delta_v;
+    d.p.mu_s = params->mu_s;
+    d.p.mu_k = params->mu_k;
     // grid geometry: tables of triangles, edges, isolated points, vertices,
     // oversized edges and giant edges (items of the last two are the edges that
     // do not fit an edge cell, routed there by the edge items' own passes)
@@ -232,6 +240,8 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     size_t NK = (size_t)N * params->plane_capacity;
     bool ok = true;
     ok &= dalloc(c, &d.planes, NK) == cudaSuccess;
+    // the contact response reads each plane's gap phi (only stored when it is on)
+    if (params->delta > 0.f) ok &= dalloc(c, &d.phi, NK) == cudaSuccess;
     if (params->flags & CCFR_FLAG_STORE_KEYS) ok &= dalloc(c, &d.keys, NK) == cudaSuccess;
     ok &= dalloc(c, &d.count, N) == cudaSuccess;
     ok &= dalloc(c, &d.dmin_drop, N) == cudaSuccess;
@@ -359,7 +369,10 @@ ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params
             params[k].eps_retract != params[0].eps_retract || params[k].eps_dep != params[0].eps_dep ||
             params[k].tau_feas != params[0].tau_feas || params[k].compliance != params[0].compliance ||
             params[k].gravity[0] != params[0].gravity[0] || params[k].gravity[1] != params[0].gravity[1] ||
-            params[k].gravity[2] != params[0].gravity[2] || params[k].flags != params[0].flags)
+            params[k].gravity[2] != params[0].gravity[2] || params[k].flags != params[0].flags ||
+            params[k].delta != params[0].delta || params[k].response_stiffness != params[0].response_stiffness ||
+            params[k].delta_v != params[0].delta_v || params[k].mu_s != params[0].mu_s ||
+            params[k].mu_k != params[0].mu_k)
             return CCFR_ERR_INVALID_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -613,21 +626,26 @@ ccfr_status ccfr_set_tuning(ccfr_ctx* c, const ccfr_tuning* t) {
         size_t NK = (size_t)c->dc.n_verts * t->plane_capacity;
         float4* planes = nullptr;
         unsigned long long* keys = nullptr;
+        float* phi = nullptr;
         if (cudaMalloc((void**)&planes, (NK ? NK : 1) * sizeof(float4)) != cudaSuccess) {
             cudaGetLastError();
             return CCFR_ERR_OOM;
         }
-        if (c->dc.keys && cudaMalloc((void**)&keys, (NK ? NK : 1) * sizeof(unsigned long long)) != cudaSuccess) {
+        if ((c->dc.keys && cudaMalloc((void**)&keys, (NK ? NK : 1) * sizeof(unsigned long long)) != cudaSuccess) ||
+            (c->dc.phi && cudaMalloc((void**)&phi, (NK ? NK : 1) * sizeof(float)) != cudaSuccess)) {
             cudaGetLastError();
             cudaFree(planes);
+            if (keys) cudaFree(keys);
             return CCFR_ERR_OOM;
         }
         for (auto& p : c->allocs) {
             if (p == (void*)c->dc.planes) { cudaFree(p); p = planes; }
             else if (c->dc.keys && p == (void*)c->dc.keys) { cudaFree(p); p = keys; }
+            else if (c->dc.phi && p == (void*)c->dc.phi) { cudaFree(p); p = phi; }
         }
         c->dc.planes = planes;
         if (c->dc.keys) c->dc.keys = keys;
+        if (c->dc.phi) c->dc.phi = phi;
         c->dc.p.K = t->plane_capacity;
         c->prm.plane_capacity = t->plane_capacity;
         c->regions_valid = false;

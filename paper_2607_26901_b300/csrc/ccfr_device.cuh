@@ -70,6 +70,7 @@ struct DevParams {
     int max_passes;
     int K;
     float cell_size;
+    float delta, k_resp, delta_v, mu_s, mu_k;   // contact response (Sec. 3.3); on when delta > 0
 };
 
 // Everything a kernel needs, passed by value.
@@ -105,6 +106,7 @@ struct DevCtx {
     float4* rec;                // [2 * n_items]
     // regions
     float4* planes;
+    float* phi;                 // [n_verts * K] gap phi of each plane's pair (contact response only)
     u64* keys;                  // may be null
     unsigned* count;
     unsigned* dmin_drop;

@@ -9,7 +9,7 @@ namespace ccfr {
 enum Stage {
     ST_PREDICT = 0, ST_GRID_EXTENT, ST_GRID_COUNT, ST_GRID_SCAN, ST_GRID_SCATTER,
     ST_EMIT_VF, ST_EMIT_EE, ST_EMIT_PP, ST_XPBD, ST_PROJECT, ST_MISC, ST_GRID_UNITS, ST_EMIT_VF_BIG,
-    ST_EMIT_EE_BIG, ST_PROJECT_HEAVY, ST_PROJECT_SHORT, N_STAGES
+    ST_EMIT_EE_BIG, ST_PROJECT_HEAVY, ST_PROJECT_SHORT, ST_RESPONSE, N_STAGES
 };
 
 struct StageTimer {

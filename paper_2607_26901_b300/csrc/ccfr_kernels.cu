@@ -255,12 +255,13 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(DevCtx c, unsigned*
 
 // ------------------------------------------------------- plane emission
 
-__device__ __forceinline__ void emit_plane(const DevCtx& c, int v, f3 n, float d, u64 key) {
+__device__ __forceinline__ void emit_plane(const DevCtx& c, int v, f3 n, float d, float phi, u64 key) {
     unsigned slot = atomicAdd(&c.count[v], 1u);
     if (slot < (unsigned)c.p.K) {
         size_t o = (size_t)v * c.p.K + slot;
         c.planes[o] = make_float4(n.x, n.y, n.z, d);
         if (c.keys) c.keys[o] = key;
+        if (c.phi) c.phi[o] = phi;
     } else {
         atomicMin(&c.dmin_drop[v], f2ord(d));
     }
@@ -345,11 +346,11 @@ __device__ int narrow_vf(const DevCtx& c, int p, float4 P, int t, int3 T, float4
     f3 mn = mk(-n.x, -n.y, -n.z);
     u64 key = pair_key(0, p, t);
     int k = 0;
-    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, key); ++k; }
+    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, phi, key); ++k; }
     float df = (wf / W) * phi;
-    if (A.w > 0.f) { emit_plane(c, T.x, mn, df, key); ++k; }
-    if (B.w > 0.f) { emit_plane(c, T.y, mn, df, key); ++k; }
-    if (C.w > 0.f) { emit_plane(c, T.z, mn, df, key); ++k; }
+    if (A.w > 0.f) { emit_plane(c, T.x, mn, df, phi, key); ++k; }
+    if (B.w > 0.f) { emit_plane(c, T.y, mn, df, phi, key); ++k; }
+    if (C.w > 0.f) { emit_plane(c, T.z, mn, df, phi, key); ++k; }
     return k;
 }
 
@@ -442,10 +443,10 @@ __device__ int narrow_ee(const DevCtx& c, const float4* __restrict__ x, int e, i
     u64 key = pair_key(1, e, f);
     float da = (wa / W) * phi, db = (wb / W) * phi;
     int k = 0;
-    if (A0.w > 0.f) { emit_plane(c, E.x, n, da, key); ++k; }
-    if (A1.w > 0.f) { emit_plane(c, E.y, n, da, key); ++k; }
-    if (B0.w > 0.f) { emit_plane(c, F.x, mn, db, key); ++k; }
-    if (B1.w > 0.f) { emit_plane(c, F.y, mn, db, key); ++k; }
+    if (A0.w > 0.f) { emit_plane(c, E.x, n, da, phi, key); ++k; }
+    if (A1.w > 0.f) { emit_plane(c, E.y, n, da, phi, key); ++k; }
+    if (B0.w > 0.f) { emit_plane(c, F.x, mn, db, phi, key); ++k; }
+    if (B1.w > 0.f) { emit_plane(c, F.y, mn, db, phi, key); ++k; }
     return k;
 }
 
@@ -462,8 +463,8 @@ __device__ int narrow_pp(const DevCtx& c, int p, int q, float4 P, float4 Q) {
     f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
     u64 key = pair_key(2, p, q);
     int k = 0;
-    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, key); ++k; }
-    if (Q.w > 0.f) { emit_plane(c, q, mk(-n.x, -n.y, -n.z), (Q.w / W) * phi, key); ++k; }
+    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, phi, key); ++k; }
+    if (Q.w > 0.f) { emit_plane(c, q, mk(-n.x, -n.y, -n.z), (Q.w / W) * phi, phi, key); ++k; }
     return k;
 }
 
@@ -1801,6 +1802,234 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
     flush_block_counters(c, bc);
 }
 
+// ------------------------------------------------------------ response
+//
+// Contact response and friction (Sec. 3.3), after the XPBD sweep and before
+// the projection (Alg. 4, applyResponse).  A contact is one of the vertex's
+// planes: normal n_c and its pair's gap phi_c beyond xi at the build position x.
+//  - signed distance along the normal at the iterate y, the other side at its
+//    build position: g_c = phi_c + n_c . (y - x);
+//  - active contacts: g_c < delta, the RESP_CAP innermost in the order of
+//    Alg. 2's planes with g as the key (g, plane hash, plane bits, slot);
+//  - visibility weight w_c = prod over the other active contacts j of
+//    (1 - S((g_c - g_j) / delta_v)), S the cubic smoothstep clamped to [0, 1],
+//    at the iterate before the response;
+//  - in that order, each active contact once (Gauss-Seidel, fresh multiplier):
+//    C = max(0, delta - g_c(y)), compliance 1 / (k w_c):
+//    y += w C / (w + 1 / (k w_c dt^2)) n_c;
+//  - friction, same order, for each contact that moved y by depth > 0: t = the
+//    tangential part of the displacement since the substep start; removed if
+//    |t| < mu_s depth, else shortened by min(mu_k depth, |t|).
+// Vertices over the plane capacity get no response.  Short plane lists are
+// handled one thread per vertex, long ones by the warp.
+constexpr int RESP_CAP = 32;
+constexpr int RESP_POOL = 256;   // active contacts of a long list held before the innermost are chosen
+constexpr int RESP_WARPS = 4;
+
+__device__ __forceinline__ float smoothstep01(float t) {
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    return t * t * (3.f - 2.f * t);
+}
+
+// Visibility weight of contact a among the na active ones (gaps ag).
+__device__ __forceinline__ float occlusion_weight(const DevCtx& c, const float* ag, int na, int a) {
+    const float inv_dv = 1.f / c.p.delta_v;
+    float w = 1.f;
+    for (int b = 0; b < na; ++b)
+        if (b != a) w *= 1.f - smoothstep01((ag[a] - ag[b]) * inv_dv);
+    return w;
+}
+
+// The response of one vertex once its active contacts are known, in order,
+// with their weights: Gauss-Seidel repulsion, then friction.
+__device__ __forceinline__ f3 respond(const DevCtx& c, int v, f3 x, f3 y, float wv, const float4* pl,
+                                      const float* ph, const int* aj, const float* wt, int na) {
+    float depth[RESP_CAP];
+    const float dt2 = c.p.dt * c.p.dt;
+    for (int a = 0; a < na; ++a) {
+        const f3 n = xyz(pl[aj[a]]);
+        const float C = c.p.delta - (ph[aj[a]] + dot(n, sub(y, x)));
+        depth[a] = 0.f;
+        if (!(C > 0.f) || !(wt[a] > 0.f) || !(c.p.k_resp > 0.f)) continue;
+        const float at = 1.f / (c.p.k_resp * wt[a] * dt2);
+        const float corr = wv * C / (wv + at);
+        y = add(y, mul(n, corr));
+        depth[a] = corr;
+    }
+    if (c.p.mu_s > 0.f || c.p.mu_k > 0.f) {
+        const f3 xn = xyz(c.x_n[v]);
+        for (int a = 0; a < na; ++a) {
+            if (!(depth[a] > 0.f)) continue;
+            const f3 n = xyz(pl[aj[a]]);
+            const f3 d = sub(y, xn);
+            const f3 t = sub(d, mul(n, dot(d, n)));
+            const float tl = len(t);
+            if (!(tl > 0.f)) continue;
+            const float f = (tl < c.p.mu_s * depth[a]) ? 1.f : fminf(c.p.mu_k * depth[a] / tl, 1.f);
+            y = sub(y, mul(t, f));
+        }
+    }
+    return y;
+}
+
+__global__ void __launch_bounds__(RESP_WARPS * 32) k_response(DevCtx c, const float4* __restrict__ x_b) {
+    if (c.flags[1]) return;
+    __shared__ float s_g[RESP_WARPS][RESP_POOL];
+    __shared__ int s_j[RESP_WARPS][RESP_POOL];
+    __shared__ float s_w[RESP_WARPS][RESP_CAP];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    const float delta = c.p.delta;
+    bool warp_job = false;
+    if (v < c.n_verts) {
+        const float4 X = x_b[v];
+        const unsigned cnt = c.count[v];
+        if (X.w > 0.f && cnt > 0u && cnt <= (unsigned)c.p.K) {
+            const int np = (int)cnt;
+            if (np > SHORT_LIST) {
+                warp_job = true;
+            } else {
+                // short list: this thread, the active contacts kept in order by insertion
+                const float4* pl = c.planes + (size_t)v * c.p.K;
+                const float* ph = c.phi + (size_t)v * c.p.K;
+                const float4 Y0 = c.x_s[v];
+                const f3 x = xyz(X), y = xyz(Y0), dy = sub(y, x);
+                float ag[RESP_CAP];
+                int aj[RESP_CAP];
+                int na = 0;
+                for (int j = 0; j < np; ++j) {
+                    const float4 P = pl[j];
+                    const float g = ph[j] + dot(xyz(P), dy);
+                    if (!(g < delta)) continue;
+                    int q = na++;
+                    const Tup t = make_tup(g, P, j);
+                    while (q > 0 && tless(t, make_tup(ag[q - 1], pl[aj[q - 1]], aj[q - 1]))) {
+                        ag[q] = ag[q - 1];
+                        aj[q] = aj[q - 1];
+                        --q;
+                    }
+                    ag[q] = g;
+                    aj[q] = j;
+                }
+                if (na > 0) {
+                    float wt[RESP_CAP];
+                    for (int a = 0; a < na; ++a) wt[a] = occlusion_weight(c, ag, na, a);
+                    const f3 yn = respond(c, v, x, y, X.w, pl, ph, aj, wt, na);
+                    c.x_s[v] = make_float4(yn.x, yn.y, yn.z, Y0.w);
+                }
+            }
+        }
+    }
+    // long lists: the warp scans the planes, collects the active contacts and
+    // picks the innermost, one per lane, in order
+    unsigned pend = __ballot_sync(FULL, warp_job);
+    float* pg = s_g[wib];
+    int* pj = s_j[wib];
+    while (pend) {
+        const int l = __ffs(pend) - 1;
+        pend &= pend - 1;
+        const int u = v - lane + l;
+        const float4 X = x_b[u];
+        const float4 Y0 = c.x_s[u];
+        const int np = (int)c.count[u];
+        const float4* pl = c.planes + (size_t)u * c.p.K;
+        const float* ph = c.phi + (size_t)u * c.p.K;
+        const f3 x = xyz(X), y = xyz(Y0), dy = sub(y, x);
+        int total = 0;
+        for (int j0 = 0; j0 < np; j0 += 32) {
+            const int j = j0 + lane;
+            float g = 0.f;
+            bool act = false;
+            if (j < np) {
+                g = ph[j] + dot(xyz(pl[j]), dy);
+                act = g < delta;
+            }
+            const unsigned bal = __ballot_sync(FULL, act);
+            const int pos = total + __popc(bal & ((1u << lane) - 1u));
+            if (act && pos < RESP_POOL) {
+                pg[pos] = g;
+                pj[pos] = j;
+            }
+            total += __popc(bal);
+        }
+        __syncwarp();
+        if (total == 0) continue;
+        const int na = min(total, RESP_CAP);
+        float mg = 0.f;
+        int mj = -1;
+        if (total <= 32) {
+            // one contact per lane: rank by the full order
+            Tup me = tup_none();
+            if (lane < total) me = make_tup(pg[lane], pl[pj[lane]], pj[lane]);
+            int rank = 0;
+            for (int t = 0; t < total; ++t) {
+                Tup o;
+                o.a = __shfl_sync(FULL, me.a, t);
+                o.b = __shfl_sync(FULL, me.b, t);
+                o.c = __shfl_sync(FULL, me.c, t);
+                o.d = __shfl_sync(FULL, me.d, t);
+                rank += tless(o, me) ? 1 : 0;
+            }
+            const float gl = (lane < total) ? pg[lane] : 0.f;
+            const int jl = (lane < total) ? pj[lane] : -1;
+            __syncwarp();
+            if (lane < total) {
+                pg[rank] = gl;
+                pj[rank] = jl;
+            }
+            __syncwarp();
+            if (lane < na) {
+                mg = pg[lane];
+                mj = pj[lane];
+            }
+        } else {
+            // repeated warp minimum, over the pool, or over the whole list when
+            // more contacts are active than the pool holds
+            Tup last = tup_none();
+            bool first = true;
+            for (int r = 0; r < na; ++r) {
+                Tup best = tup_none();
+                if (total <= RESP_POOL) {
+                    for (int i = lane; i < total; i += 32) {
+                        const Tup t = make_tup(pg[i], pl[pj[i]], pj[i]);
+                        if ((first || tless(last, t)) && tless(t, best)) best = t;
+                    }
+                } else {
+                    for (int j = lane; j < np; j += 32) {
+                        const float4 P = pl[j];
+                        const float g = ph[j] + dot(xyz(P), dy);
+                        if (!(g < delta)) continue;
+                        const Tup t = make_tup(g, P, j);
+                        if ((first || tless(last, t)) && tless(t, best)) best = t;
+                    }
+                }
+                best = warp_min_tup(best);
+                if (lane == r) {
+                    mj = (int)best.d;
+                    mg = ord2f((unsigned)(best.a >> 32));
+                }
+                last = best;
+                first = false;
+            }
+        }
+        __syncwarp();
+        // the chosen contacts in order at the pool's head; each lane weighs its
+        // own contact, then lane 0 runs the sequential repulsion and friction
+        if (lane < na) {
+            pg[lane] = mg;
+            pj[lane] = mj;
+        }
+        __syncwarp();
+        if (lane < na) s_w[wib][lane] = occlusion_weight(c, pg, na, lane);
+        __syncwarp();
+        if (lane == 0) {
+            const f3 yn = respond(c, u, x, y, X.w, pl, ph, pj, s_w[wib], na);
+            c.x_s[u] = make_float4(yn.x, yn.y, yn.z, Y0.w);
+        }
+        __syncwarp();
+    }
+}
+
 // ------------------------------------------------------------------ XPBD
 
 // Alg. 4 prediction: x~ = x + dt v + dt^2 g for movable vertices; keeps x^n.
@@ -2001,6 +2230,9 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
         if (e1 > e0) k_xpbd_color<<<nblk(e1 - e0, 256), 256, 0, st>>>(c, e0, e1);
     }
     if (tm) tm->mark(ST_XPBD, st);
+    if (c.p.delta > 0.f && c.phi && c.n_verts > 0)
+        k_response<<<nblk(c.n_verts, RESP_WARPS * 32), RESP_WARPS * 32, 0, st>>>(c, x);
+    if (tm) tm->mark(ST_RESPONSE, st);
     long threads = (long)c.n_verts * 32;
     cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) k_project<true><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);

@@ -84,12 +84,12 @@ namespace {
 // Device bytes of a context for n verts, e edges, t triangles and capacity k
 // (the allocations of ccfr_create, isolated points bounded by the vertices),
 // plus the resident state x, v.
-size_t ctx_bytes(long n, long e, long t, long k, bool keys) {
+size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false) {
     auto pow2 = [](long v) { long p = 64; while (p < v) p <<= 1; return p; };
-    long buckets = pow2(t) + pow2(e) + pow2(n) + pow2(n) + pow2(e / 4) + 1;
-    long items = t + 2 * e + 2 * n;
+    long buckets = pow2(t) + pow2(e) + pow2(n) + pow2(n) + 2 * pow2(e / 4) + pow2(e / 16) + 1;
+    long items = t + e + 2 * n;
     size_t b = 0;
-    b += (size_t)n * k * 16 + (keys ? (size_t)n * k * 8 : 0);
+    b += (size_t)n * k * 16 + (keys ? (size_t)n * k * 8 : 0) + (phi ? (size_t)n * k * 4 : 0);
     b += (size_t)n * (16 * 5 + 4 * 2 + 16 + 16 * 2 + 4);
     b += (size_t)e * (8 + 8 + 4 + 4);
     b += (size_t)t * 12;
@@ -276,7 +276,7 @@ ccfr_status ccfr_server_add_scene(ccfr_server* sv, int n_verts, int n_edges, int
     sc.rest = sc.x;
     sc.params = *params;
     sc.params.flags &= ~(unsigned)CCFR_FLAG_STORE_KEYS;
-    sc.bytes = ctx_bytes(n_verts, n_edges, n_tris, params->plane_capacity, false);
+    sc.bytes = ctx_bytes(n_verts, n_edges, n_tris, params->plane_capacity, false, params->delta > 0.f);
     if (sc.bytes > sv->budget) return CCFR_ERR_OOM;
     sv->scenes.push_back(std::move(sc));
     *scene_id = (int)sv->scenes.size() - 1;

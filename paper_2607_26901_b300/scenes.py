@@ -71,6 +71,20 @@ def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 /
                 delta_v=float(0.5 * delta if delta_v is None else delta_v), mu_s=float(mu_s), mu_k=float(mu_k))
 
 
+def with_response(sc: "Scene", delta: float, k_resp: float, mu_s: float = 0.0, mu_k: float = 0.0,
+                  delta_v: float | None = None) -> "Scene":
+    """Copy of a scene with the contact response of Sec. 3.3 switched on
+    (the AABB pad is re-derived with the repulsion range included)."""
+    p = sc.params
+    q = default_params(p["r"], p["xi"], delta=delta, dt=p["dt"], iters=p["iters"], steps=p["steps"],
+                       plane_capacity=p["plane_capacity"], k_resp=k_resp, delta_v=delta_v, mu_s=mu_s, mu_k=mu_k)
+    q["gravity"] = p["gravity"]
+    q["compliance"] = p["compliance"]
+    out = sc.copy()
+    out.params = q
+    return out
+
+
 def canonical_edges(e: np.ndarray) -> np.ndarray:
     """Unique undirected edges (min, max), sorted lexicographically."""
     if len(e) == 0:
