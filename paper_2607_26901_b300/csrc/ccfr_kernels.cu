@@ -1877,6 +1877,7 @@ __global__ void __launch_bounds__(RESP_WARPS * 32) k_response(DevCtx c, const fl
     __shared__ float s_g[RESP_WARPS][RESP_POOL];
     __shared__ int s_j[RESP_WARPS][RESP_POOL];
     __shared__ float s_w[RESP_WARPS][RESP_CAP];
+    __shared__ unsigned s_h[RESP_WARPS][256];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     const float delta = c.p.delta;
@@ -1954,10 +1955,88 @@ __global__ void __launch_bounds__(RESP_WARPS * 32) k_response(DevCtx c, const fl
         }
         __syncwarp();
         if (total == 0) continue;
+        int sel = total;   // contacts in the pool's head to order (after the select below)
+        if (total > 32 && total <= RESP_POOL) {
+            // radix select on the ordered gap: the 32nd smallest key K, then the
+            // contacts below K and, of those at K, the first in the full order
+            unsigned* hist = s_h[wib];
+            unsigned prefix = 0u, pmask = 0u;
+            int need = RESP_CAP;
+            for (int shift = 24; shift >= 0; shift -= 8) {
+                for (int b = lane; b < 256; b += 32) hist[b] = 0u;
+                __syncwarp();
+                for (int i = lane; i < total; i += 32) {
+                    const unsigned k = f2ord(pg[i]);
+                    if ((k & pmask) == prefix) atomicAdd(&hist[(k >> shift) & 255u], 1u);
+                }
+                __syncwarp();
+                unsigned loc[8], tot = 0;
+                #pragma unroll
+                for (int q = 0; q < 8; ++q) { loc[q] = hist[lane * 8 + q]; tot += loc[q]; }
+                unsigned inc = tot;
+                #pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned t = __shfl_up_sync(FULL, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                const unsigned before = inc - tot;
+                // the lane whose bins reach the need-th key holds the digit
+                int digit = -1;
+                unsigned below = 0u;
+                if (before < (unsigned)need && inc >= (unsigned)need) {
+                    unsigned acc = before;
+                    for (int q = 0; q < 8; ++q) {
+                        if (acc + loc[q] >= (unsigned)need) { digit = lane * 8 + q; below = acc; break; }
+                        acc += loc[q];
+                    }
+                }
+                const unsigned bd = __ballot_sync(FULL, digit >= 0);
+                const int owner = __ffs(bd) - 1;
+                digit = __shfl_sync(FULL, digit, owner);
+                below = __shfl_sync(FULL, below, owner);
+                prefix |= (unsigned)digit << shift;
+                pmask |= 255u << shift;
+                need -= (int)below;
+                __syncwarp();
+            }
+            // compact: keys below K first (fewer than 32), then the ties at K
+            int n_lt = 0;
+            for (int i0 = 0; i0 < total; i0 += 32) {
+                const int i = i0 + lane;
+                const bool lt = i < total && f2ord(pg[i]) < prefix;
+                const unsigned bal = __ballot_sync(FULL, lt);
+                if (lt) hist[n_lt + __popc(bal & ((1u << lane) - 1u))] = (unsigned)i;
+                n_lt += __popc(bal);
+            }
+            __syncwarp();
+            int n_eq = 0;
+            for (int i0 = 0; i0 < total; i0 += 32) {
+                const int i = i0 + lane;
+                const bool eq = i < total && f2ord(pg[i]) == prefix;
+                const unsigned bal = __ballot_sync(FULL, eq);
+                const int pos = n_lt + n_eq + __popc(bal & ((1u << lane) - 1u));
+                if (eq && pos < 256) hist[pos] = (unsigned)i;
+                n_eq += __popc(bal);
+            }
+            __syncwarp();
+            if (n_lt + n_eq <= 32) {
+                // gather the chosen (all of the ties fit) to the pool's head
+                float gl = 0.f;
+                int jl = -1;
+                const bool mine = lane < n_lt + n_eq;
+                if (mine) { gl = pg[hist[lane]]; jl = pj[hist[lane]]; }
+                __syncwarp();
+                if (mine) { pg[lane] = gl; pj[lane] = jl; }
+                __syncwarp();
+                sel = n_lt + n_eq;
+            }
+            // else: too many exact ties at K, the repeated minimum below decides
+        }
         const int na = min(total, RESP_CAP);
         float mg = 0.f;
         int mj = -1;
-        if (total <= 32) {
+        if (sel <= 32) {
+            total = sel;
             // one contact per lane: rank by the full order
             Tup me = tup_none();
             if (lane < total) me = make_tup(pg[lane], pl[pj[lane]], pj[lane]);
