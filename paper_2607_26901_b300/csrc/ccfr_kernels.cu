@@ -255,8 +255,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(DevCtx c, unsigned*
 
 // ------------------------------------------------------- plane emission
 
-__device__ __forceinline__ void emit_plane(const DevCtx& c, int v, f3 n, float d, float phi, u64 key) {
-    unsigned slot = atomicAdd(&c.count[v], 1u);
+// A pair's planes are emitted in two steps: every plane first reserves its
+// slot in its vertex's list (one count atomic each, all issued before any
+// store, so that their round trips to L2 overlap), then the planes are stored.
+// A plane beyond the list capacity only lowers the vertex's smallest dropped d.
+__device__ __forceinline__ unsigned reserve_slot(const DevCtx& c, int v, bool on) {
+    return on ? atomicAdd(&c.count[v], 1u) : 0u;
+}
+__device__ __forceinline__ void store_plane(const DevCtx& c, int v, bool on, unsigned slot, f3 n, float d, float phi,
+                                            u64 key) {
+    if (!on) return;
     if (slot < (unsigned)c.p.K) {
         size_t o = (size_t)v * c.p.K + slot;
         c.planes[o] = make_float4(n.x, n.y, n.z, d);
@@ -345,13 +353,15 @@ __device__ int narrow_vf(const DevCtx& c, int p, float4 P, int t, int3 T, float4
     f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
     f3 mn = mk(-n.x, -n.y, -n.z);
     u64 key = pair_key(0, p, t);
-    int k = 0;
-    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, phi, key); ++k; }
-    float df = (wf / W) * phi;
-    if (A.w > 0.f) { emit_plane(c, T.x, mn, df, phi, key); ++k; }
-    if (B.w > 0.f) { emit_plane(c, T.y, mn, df, phi, key); ++k; }
-    if (C.w > 0.f) { emit_plane(c, T.z, mn, df, phi, key); ++k; }
-    return k;
+    const bool op = P.w > 0.f, oa = A.w > 0.f, ob = B.w > 0.f, oc = C.w > 0.f;
+    const unsigned sp_ = reserve_slot(c, p, op), sa = reserve_slot(c, T.x, oa), sb = reserve_slot(c, T.y, ob),
+                   sc = reserve_slot(c, T.z, oc);
+    const float df = (wf / W) * phi;
+    store_plane(c, p, op, sp_, n, (P.w / W) * phi, phi, key);
+    store_plane(c, T.x, oa, sa, mn, df, phi, key);
+    store_plane(c, T.y, ob, sb, mn, df, phi, key);
+    store_plane(c, T.z, oc, sc, mn, df, phi, key);
+    return (int)op + (int)oa + (int)ob + (int)oc;
 }
 
 // Closest points of segments p1 + s d1 and p2 + t d2 in FP64 with the
@@ -442,12 +452,14 @@ __device__ int narrow_ee(const DevCtx& c, const float4* __restrict__ x, int e, i
     f3 mn = mk(-n.x, -n.y, -n.z);
     u64 key = pair_key(1, e, f);
     float da = (wa / W) * phi, db = (wb / W) * phi;
-    int k = 0;
-    if (A0.w > 0.f) { emit_plane(c, E.x, n, da, phi, key); ++k; }
-    if (A1.w > 0.f) { emit_plane(c, E.y, n, da, phi, key); ++k; }
-    if (B0.w > 0.f) { emit_plane(c, F.x, mn, db, phi, key); ++k; }
-    if (B1.w > 0.f) { emit_plane(c, F.y, mn, db, phi, key); ++k; }
-    return k;
+    const bool o0 = A0.w > 0.f, o1 = A1.w > 0.f, o2 = B0.w > 0.f, o3 = B1.w > 0.f;
+    const unsigned s0 = reserve_slot(c, E.x, o0), s1 = reserve_slot(c, E.y, o1), s2 = reserve_slot(c, F.x, o2),
+                   s3 = reserve_slot(c, F.y, o3);
+    store_plane(c, E.x, o0, s0, n, da, phi, key);
+    store_plane(c, E.y, o1, s1, n, da, phi, key);
+    store_plane(c, F.x, o2, s2, mn, db, phi, key);
+    store_plane(c, F.y, o3, s3, mn, db, phi, key);
+    return (int)o0 + (int)o1 + (int)o2 + (int)o3;
 }
 
 // Point-point pair (isolated particles).
@@ -462,10 +474,11 @@ __device__ int narrow_pp(const DevCtx& c, int p, int q, float4 P, float4 Q) {
     if (W == 0.f) return 0;
     f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
     u64 key = pair_key(2, p, q);
-    int k = 0;
-    if (P.w > 0.f) { emit_plane(c, p, n, (P.w / W) * phi, phi, key); ++k; }
-    if (Q.w > 0.f) { emit_plane(c, q, mk(-n.x, -n.y, -n.z), (Q.w / W) * phi, phi, key); ++k; }
-    return k;
+    const bool op = P.w > 0.f, oq = Q.w > 0.f;
+    const unsigned sp_ = reserve_slot(c, p, op), sq = reserve_slot(c, q, oq);
+    store_plane(c, p, op, sp_, n, (P.w / W) * phi, phi, key);
+    store_plane(c, q, oq, sq, mk(-n.x, -n.y, -n.z), (Q.w / W) * phi, phi, key);
+    return (int)op + (int)oq;
 }
 
 // ------------------------------------------------------ neighbourhood scan
