@@ -1184,14 +1184,18 @@ struct BlockCounters {
     unsigned short_verts;
 };
 
-// Per-warp shared memory of the projection: the candidate planes of a pass
-// as (sort key, slot) pairs, double-buffered for a stable radix sort, plus
-// the digit histogram.  Dynamic shared memory (PROJ_WARPS x 13 KB).
+// Per-warp shared memory of the projection: the slots of a pass's candidate
+// planes, double-buffered for a stable radix sort, the current pass's digit
+// of each entry and the digit histogram (6 KB).  The sort keys themselves are
+// not stored: each pass recomputes its digit from the plane (rho at the first
+// input, or the plane hash), a read that stays in L1 because the small
+// buffers leave it room for the warps' plane lists.  Dynamic shared memory
+// (PROJ_WARPS x 6 KB).
 constexpr int SCAP = 1024;
 constexpr int PROJ_WARPS = 4;
 struct SortBuf {
-    unsigned key[2][SCAP];
     unsigned short idx[2][SCAP];
+    unsigned char dig[SCAP];
     unsigned hist[256];
 };
 constexpr size_t PROJ_SMEM = PROJ_WARPS * sizeof(SortBuf);
@@ -1259,8 +1263,9 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
     return W.nv;
 }
 
-// One stable counting pass of a warp LSD radix sort over n (key, slot) pairs
-// from buffer src into buffer src ^ 1, on the 8-bit digit dig(key, slot).
+// One stable counting pass of a warp LSD radix sort over n slots from buffer
+// src into buffer src ^ 1, on the 8-bit digit dig(slot), computed once per
+// entry (four planes in flight per lane) and kept in sb.dig for the scatter.
 // Equal digits keep their relative order: ranks within each 32-entry chunk
 // come from the intersection of the eight bit-slice ballots.
 template <typename Dig>
@@ -1268,7 +1273,22 @@ __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src
     const unsigned lt = (1u << lane) - 1u;
     for (int b = lane; b < 256; b += 32) sb.hist[b] = 0u;
     __syncwarp();
-    for (int i = lane; i < n; i += 32) atomicAdd(&sb.hist[dig(sb.key[src][i], sb.idx[src][i])], 1u);
+    for (int i0 = lane; i0 < n; i0 += 128) {
+        unsigned d[4];
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + 32 * k;
+            d[k] = (i < n) ? dig(sb.idx[src][i]) : 0u;
+        }
+        #pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int i = i0 + 32 * k;
+            if (i < n) {
+                sb.dig[i] = (unsigned char)d[k];
+                atomicAdd(&sb.hist[d[k]], 1u);
+            }
+        }
+    }
     __syncwarp();
     // exclusive scan of the 256 bins, 8 per lane
     unsigned loc[8], tot = 0;
@@ -1288,9 +1308,8 @@ __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src
     for (int base = 0; base < n; base += 32) {
         const int i = base + lane;
         const bool valid = i < n;
-        const unsigned k = valid ? sb.key[src][i] : 0u;
         const unsigned short j = valid ? sb.idx[src][i] : 0;
-        const unsigned dg = valid ? dig(k, j) : 256u;
+        const unsigned dg = valid ? (unsigned)sb.dig[i] : 256u;
         // lanes holding the same digit: intersect the eight bit-slice ballots
         unsigned peers = __ballot_sync(FULL, valid);
         if (!valid) peers = ~peers;
@@ -1303,7 +1322,6 @@ __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src
         __syncwarp();
         if (valid) {
             const unsigned dst = start + __popc(peers & lt);
-            sb.key[src ^ 1][dst] = k;
             sb.idx[src ^ 1][dst] = j;
             if ((peers & lt) == 0u) sb.hist[dg] = start + __popc(peers);
         }
@@ -1311,15 +1329,19 @@ __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src
     }
 }
 
-// Stable LSD radix sort by (rho key, plane hash) of the n pairs in buffer 0,
+// Sort key of a candidate plane: rho at the first input y0, as an ordered
+// integer (Alg. 2 sorts once, by the violation at the pass start).
+__device__ __forceinline__ unsigned plane_key(const float4* pl, int j, f3 y0) { return f2ord(rho_at(y0, pl[j])); }
+
+// Stable LSD radix sort by (rho key, plane hash) of the n slots in buffer 0,
 // which arrive in slot order: two passes on the hash, then four on the key.
-// Six passes: the sorted data is back in buffer 0, ordered by (key, hash, slot).
-__device__ void warp_radix_sort(SortBuf& sb, int n, int lane, const float4* pl) {
+// Six passes: the sorted slots are back in buffer 0, ordered by (key, hash, slot).
+__device__ void warp_radix_sort(SortBuf& sb, int n, int lane, const float4* pl, f3 y0) {
     int src = 0;
     for (int shift = 0; shift < 16; shift += 8, src ^= 1)
-        radix_pass(sb, n, lane, src, [&](unsigned, unsigned short j) { return (plane_hash16(pl[j]) >> shift) & 255u; });
+        radix_pass(sb, n, lane, src, [&](unsigned short j) { return (plane_hash16(pl[j]) >> shift) & 255u; });
     for (int shift = 0; shift < 32; shift += 8, src ^= 1)
-        radix_pass(sb, n, lane, src, [&](unsigned k, unsigned short) { return (k >> shift) & 255u; });
+        radix_pass(sb, n, lane, src, [&](unsigned short j) { return (plane_key(pl, j, y0) >> shift) & 255u; });
 }
 
 // Plane order of Alg. 2 among equal (key, hash): the plane's own bits (d, n)
@@ -1338,7 +1360,7 @@ __device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
     return a < b;
 }
 
-// One pass of Alg. 2 over the sorted candidates sb.key/idx[0][0..m): walk
+// One pass of Alg. 2 over the sorted candidates sb.idx[0][0..m): walk
 // the list in order, 32 planes per chunk held one per lane; the first plane of
 // the chunk violated at the current iterate is handled (Alg. 1 + retraction)
 // and the walk resumes with the chunk's later planes, tested at the new iterate.
@@ -1656,10 +1678,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                         const bool take = (j < np) && rho_at(ypass, P[k]) <= T;
                         const unsigned bal = __ballot_sync(FULL, take);
                         const int pos = m + __popc(bal & ((1u << lane) - 1u));
-                        if (take && pos < SCAP) {
-                            sb.key[0][pos] = f2ord(rho_at(y0, P[k]));
-                            sb.idx[0][pos] = (unsigned short)j;
-                        }
+                        if (take && pos < SCAP) sb.idx[0][pos] = (unsigned short)j;
                         m += __popc(bal);
                     }
                 }
@@ -1672,7 +1691,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                     unsigned short jj = 0;
                     if (lane < m) {
                         jj = sb.idx[0][lane];
-                        me = make_tup_ord(sb.key[0][lane], pl[jj], jj);
+                        me = make_tup_ord(plane_key(pl, jj, y0), pl[jj], jj);
                     }
                     int rank = 0;
                     for (int t = 0; t < m; ++t) {
@@ -1684,28 +1703,24 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32) k_project_heavy(DevCtx c, con
                         rank += tless(o, me) ? 1 : 0;
                     }
                     __syncwarp();
-                    if (lane < m) {
-                        sb.key[0][rank] = (unsigned)(me.a >> 32);
-                        sb.idx[0][rank] = jj;
-                    }
+                    if (lane < m) sb.idx[0][rank] = jj;
                     __syncwarp();
                 } else {
-                warp_radix_sort(sb, m, lane, pl);
+                warp_radix_sort(sb, m, lane, pl, y0);
                 // equal (key, hash) on distinct planes (a hash collision; rare): order
                 // each such run by the plane itself (its bits, then its slot).
                 // Bitwise-identical planes act identically in any order.  Runs are
                 // disjoint: each lane sorts the runs that start at its indices.
                 bool tie = false;
                 for (int i = lane; i + 1 < m; i += 32) {
-                    if (sb.key[0][i] == sb.key[0][i + 1]) {
-                        const float4 A = pl[sb.idx[0][i]], B = pl[sb.idx[0][i + 1]];
+                    const float4 A = pl[sb.idx[0][i]], B = pl[sb.idx[0][i + 1]];
+                    if (f2ord(rho_at(y0, A)) == f2ord(rho_at(y0, B)))
                         tie |= !(A.x == B.x && A.y == B.y && A.z == B.z && A.w == B.w) &&
                                plane_hash16(A) == plane_hash16(B);
-                    }
                 }
                 if (__any_sync(FULL, tie)) {
                     auto same = [&](int i, int k) {
-                        return sb.key[0][i] == sb.key[0][k] &&
+                        return plane_key(pl, sb.idx[0][i], y0) == plane_key(pl, sb.idx[0][k], y0) &&
                                plane_hash16(pl[sb.idx[0][i]]) == plane_hash16(pl[sb.idx[0][k]]);
                     };
                     for (int i = lane; i < m; i += 32) {
@@ -2280,6 +2295,8 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
 // are resident at once, found by configure_kernels
 static int g_short_blocks_per_sm = 4;
 #define SHORT_BLOCKS_PER_SM g_short_blocks_per_sm
+static int g_heavy_blocks_per_sm = 4;
+#define HEAVY_BLOCKS_PER_SM g_heavy_blocks_per_sm
 
 cudaError_t configure_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_project_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2289,6 +2306,10 @@ cudaError_t configure_kernels() {
     int nb = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_short<true>, 128, 0);
     if (e == cudaSuccess && nb > 0) g_short_blocks_per_sm = nb;
+    nb = 0;
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_heavy<true>, PROJ_WARPS * 32, PROJ_SMEM);
+    if (e == cudaSuccess && nb > 0) g_heavy_blocks_per_sm = nb;
     return e;
 }
 
@@ -2302,7 +2323,7 @@ void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned cha
     cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) {
         k_project<false><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
-        k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
+        k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
         k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, xb, xio, xio, halt);
     }
 }
@@ -2329,7 +2350,7 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
     cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
     if (threads > 0) k_project<true><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
-    if (threads > 0) k_project_heavy<true><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
+    if (threads > 0) k_project_heavy<true><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_HEAVY, st);
     if (threads > 0) k_project_short<true><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_SHORT, st);
@@ -2471,7 +2492,7 @@ extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const fl
     c.n_sm = su->n_sm;
     k_static_dmin<<<nblk(n_verts, 256), 256, 0, s>>>(dmin_drop, sc->dmin, n_verts);
     k_project<false><<<nblk(n_verts, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
-    k_project_heavy<false><<<c.n_sm * 4, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
+    k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                          (float4*)x_io, halt_out);
     k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                        (float4*)x_io, halt_out);
