@@ -1336,12 +1336,19 @@ __device__ __forceinline__ unsigned plane_key(const float4* pl, int j, f3 y0) { 
 // Stable LSD radix sort by (rho key, plane hash) of the n slots in buffer 0,
 // which arrive in slot order: two passes on the hash, then four on the key.
 // Six passes: the sorted slots are back in buffer 0, ordered by (key, hash, slot).
+// One loop over a single pass body (the digit source chosen per pass), so that
+// the kernel holds one copy of the pass code.
 __device__ void warp_radix_sort(SortBuf& sb, int n, int lane, const float4* pl, f3 y0) {
-    int src = 0;
-    for (int shift = 0; shift < 16; shift += 8, src ^= 1)
-        radix_pass(sb, n, lane, src, [&](unsigned short j) { return (plane_hash16(pl[j]) >> shift) & 255u; });
-    for (int shift = 0; shift < 32; shift += 8, src ^= 1)
-        radix_pass(sb, n, lane, src, [&](unsigned short j) { return (plane_key(pl, j, y0) >> shift) & 255u; });
+    #pragma unroll 1
+    for (int p = 0; p < 6; ++p) {
+        const bool hashp = p < 2;
+        const int shift = 8 * (hashp ? p : p - 2);
+        radix_pass(sb, n, lane, p & 1, [&](unsigned short j) {
+            const float4 P = pl[j];
+            const unsigned w = hashp ? plane_hash16(P) : f2ord(rho_at(y0, P));
+            return (w >> shift) & 255u;
+        });
+    }
 }
 
 // Plane order of Alg. 2 among equal (key, hash): the plane's own bits (d, n)
