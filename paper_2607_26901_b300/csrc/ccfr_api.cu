@@ -30,6 +30,7 @@ struct ccfr_ctx {
     std::vector<int> color_off;
     int n_colors = 0;
     cudaStream_t cap_stream = nullptr;
+    SideStream side;
     std::vector<GraphEntry> graphs;
     bool regions_valid = false;
     bool rest_pending = false;
@@ -66,6 +67,9 @@ void free_ctx(ccfr_ctx* c) {
     c->graphs.clear();
     for (void* p : c->allocs) cudaFree(p);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->side.s) cudaStreamDestroy(c->side.s);
+    if (c->side.fork) cudaEventDestroy(c->side.fork);
+    if (c->side.join) cudaEventDestroy(c->side.join);
     delete c;
 }
 
@@ -101,7 +105,8 @@ void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer
     if (tm) tm->mark(ST_PREDICT, st);
     int early = (c->prm.flags & CCFR_FLAG_EARLY_EXIT) ? 1 : 0;
     for (int it = 0; it < c->prm.solver_iters; ++it)
-        launch_iteration(c->dc, x, st, c->color_off.data(), c->n_colors, c->tile_sums, c->n_buckets_total, early, tm);
+        launch_iteration(c->dc, x, st, c->color_off.data(), c->n_colors, c->tile_sums, c->n_buckets_total, early, tm,
+                         &c->side);
     launch_update(c->dc, x, v, st);
     if (tm) tm->mark(ST_MISC, st);
 }
@@ -318,6 +323,9 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     }
     if (err == cudaSuccess) err = configure_kernels();
     if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaStreamSynchronize(st);
     if (err != cudaSuccess) { free_ctx(c); return CCFR_ERR_CUDA; }
     *out = c;
@@ -456,7 +464,8 @@ ccfr_status ccfr_build_regions(ccfr_ctx* c, const float* x, void* stream) {
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     launch_clear_regions(c->dc, st);
-    launch_build(c->dc, (const float4*)x, st, MODE_PLANES, nullptr, c->tile_sums, c->n_buckets_total);
+    launch_build(c->dc, (const float4*)x, st, MODE_PLANES, nullptr, c->tile_sums, c->n_buckets_total, nullptr,
+                 &c->side);
     c->regions_valid = true;
     return from_cuda(cudaGetLastError());
 }

@@ -27,14 +27,25 @@ struct PairOutHost {
     unsigned long long* count;   // device [3]
 };
 
+// A second stream of a context with two events: the region build forks the
+// oversized-primitive and point-point emission onto it, so that they run
+// beside the vertex-face and edge-edge emission (graph branches under stream
+// capture), and joins it back before the region is used.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
 void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* po,
-                  unsigned* tile_sums, int n_buckets_total, StageTimer* tm = nullptr);
+                  unsigned* tile_sums, int n_buckets_total, StageTimer* tm = nullptr,
+                  const SideStream* side = nullptr);
 cudaError_t configure_kernels();
 void launch_clear_regions(const DevCtx& c, cudaStream_t st);
 void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st);
 void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st);
 void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* color_off, int n_colors,
-                      unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm = nullptr);
+                      unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm = nullptr,
+                      const SideStream* side = nullptr);
 void launch_update(const DevCtx& c, const float4* x, float4* v, cudaStream_t st);
 void launch_rest_lengths(const int2* edges_col, const float4* x, float* rest, int ne, cudaStream_t st);
 void launch_load_regions(const DevCtx& c, const float4* planes, const int* count, int cap, cudaStream_t st);

@@ -2245,7 +2245,7 @@ __global__ void k_dmin_export(DevCtx c, float* out) {
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* poh,
-                  unsigned* tile_sums, int n_buckets_total, StageTimer* tm) {
+                  unsigned* tile_sums, int n_buckets_total, StageTimer* tm, const SideStream* side) {
     PairOut po{};
     if (poh) {
         for (int k = 0; k < 3; ++k) { po.out[k] = poh->out[k]; po.cap[k] = poh->cap[k]; }
@@ -2275,16 +2275,30 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     if (tm) tm->mark(ST_GRID_UNITS, st);
     const int G = c.n_sm * (c.emit_bps > 0 ? c.emit_bps : 8);
     if (mode == MODE_PLANES) {
+        // The emission kernels only add planes through count atomics, so they are
+        // independent: with a side stream (and no per-stage timing) the oversized
+        // and point-point ones run beside the per-cell ones and fill their tails.
+        const bool fork = side && !tm;
+        cudaStream_t sb = st;
+        if (fork) {
+            cudaEventRecord(side->fork, st);
+            cudaStreamWaitEvent(side->s, side->fork, 0);
+            sb = side->s;
+        }
         if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF, st);
-        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF_BIG, st);
         if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE, st);
-        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE_BIG, st);
-        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_PP, st);
+        if (fork) {
+            cudaEventRecord(side->join, sb);
+            cudaStreamWaitEvent(st, side->join, 0);
+        }
     } else {
         if (c.n_tris > 0) {
             k_emit<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
@@ -2342,9 +2356,10 @@ void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStrea
 }
 
 void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* color_off, int n_colors,
-                      unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm) {
+                      unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm,
+                      const SideStream* side) {
     if (c.n_verts > 0) k_iter_begin<<<nblk(c.n_verts, 256), 256, 0, st>>>(c);
-    launch_build(c, x, st, MODE_PLANES, nullptr, tile_sums, n_buckets_total, tm);
+    launch_build(c, x, st, MODE_PLANES, nullptr, tile_sums, n_buckets_total, tm, side);
     for (int k = 0; k < n_colors; ++k) {
         int e0 = color_off[k], e1 = color_off[k + 1];
         if (e1 > e0) k_xpbd_color<<<nblk(e1 - e0, 256), 256, 0, st>>>(c, e0, e1);
