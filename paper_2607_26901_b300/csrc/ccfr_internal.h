@@ -28,8 +28,8 @@ struct PairOutHost {
 };
 
 // A second stream of a context with two events: the region build forks the
-// oversized-primitive and point-point emission onto it, so that they run
-// beside the vertex-face and edge-edge emission (graph branches under stream
+// edge-edge and point-point emission onto it, so that they run beside the
+// vertex-face and oversized-primitive emission (graph branches under stream
 // capture), and joins it back before the region is used.
 struct SideStream {
     cudaStream_t s = nullptr;

@@ -2276,8 +2276,9 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     const int G = c.n_sm * (c.emit_bps > 0 ? c.emit_bps : 8);
     if (mode == MODE_PLANES) {
         // The emission kernels only add planes through count atomics, so they are
-        // independent: with a side stream (and no per-stage timing) the oversized
-        // and point-point ones run beside the per-cell ones and fill their tails.
+        // independent: with a side stream (and no per-stage timing) the edge-edge
+        // and point-point ones run beside the vertex-face and oversized ones (two
+        // branches of similar length that fill each other's tails).
         const bool fork = side && !tm;
         cudaStream_t sb = st;
         if (fork) {
@@ -2287,11 +2288,11 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
         }
         if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF, st);
-        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
+        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF_BIG, st);
-        if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE, st);
-        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
+        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE_BIG, st);
         if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_PP, st);
