@@ -47,6 +47,26 @@
  *       its step is clamped to max(0, min_k d_k) over all its planes, which
  *       satisfies every plane because |n . y| <= |y|.
  *
+ * Scenes that mix rods, cloth, volumes and particles (the paper's coupled
+ * codimensional scene, Sec. 5) use these further readings:
+ *   X1  bending: extra distance constraints ("links") given by the scene (for
+ *       cloth the two vertices opposite each interior edge, for rods every
+ *       second neighbour), each with its own compliance; rest lengths from the
+ *       rest shape.
+ *   X2  volume: per tetrahedron (x0, x1, x2, x3) the constraint
+ *       C = 6 V - 6 V0 with 6 V = (x1 - x0) . ((x2 - x0) x (x3 - x0)), signed,
+ *       V0 from the rest shape, one compliance for all tetrahedra.
+ *   X3  constraint order: the edges (canonical order) and then the links form
+ *       one list coloured greedily first-fit; its colours are swept in
+ *       ascending order, then the tetrahedra, coloured the same way.
+ *   X4  vertex-edge pairs between isolated points and free edges (edges of no
+ *       triangle, i.e. rods): a particle meets a wire through no pair of
+ *       Alg. 3.  The plane is built as in Alg. 3 with the point on the segment
+ *       and its barycentric inverse mass (R4); pair kind 3.
+ *   X5  a vertex that belongs to links or tetrahedra but to no edge or triangle
+ *       (the interior of a volume) takes no part in collision: it is neither an
+ *       isolated point nor a vertex-face query.
+ *
  * Parity pins: every function here is pinned by tests against closed forms,
  * brute force or invariants (see tests/test_oracle_*.py).
  */
@@ -134,34 +154,86 @@ static int cmp_pair(const void *x, const void *y) {
     return 0;
 }
 
+/* Constraints beyond the collision edges (readings X1-X3): distance links
+ * with their compliances, rest lengths and tetrahedra with their rest volumes
+ * (6 V0).  A null pointer means none. */
+typedef struct {
+    int nl;
+    const int *links;              /* nl x 2 */
+    const double *link_compliance; /* nl */
+    const double *link_rest;       /* nl */
+    int ntet;
+    const int *tets;               /* ntet x 4 */
+    const double *vol6_rest;       /* ntet */
+    double volume_compliance;
+} orc_extra;
+
 typedef struct {
     int n, ne, nt;
     const int *edges, *tris;
     const float *w;      /* inverse masses (as stored in binary32) */
     int *iso;            /* isolated vertices */
     int niso;
+    unsigned char *collides;   /* per vertex: takes part in collision (X5) */
+    unsigned char *free_edge;  /* per edge: belongs to no triangle (X4) */
 } topo;
 
-static void topo_init(topo *t, int n, const int *edges, int ne, const int *tris, int nt, const float *x4) {
+static long find_edge(const int *edges, int ne, int a, int b) {
+    long lo = 0, hi = ne;
+    while (lo < hi) {
+        long mid = (lo + hi) / 2;
+        const int *e = edges + 2 * mid;
+        if (e[0] < a || (e[0] == a && e[1] < b)) lo = mid + 1; else hi = mid;
+    }
+    return (lo < ne && edges[2 * lo] == a && edges[2 * lo + 1] == b) ? lo : -1;
+}
+
+static void topo_init_ext(topo *t, int n, const int *edges, int ne, const int *tris, int nt, const float *x4,
+                          const orc_extra *ex) {
     t->n = n; t->ne = ne; t->nt = nt; t->edges = edges; t->tris = tris;
     float *w = (float *)malloc(sizeof(float) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) w[i] = x4[4 * i + 3];
     t->w = w;
-    char *used = (char *)calloc(n > 0 ? n : 1, 1);
+    char *used = (char *)calloc(n > 0 ? n : 1, 1);   /* 1: collision edge, 2: link or tetrahedron only */
     for (int e = 0; e < ne; ++e) { used[edges[2 * e]] = 1; used[edges[2 * e + 1]] = 1; }
+    for (int f = 0; f < nt; ++f)
+        for (int k = 0; k < 3; ++k) used[tris[3 * f + k]] = 1;
+    if (ex) {
+        for (int l = 0; l < ex->nl; ++l)
+            for (int k = 0; k < 2; ++k) if (!used[ex->links[2 * l + k]]) used[ex->links[2 * l + k]] = 2;
+        for (int q = 0; q < ex->ntet; ++q)
+            for (int k = 0; k < 4; ++k) if (!used[ex->tets[4 * q + k]]) used[ex->tets[4 * q + k]] = 2;
+    }
     t->iso = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+    t->collides = (unsigned char *)malloc(n > 0 ? n : 1);
     t->niso = 0;
-    for (int i = 0; i < n; ++i) if (!used[i]) t->iso[t->niso++] = i;
+    for (int i = 0; i < n; ++i) {
+        if (!used[i]) t->iso[t->niso++] = i;
+        t->collides[i] = used[i] != 2;
+    }
     free(used);
+    t->free_edge = (unsigned char *)malloc(ne > 0 ? ne : 1);
+    for (int e = 0; e < ne; ++e) t->free_edge[e] = 1;
+    for (int f = 0; f < nt; ++f)
+        for (int k = 0; k < 3; ++k) {
+            int a = tris[3 * f + k], b = tris[3 * f + (k + 1) % 3];
+            long e = find_edge(edges, ne, a < b ? a : b, a < b ? b : a);
+            if (e >= 0) t->free_edge[e] = 0;
+        }
 }
 
-static void topo_free(topo *t) { free((void *)t->w); free(t->iso); }
+static void topo_init(topo *t, int n, const int *edges, int ne, const int *tris, int nt, const float *x4) {
+    topo_init_ext(t, n, edges, ne, tris, nt, x4, NULL);
+}
+
+static void topo_free(topo *t) { free((void *)t->w); free(t->iso); free(t->collides); free(t->free_edge); }
 
 /* Pair filters (Alg. 3 exclusions): a VF pair needs the vertex outside the
  * triangle, an EE pair needs e < e' and no shared vertex, a VV pair needs two
  * isolated points p < q; every pair needs one movable vertex. */
 static int vf_ok(const topo *t, int v, int f) {
     const int *T = t->tris + 3 * f;
+    if (!t->collides[v]) return 0;   /* X5 */
     if (v == T[0] || v == T[1] || v == T[2]) return 0;
     return (t->w[v] > 0 || t->w[T[0]] > 0 || t->w[T[1]] > 0 || t->w[T[2]] > 0);
 }
@@ -178,9 +250,17 @@ static int vv_ok(const topo *t, int p, int q) {
     return (t->w[p] > 0 || t->w[q] > 0);
 }
 
+/* X4: an isolated point against a free edge (a point is never an endpoint). */
+static int ve_ok(const topo *t, int p, int e) {
+    if (!t->free_edge[e]) return 0;
+    const int *E = t->edges + 2 * e;
+    return (t->w[p] > 0 || t->w[E[0]] > 0 || t->w[E[1]] > 0);
+}
+
 /* Sort-and-sweep over x of the item boxes; returns all (query, item) pairs
  * whose binary32 boxes overlap.  kind 0 = VF (queries vertices, items tris),
- * 1 = EE (edges, edges), 2 = VV (isolated points, isolated points). */
+ * 1 = EE (edges, edges), 2 = VV (isolated points, isolated points),
+ * 3 = VE (isolated points, edges; X4). */
 typedef struct { float lo; int idx; } sortkey;
 static int cmp_sk(const void *x, const void *y) {
     const sortkey *p = (const sortkey *)x, *q = (const sortkey *)y;
@@ -200,7 +280,7 @@ static fbox kind_query_box(const topo *t, const float *x4, int kind, int i, floa
 static fbox kind_item_box(const topo *t, const float *x4, int kind, int j, float pad) {
     int vid[1];
     if (kind == 0) return box_of(x4, t->tris + 3 * j, 3, pad);
-    if (kind == 1) return box_of(x4, t->edges + 2 * j, 2, pad);
+    if (kind == 1 || kind == 3) return box_of(x4, t->edges + 2 * j, 2, pad);
     vid[0] = t->iso[j];
     return box_of(x4, vid, 1, pad);
 }
@@ -208,12 +288,15 @@ static fbox kind_item_box(const topo *t, const float *x4, int kind, int j, float
 static int kind_ok(const topo *t, int kind, int i, int j) {
     if (kind == 0) return vf_ok(t, i, j);
     if (kind == 1) return ee_ok(t, i, j);
+    if (kind == 3) return ve_ok(t, t->iso[i], j);
     return vv_ok(t, t->iso[i], t->iso[j]);
 }
 
+#define N_PAIR_KINDS 4
+
 static void broad_kind(const topo *t, const float *x4, float pad, int kind, int brute, pairvec *out) {
     int nq = kind == 0 ? t->n : (kind == 1 ? t->ne : t->niso);
-    int ni = kind == 0 ? t->nt : (kind == 1 ? t->ne : t->niso);
+    int ni = kind == 0 ? t->nt : ((kind == 1 || kind == 3) ? t->ne : t->niso);
     if (nq <= 0 || ni <= 0) return;
     fbox *ib = (fbox *)malloc(sizeof(fbox) * ni);
     for (int j = 0; j < ni; ++j) ib[j] = kind_item_box(t, x4, kind, j, pad);
@@ -222,7 +305,7 @@ static void broad_kind(const topo *t, const float *x4, float pad, int kind, int 
             fbox q = kind_query_box(t, x4, kind, i, pad);
             for (int j = 0; j < ni; ++j)
                 if (overlap(&q, &ib[j]) && kind_ok(t, kind, i, j))
-                    pv_push(out, kind == 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
+                    pv_push(out, kind >= 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
         }
     } else {
         sortkey *sk = (sortkey *)malloc(sizeof(sortkey) * ni);
@@ -245,7 +328,7 @@ static void broad_kind(const topo *t, const float *x4, float pad, int kind, int 
             for (int s = lo; s < ni && sk[s].lo <= q.hi[0]; ++s) {
                 int j = sk[s].idx;
                 if (overlap(&q, &ib[j]) && kind_ok(t, kind, i, j))
-                    pv_push(out, kind == 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
+                    pv_push(out, kind >= 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
             }
         }
         free(sk);
@@ -254,15 +337,15 @@ static void broad_kind(const topo *t, const float *x4, float pad, int kind, int 
     qsort(out->v, out->n, sizeof(ipair), cmp_pair);
 }
 
-/* Candidate sets C_VF, C_EE, C_VV.  Two-call protocol: with out == NULL only
- * the counts are written.  out receives VF pairs, then EE, then VV, each
- * sorted lexicographically. */
-long orc_candidates(const float *x4, int n, const int *edges, int ne, const int *tris, int nt,
-                    float pad, int brute, int *out, long counts[3]) {
+/* Candidate sets C_VF, C_EE, C_VV, C_VE.  Two-call protocol: with out == NULL
+ * only the counts are written.  out receives VF pairs, then EE, VV and VE
+ * (point, edge), each sorted lexicographically. */
+long orc_candidates_ext(const float *x4, int n, const int *edges, int ne, const int *tris, int nt,
+                        const orc_extra *ex, float pad, int brute, int *out, long counts[N_PAIR_KINDS]) {
     topo t;
-    topo_init(&t, n, edges, ne, tris, nt, x4);
+    topo_init_ext(&t, n, edges, ne, tris, nt, x4, ex);
     long total = 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < N_PAIR_KINDS; ++k) {
         pairvec pv = {0, 0, 0};
         broad_kind(&t, x4, pad, k, brute, &pv);
         counts[k] = pv.n;
@@ -277,6 +360,11 @@ long orc_candidates(const float *x4, int n, const int *edges, int ne, const int 
     }
     topo_free(&t);
     return total;
+}
+
+long orc_candidates(const float *x4, int n, const int *edges, int ne, const int *tris, int nt,
+                    float pad, int brute, int *out, long counts[N_PAIR_KINDS]) {
+    return orc_candidates_ext(x4, n, edges, ne, tris, nt, NULL, pad, brute, out, counts);
 }
 
 /* ------------------------------------------------------- closest points */
@@ -345,6 +433,15 @@ void orc_closest_segments(const double *p1, const double *q1, const double *p2, 
         }
     }
     *s_out = s; *t_out = t;
+}
+
+/* Closest point of segment ab to p: parameter t = (p - a).(b - a) / |b - a|^2
+ * clamped to [0, 1] (t = 0 for a degenerate segment). */
+double orc_closest_point_segment(const double *p, const double *a, const double *b) {
+    double ab[3], ap[3];
+    sub3(b, a, ab); sub3(p, a, ap);
+    double l2 = dot3(ab, ab);
+    return l2 > 0.0 ? clamp01(dot3(ap, ab) / l2) : 0.0;
 }
 
 /* ---------------------------------------------------------- narrow phase */
@@ -425,6 +522,17 @@ static int narrow_vv(planevec *out, const double *x3, const double *w, int p, in
     return emit_pair(out, w, x3 + 3 * p, x3 + 3 * q, &p, &one, 1, &q, &one, 1, P, make_key(2, p, q), vflag);
 }
 
+/* X4: isolated point p against free edge e; side A is the point. */
+static int narrow_ve(planevec *out, const double *x3, const double *w, const topo *t, int p, int e,
+                      const orc_params *P, unsigned char *vflag) {
+    const int *E = t->edges + 2 * e;
+    double u = orc_closest_point_segment(x3 + 3 * p, x3 + 3 * E[0], x3 + 3 * E[1]);
+    double q[3];
+    for (int i = 0; i < 3; ++i) q[i] = (1 - u) * x3[3 * E[0] + i] + u * x3[3 * E[1] + i];
+    double one = 1.0, bb[2] = {1 - u, u};
+    return emit_pair(out, w, x3 + 3 * p, q, &p, &one, 1, E, bb, 2, P, make_key(3, p, e), vflag);
+}
+
 /* Per-vertex region = CSR list of planes sorted by key. */
 typedef struct {
     int n;
@@ -433,7 +541,7 @@ typedef struct {
     long total;
     double *dlimit;      /* +inf, or the step bound of an overflowing vertex (R16) */
     unsigned char *vflag;/* bit0 overflow, bit1 band pair */
-    long cand[3], acc[3];
+    long cand[N_PAIR_KINDS], acc[N_PAIR_KINDS];
 } orc_regions;
 
 static int cmp_plane(const void *x, const void *y) {
@@ -455,7 +563,7 @@ static orc_regions *build_regions(const double *x3, const double *w, const topo 
     R->n = n;
     R->vflag = (unsigned char *)calloc(n > 0 ? n : 1, 1);
     planevec pv = {0, 0, 0};
-    for (int kind = 0; kind < 3; ++kind) {
+    for (int kind = 0; kind < N_PAIR_KINDS; ++kind) {
         pairvec c = {0, 0, 0};
         broad_kind(t, x4, P->pad, kind, 0, &c);
         R->cand[kind] = c.n;
@@ -463,7 +571,8 @@ static orc_regions *build_regions(const double *x3, const double *w, const topo 
             int acc;
             if (kind == 0) acc = narrow_vf(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
             else if (kind == 1) acc = narrow_ee(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
-            else acc = narrow_vv(&pv, x3, w, c.v[i].a, c.v[i].b, P, R->vflag);
+            else if (kind == 2) acc = narrow_vv(&pv, x3, w, c.v[i].a, c.v[i].b, P, R->vflag);
+            else acc = narrow_ve(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
             R->acc[kind] += acc;
         }
         free(c.v);
@@ -494,10 +603,10 @@ void orc_regions_free(orc_regions *R) {
     free(R->offs); free(R->p); free(R->dlimit); free(R->vflag); free(R);
 }
 
-orc_regions *orc_build(const double *x3, const float *x4w, int n, const int *edges, int ne,
-                       const int *tris, int nt, const orc_params *P) {
+orc_regions *orc_build_ext(const double *x3, const float *x4w, int n, const int *edges, int ne,
+                           const int *tris, int nt, const orc_extra *ex, const orc_params *P) {
     topo t;
-    topo_init(&t, n, edges, ne, tris, nt, x4w);
+    topo_init_ext(&t, n, edges, ne, tris, nt, x4w, ex);
     double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) w[i] = (double)x4w[4 * i + 3];
     orc_regions *R = build_regions(x3, w, &t, P);
@@ -506,10 +615,15 @@ orc_regions *orc_build(const double *x3, const float *x4w, int n, const int *edg
     return R;
 }
 
+orc_regions *orc_build(const double *x3, const float *x4w, int n, const int *edges, int ne,
+                       const int *tris, int nt, const orc_params *P) {
+    return orc_build_ext(x3, x4w, n, edges, ne, tris, nt, NULL, P);
+}
+
 long orc_regions_total(const orc_regions *R) { return R->total; }
 
 void orc_regions_export(const orc_regions *R, long *offs, double *planes4, double *phi, u64 *key,
-                        double *dlimit, unsigned char *vflag, long *cand_acc6) {
+                        double *dlimit, unsigned char *vflag, long *cand_acc) {
     for (int i = 0; i <= R->n; ++i) offs[i] = R->offs[i];
     for (long k = 0; k < R->total; ++k) {
         planes4[4 * k + 0] = R->p[k].n[0];
@@ -520,7 +634,7 @@ void orc_regions_export(const orc_regions *R, long *offs, double *planes4, doubl
         key[k] = R->p[k].key;
     }
     for (int i = 0; i < R->n; ++i) { dlimit[i] = R->dlimit[i]; vflag[i] = R->vflag[i]; }
-    for (int k = 0; k < 3; ++k) { cand_acc6[k] = R->cand[k]; cand_acc6[3 + k] = R->acc[k]; }
+    for (int k = 0; k < N_PAIR_KINDS; ++k) { cand_acc[k] = R->cand[k]; cand_acc[N_PAIR_KINDS + k] = R->acc[k]; }
 }
 
 /* ------------------------------------------------------------- Alg. 1 */
@@ -753,6 +867,44 @@ int orc_edge_colors(const int *edges, int ne, int n, int *color) {
     return ncol;
 }
 
+/* Greedy first-fit colouring of tetrahedra (no two of a colour share a vertex),
+ * in tetrahedron order (X3). */
+int orc_tet_colors(const int *tets, int ntet, int n, int *color) {
+    u64 *used = (u64 *)calloc(n > 0 ? n : 1, sizeof(u64));
+    int ncol = 0;
+    for (int q = 0; q < ntet; ++q) {
+        const int *T = tets + 4 * q;
+        u64 m = used[T[0]] | used[T[1]] | used[T[2]] | used[T[3]];
+        int c = 0;
+        while (c < 64 && (m >> c & 1ull)) ++c;
+        if (c == 64) { free(used); return -1; }
+        color[q] = c;
+        for (int k = 0; k < 4; ++k) used[T[k]] |= 1ull << c;
+        if (c + 1 > ncol) ncol = c + 1;
+    }
+    free(used);
+    return ncol;
+}
+
+static void cross3(const double *a, const double *b, double *o) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Six times the signed volume of each tetrahedron (X2). */
+void orc_tet_volumes6(const double *x3, const int *tets, int ntet, double *out) {
+    for (int q = 0; q < ntet; ++q) {
+        const int *T = tets + 4 * q;
+        double e1[3], e2[3], e3[3], c[3];
+        sub3(x3 + 3 * T[1], x3 + 3 * T[0], e1);
+        sub3(x3 + 3 * T[2], x3 + 3 * T[0], e2);
+        sub3(x3 + 3 * T[3], x3 + 3 * T[0], e3);
+        cross3(e2, e3, c);
+        out[q] = dot3(e1, c);
+    }
+}
+
 typedef struct {
     int iters_run;
     long planes, violated, halts, overflow, shortened;
@@ -861,23 +1013,44 @@ void orc_response(double *y, const double *x, const double *xn, const double *pl
     free(all);
 }
 
-/* One substep of Alg. 4 with the readings R12-R16.  x3, v3 are updated in
- * place (FP64).  x4w supplies inverse masses; rest[e] the rest lengths.
- * vband (optional, per vertex) collects band flags over all iterations. */
-int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
-             const int *tris, int nt, const double *rest, const orc_params *P,
-             unsigned char *vband, orc_step_info *info) {
+/* One substep of Alg. 4 with the readings R12-R16 (and X1-X5 for the
+ * constraints in ex).  x3, v3 are updated in place (FP64).  x4w supplies
+ * inverse masses; rest[e] the edges' rest lengths.  vband (optional, per
+ * vertex) collects band flags over all iterations. */
+int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
+                 const int *tris, int nt, const double *rest, const orc_extra *ex, const orc_params *P,
+                 unsigned char *vband, orc_step_info *info) {
     topo t;
-    topo_init(&t, n, edges, ne, tris, nt, x4w);
+    topo_init_ext(&t, n, edges, ne, tris, nt, x4w, ex);
     double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) w[i] = (double)x4w[4 * i + 3];
-    int *color = (int *)malloc(sizeof(int) * (ne > 0 ? ne : 1));
-    int ncol = orc_edge_colors(edges, ne, n, color);
-    if (ncol < 0) { free(w); free(color); topo_free(&t); return -1; }
+    /* distance constraints: the edges, then the links (X1, X3) */
+    const int nl = ex ? ex->nl : 0, ntet = ex ? ex->ntet : 0;
+    const int nd = ne + nl;
+    int *dpair = (int *)malloc(sizeof(int) * 2 * (nd > 0 ? nd : 1));
+    double *drest = (double *)malloc(sizeof(double) * (nd > 0 ? nd : 1));
+    double *dcomp = (double *)malloc(sizeof(double) * (nd > 0 ? nd : 1));
+    for (int e = 0; e < ne; ++e) {
+        dpair[2 * e] = edges[2 * e]; dpair[2 * e + 1] = edges[2 * e + 1];
+        drest[e] = rest[e]; dcomp[e] = P->compliance;
+    }
+    for (int l = 0; l < nl; ++l) {
+        dpair[2 * (ne + l)] = ex->links[2 * l]; dpair[2 * (ne + l) + 1] = ex->links[2 * l + 1];
+        drest[ne + l] = ex->link_rest[l]; dcomp[ne + l] = ex->link_compliance[l];
+    }
+    int *color = (int *)malloc(sizeof(int) * (nd > 0 ? nd : 1));
+    int ncol = orc_edge_colors(dpair, nd, n, color);
+    int *tcolor = (int *)malloc(sizeof(int) * (ntet > 0 ? ntet : 1));
+    int ntcol = ntet > 0 ? orc_tet_colors(ex->tets, ntet, n, tcolor) : 0;
+    if (ncol < 0 || ntcol < 0) {
+        free(w); free(color); free(tcolor); free(dpair); free(drest); free(dcomp); topo_free(&t);
+        return -1;
+    }
     size_t N3 = sizeof(double) * 3 * (n > 0 ? n : 1);
     double *xn = (double *)malloc(N3), *xt = (double *)malloc(N3), *xc = (double *)malloc(N3);
     double *xs = (double *)malloc(N3), *pre = (double *)malloc(N3);
-    double *lambda = (double *)calloc(ne > 0 ? ne : 1, sizeof(double));
+    double *lambda = (double *)calloc(nd > 0 ? nd : 1, sizeof(double));
+    double *tlambda = (double *)calloc(ntet > 0 ? ntet : 1, sizeof(double));
     memcpy(xn, x3, N3);
     memcpy(xc, x3, N3);
     double dt = P->dt;
@@ -885,30 +1058,54 @@ int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, 
         for (int a = 0; a < 3; ++a)
             xt[3 * i + a] = w[i] > 0 ? x3[3 * i + a] + dt * v3[3 * i + a] + dt * dt * P->g[a] : x3[3 * i + a];
     memset(info, 0, sizeof(*info));
-    double at = P->compliance / (dt * dt);
+    double atv = ex ? ex->volume_compliance / (dt * dt) : 0.0;
     unsigned char *bflag = (unsigned char *)calloc(n > 0 ? n : 1, 1);
     for (int it = 0; it < P->iters; ++it) {
         orc_regions *R = build_regions(xc, w, &t, P);
         info->planes += R->total;
         memcpy(xs, xt, N3);
-        /* XPBD sweep of edge-distance constraints, colours ascending */
+        /* XPBD sweep of the distance constraints, colours ascending (R15, X3) */
         for (int c = 0; c < ncol; ++c) {
-            for (int e = 0; e < ne; ++e) {
+            for (int e = 0; e < nd; ++e) {
                 if (color[e] != c) continue;
-                int a = edges[2 * e], b = edges[2 * e + 1];
+                int a = dpair[2 * e], b = dpair[2 * e + 1];
+                double at = dcomp[e] / (dt * dt);
                 double wsum = w[a] + w[b] + at;
                 if (wsum == 0.0) continue;
                 double dd[3];
                 sub3(xs + 3 * a, xs + 3 * b, dd);
                 double L = norm3(dd);
                 if (L == 0.0) continue;
-                double C = L - rest[e];
+                double C = L - drest[e];
                 double dl = (-C - at * lambda[e]) / wsum;
                 for (int k = 0; k < 3; ++k) {
                     xs[3 * a + k] += w[a] * dl * dd[k] / L;
                     xs[3 * b + k] -= w[b] * dl * dd[k] / L;
                 }
                 lambda[e] += dl;
+            }
+        }
+        /* then the volume constraints of the tetrahedra, colours ascending (X2, X3) */
+        for (int c = 0; c < ntcol; ++c) {
+            for (int q = 0; q < ntet; ++q) {
+                if (tcolor[q] != c) continue;
+                const int *T = ex->tets + 4 * q;
+                double e1[3], e2[3], e3[3], g[4][3];
+                sub3(xs + 3 * T[1], xs + 3 * T[0], e1);
+                sub3(xs + 3 * T[2], xs + 3 * T[0], e2);
+                sub3(xs + 3 * T[3], xs + 3 * T[0], e3);
+                cross3(e2, e3, g[1]);
+                cross3(e3, e1, g[2]);
+                cross3(e1, e2, g[3]);
+                for (int k = 0; k < 3; ++k) g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);
+                double C = dot3(e1, g[1]) - ex->vol6_rest[q];
+                double den = atv;
+                for (int i = 0; i < 4; ++i) den += w[T[i]] * dot3(g[i], g[i]);
+                if (den == 0.0) continue;
+                double dl = (-C - atv * tlambda[q]) / den;
+                for (int i = 0; i < 4; ++i)
+                    for (int k = 0; k < 3; ++k) xs[3 * T[i] + k] += w[T[i]] * dl * g[i][k];
+                tlambda[q] += dl;
             }
         }
         /* contact response on every movable vertex, then the projection */
@@ -984,8 +1181,15 @@ int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, 
     }
     free(bflag);
     free(xn); free(xt); free(xc); free(xs); free(pre); free(lambda); free(w); free(color);
+    free(tlambda); free(tcolor); free(dpair); free(drest); free(dcomp);
     topo_free(&t);
     return 0;
+}
+
+int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
+             const int *tris, int nt, const double *rest, const orc_params *P,
+             unsigned char *vband, orc_step_info *info) {
+    return orc_step_ext(x3, v3, x4w, n, edges, ne, tris, nt, rest, NULL, P, vband, info);
 }
 
 void orc_rest_lengths(const double *x3, const int *edges, int ne, double *rest) {

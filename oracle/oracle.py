@@ -35,6 +35,14 @@ class OrcParams(C.Structure):
     ]
 
 
+class OrcExtra(C.Structure):
+    """Constraints beyond the collision edges (readings X1-X3 of the C file)."""
+    _fields_ = [
+        ("nl", C.c_int), ("links", C.c_void_p), ("link_compliance", C.c_void_p), ("link_rest", C.c_void_p),
+        ("ntet", C.c_int), ("tets", C.c_void_p), ("vol6_rest", C.c_void_p), ("volume_compliance", C.c_double),
+    ]
+
+
 class OrcStepInfo(C.Structure):
     _fields_ = [
         ("iters_run", C.c_int),
@@ -63,8 +71,14 @@ def lib():
         P = C.c_void_p
         _lib.orc_candidates.restype = C.c_long
         _lib.orc_candidates.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.c_float, C.c_int, P, P]
+        _lib.orc_candidates_ext.restype = C.c_long
+        _lib.orc_candidates_ext.argtypes = [P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcExtra), C.c_float,
+                                            C.c_int, P, P]
         _lib.orc_build.restype = C.c_void_p
         _lib.orc_build.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcParams)]
+        _lib.orc_build_ext.restype = C.c_void_p
+        _lib.orc_build_ext.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcExtra),
+                                       C.POINTER(OrcParams)]
         _lib.orc_regions_total.restype = C.c_long
         _lib.orc_regions_total.argtypes = [P]
         _lib.orc_regions_export.argtypes = [P, P, P, P, P, P, P, P]
@@ -77,6 +91,14 @@ def lib():
         _lib.orc_step.restype = C.c_int
         _lib.orc_step.argtypes = [P, P, P, C.c_int, P, C.c_int, P, C.c_int, P,
                                   C.POINTER(OrcParams), P, C.POINTER(OrcStepInfo)]
+        _lib.orc_step_ext.restype = C.c_int
+        _lib.orc_step_ext.argtypes = [P, P, P, C.c_int, P, C.c_int, P, C.c_int, P, C.POINTER(OrcExtra),
+                                      C.POINTER(OrcParams), P, C.POINTER(OrcStepInfo)]
+        _lib.orc_tet_colors.restype = C.c_int
+        _lib.orc_tet_colors.argtypes = [P, C.c_int, C.c_int, P]
+        _lib.orc_tet_volumes6.argtypes = [P, P, C.c_int, P]
+        _lib.orc_closest_point_segment.restype = C.c_double
+        _lib.orc_closest_point_segment.argtypes = [P, P, P]
         _lib.orc_rest_lengths.argtypes = [P, P, C.c_int, P]
         _lib.orc_min_distances.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.c_double, P]
         _lib.orc_count_edge_triangle_intersections.restype = C.c_long
@@ -118,32 +140,67 @@ def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
     return o
 
 
-def candidates(x4: np.ndarray, edges: np.ndarray, tris: np.ndarray, pad: float, brute: bool = False):
-    """Candidate sets C_VF, C_EE, C_VV under the binary32 padded-AABB
-    predicate with the exclusions of Alg. 3, each sorted lexicographically."""
+class Extra:
+    """Links, tetrahedra and their rest values for the mixed-scene readings
+    X1-X5 (rest lengths and rest volumes from the rest positions in FP64).
+    Holds the arrays the C structure points to."""
+
+    def __init__(self, rest_x3, links=None, link_compliance=None, tets=None, volume_compliance=0.0):
+        rest_x3 = _c(rest_x3, np.float64)
+        self.links = _c(np.zeros((0, 2)) if links is None else links, np.int32).reshape(-1, 2)
+        self.link_compliance = _c(np.zeros(len(self.links)) if link_compliance is None else link_compliance,
+                                  np.float64)
+        self.link_rest = rest_lengths(rest_x3, self.links) if len(self.links) else np.zeros(0)
+        self.tets = _c(np.zeros((0, 4)) if tets is None else tets, np.int32).reshape(-1, 4)
+        self.vol6_rest = tet_volumes6(rest_x3, self.tets) if len(self.tets) else np.zeros(0)
+        self.s = OrcExtra()
+        self.s.nl = len(self.links)
+        self.s.links = _p(self.links)
+        self.s.link_compliance = _p(self.link_compliance)
+        self.s.link_rest = _p(self.link_rest)
+        self.s.ntet = len(self.tets)
+        self.s.tets = _p(self.tets)
+        self.s.vol6_rest = _p(self.vol6_rest)
+        self.s.volume_compliance = float(volume_compliance)
+
+    def ref(self):
+        return C.byref(self.s)
+
+
+def _xref(extra):
+    return None if extra is None else extra.ref()
+
+
+def candidates(x4: np.ndarray, edges: np.ndarray, tris: np.ndarray, pad: float, brute: bool = False,
+               extra: Extra | None = None):
+    """Candidate sets C_VF, C_EE, C_VV and C_VE (X4) under the binary32
+    padded-AABB predicate with the exclusions of Alg. 3, each sorted
+    lexicographically."""
     L = lib()
     x4 = _c(x4, np.float32)
     e = _c(edges, np.int32)
     t = _c(tris, np.int32)
-    counts = np.zeros(3, np.int64)
-    args = (_p(x4), len(x4), _p(e), len(e), _p(t), len(t), C.c_float(pad), int(brute))
-    tot = L.orc_candidates(*args, None, _p(counts))
+    counts = np.zeros(4, np.int64)
+    args = (_p(x4), len(x4), _p(e), len(e), _p(t), len(t), _xref(extra), C.c_float(pad), int(brute))
+    tot = L.orc_candidates_ext(*args, None, _p(counts))
     out = np.zeros((max(tot, 1), 2), np.int32)
-    L.orc_candidates(*args, _p(out), _p(counts))
-    c0, c1, c2 = (int(c) for c in counts)
-    return {"vf": out[:c0], "ee": out[c0:c0 + c1], "vv": out[c0 + c1:c0 + c1 + c2]}
+    L.orc_candidates_ext(*args, _p(out), _p(counts))
+    c0, c1, c2, c3 = (int(c) for c in counts)
+    return {"vf": out[:c0], "ee": out[c0:c0 + c1], "vv": out[c0 + c1:c0 + c1 + c2],
+            "ve": out[c0 + c1 + c2:c0 + c1 + c2 + c3]}
 
 
-def build_regions(x3: np.ndarray, x4w: np.ndarray, edges, tris, params: OrcParams):
-    """Per-vertex constraint sets (Alg. 3 over all vertices), CSR by vertex,
-    planes sorted by key within a vertex."""
+def build_regions(x3: np.ndarray, x4w: np.ndarray, edges, tris, params: OrcParams, extra: Extra | None = None):
+    """Per-vertex constraint sets (Alg. 3 over all vertices, plus the
+    vertex-edge pairs of X4), CSR by vertex, planes sorted by key within a
+    vertex."""
     L = lib()
     x3 = _c(x3, np.float64)
     x4w = _c(x4w, np.float32)
     e = _c(edges, np.int32)
     t = _c(tris, np.int32)
     n = len(x3)
-    h = L.orc_build(_p(x3), _p(x4w), n, _p(e), len(e), _p(t), len(t), C.byref(params))
+    h = L.orc_build_ext(_p(x3), _p(x4w), n, _p(e), len(e), _p(t), len(t), _xref(extra), C.byref(params))
     try:
         tot = L.orc_regions_total(h)
         offs = np.zeros(n + 1, np.int64)
@@ -152,12 +209,12 @@ def build_regions(x3: np.ndarray, x4w: np.ndarray, edges, tris, params: OrcParam
         key = np.zeros(max(tot, 1), np.uint64)
         dlimit = np.zeros(n, np.float64)
         vflag = np.zeros(n, np.uint8)
-        ca = np.zeros(6, np.int64)
+        ca = np.zeros(8, np.int64)
         L.orc_regions_export(h, _p(offs), _p(planes), _p(phi), _p(key), _p(dlimit), _p(vflag), _p(ca))
     finally:
         L.orc_regions_free(h)
     return {"offs": offs, "planes": planes[:tot], "phi": phi[:tot], "key": key[:tot],
-            "dlimit": dlimit, "vflag": vflag, "cand": ca[:3], "acc": ca[3:]}
+            "dlimit": dlimit, "vflag": vflag, "cand": ca[:4], "acc": ca[4:]}
 
 
 def project(x3, xp3, w, offs, planes4, keys, dlimit, params: OrcParams):
@@ -218,6 +275,31 @@ def edge_colors(edges, n):
     return col[: len(e)], nc
 
 
+def tet_colors(tets, n):
+    L = lib()
+    t = _c(tets, np.int32).reshape(-1, 4)
+    col = np.zeros(max(len(t), 1), np.int32)
+    nc = L.orc_tet_colors(_p(t), len(t), n, _p(col))
+    return col[: len(t)], nc
+
+
+def tet_volumes6(x3, tets):
+    """Six times the signed volume of each tetrahedron (X2)."""
+    L = lib()
+    x3 = _c(x3, np.float64)
+    t = _c(tets, np.int32).reshape(-1, 4)
+    out = np.zeros(max(len(t), 1))
+    L.orc_tet_volumes6(_p(x3), _p(t), len(t), _p(out))
+    return out[: len(t)]
+
+
+def closest_point_segment(p, a, b):
+    """Parameter t in [0, 1] of the point of segment ab closest to p."""
+    L = lib()
+    args = [_c(v, np.float64) for v in (p, a, b)]
+    return float(L.orc_closest_point_segment(*[_p(v) for v in args]))
+
+
 def rest_lengths(x3, edges):
     L = lib()
     x3 = _c(x3, np.float64)
@@ -227,8 +309,9 @@ def rest_lengths(x3, edges):
     return out[: len(e)]
 
 
-def step(x3, v3, x4w, edges, tris, rest, params: OrcParams):
-    """One substep of Alg. 4.  Returns (x, v, info, vband)."""
+def step(x3, v3, x4w, edges, tris, rest, params: OrcParams, extra: Extra | None = None):
+    """One substep of Alg. 4 (with the links and tetrahedra of X1-X3 when
+    extra is given).  Returns (x, v, info, vband)."""
     L = lib()
     x = _c(x3, np.float64).copy()
     v = _c(v3, np.float64).copy()
@@ -238,8 +321,8 @@ def step(x3, v3, x4w, edges, tris, rest, params: OrcParams):
     rest = _c(rest, np.float64)
     vband = np.zeros(len(x), np.uint8)
     info = OrcStepInfo()
-    rc = L.orc_step(_p(x), _p(v), _p(x4w), len(x), _p(e), len(e), _p(t), len(t), _p(rest),
-                    C.byref(params), _p(vband), C.byref(info))
+    rc = L.orc_step_ext(_p(x), _p(v), _p(x4w), len(x), _p(e), len(e), _p(t), len(t), _p(rest), _xref(extra),
+                        C.byref(params), _p(vband), C.byref(info))
     if rc != 0:
         raise RuntimeError("oracle step failed (edge colouring needs more than 64 colours)")
     return x, v, info, vband

@@ -31,6 +31,13 @@ class Scene:
     tris: np.ndarray               # (T, 3) int32
     edges: np.ndarray              # (E, 2) int32, a < b, sorted lexicographically
     params: dict = field(default_factory=dict)
+    # XPBD constraints that are no collision primitives (mixed scenes): extra
+    # distance links with their compliances, and tetrahedra with one volume
+    # compliance
+    links: np.ndarray = field(default_factory=lambda: np.zeros((0, 2), np.int32))
+    link_compliance: np.ndarray = field(default_factory=lambda: np.zeros(0, np.float32))
+    tets: np.ndarray = field(default_factory=lambda: np.zeros((0, 4), np.int32))
+    volume_compliance: float = 0.0
 
     @property
     def n_verts(self) -> int:
@@ -42,7 +49,8 @@ class Scene:
 
     def copy(self) -> "Scene":
         return Scene(self.name, self.x.copy(), self.v.copy(), self.tris.copy(),
-                     self.edges.copy(), dict(self.params))
+                     self.edges.copy(), dict(self.params), self.links.copy(), self.link_compliance.copy(),
+                     self.tets.copy(), self.volume_compliance)
 
 
 def default_params(r: float, xi: float, *, delta: float = 0.0, dt: float = 1.0 / 60.0,
@@ -340,6 +348,194 @@ def particle_cloud(n: int, spacing: float = 3e-3, jitter: float = 4e-4, seed: in
     params = default_params(1e-3, 2e-3, iters=iters, steps=steps, plane_capacity=plane_capacity)
     return _assemble("particle_cloud", [p, sp], [np.full(len(p), 1.0 / mass), np.zeros(len(sp))],
                      [None, st], [None, edges_of_tris(st)], params)
+
+
+def _tet_lattice(n: int, h: float, origin) -> tuple[np.ndarray, np.ndarray]:
+    """n^3 vertex lattice of spacing h; every cube cell split into six
+    tetrahedra around its main diagonal (the same diagonal in every cell, so
+    shared faces match)."""
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    P = np.stack([i.ravel(), j.ravel(), k.ravel()], 1).astype(np.float64) * h + np.asarray(origin, np.float64)
+    vid = lambda a, b, c: (a * n + b) * n + c  # noqa: E731
+    a, b, c = np.meshgrid(np.arange(n - 1), np.arange(n - 1), np.arange(n - 1), indexing="ij")
+    a, b, c = a.ravel(), b.ravel(), c.ravel()
+    c000, c111 = vid(a, b, c), vid(a + 1, b + 1, c + 1)
+    c100, c010, c001 = vid(a + 1, b, c), vid(a, b + 1, c), vid(a, b, c + 1)
+    c110, c101, c011 = vid(a + 1, b + 1, c), vid(a + 1, b, c + 1), vid(a, b + 1, c + 1)
+    tets = np.concatenate([np.stack(t, 1) for t in (
+        (c000, c100, c110, c111), (c000, c100, c101, c111), (c000, c010, c110, c111),
+        (c000, c010, c011, c111), (c000, c001, c101, c111), (c000, c001, c011, c111))], 0)
+    return P, tets.astype(np.int32)
+
+
+def _boundary_faces(tets: np.ndarray) -> np.ndarray:
+    """Faces that belong to exactly one tetrahedron (the volume's surface)."""
+    f = np.concatenate([tets[:, [0, 1, 2]], tets[:, [0, 1, 3]], tets[:, [0, 2, 3]], tets[:, [1, 2, 3]]], 0)
+    fs = np.sort(f, axis=1)
+    _, inv, cnt = np.unique(fs, axis=0, return_inverse=True, return_counts=True)
+    return f[cnt[inv.ravel()] == 1].astype(np.int32)
+
+
+def _hinge_links(tris: np.ndarray) -> np.ndarray:
+    """For every edge shared by two triangles, the two vertices opposite it
+    (the cloth's bending links)."""
+    t = np.asarray(tris, np.int64)
+    rows = []
+    for a, b, o in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+        e = np.sort(np.stack([t[:, a], t[:, b]], 1), axis=1)
+        rows.append(np.concatenate([e, t[:, [o]]], 1))
+    r = np.concatenate(rows, 0)
+    order = np.lexsort((r[:, 1], r[:, 0]))
+    r = r[order]
+    same = (r[1:, 0] == r[:-1, 0]) & (r[1:, 1] == r[:-1, 1])
+    pairs = np.stack([r[:-1][same, 2], r[1:][same, 2]], 1)
+    return np.sort(pairs, axis=1).astype(np.int32)
+
+
+def codimensional(rod_seg: int = 16, cube_n: int = 3, particle_layers: int = 1, seed: int = 6,
+                  iters: int = 10, steps: int = 20, plane_capacity: int = 128, speed: float = 0.5,
+                  cloth_bending: float = 1.0, rod_bending: float = 0.1, volume_compliance: float = 0.0) -> Scene:
+    """Rods, soft volumes, a cloth and particles in one simulation (a synthetic
+    stand-in for the paper's coupled codimensional scene, Sec. 5).
+
+    Lattice spacing h = 4 mm, scene width W = rod_seg * h.  Two crossing layers
+    of rods pinned at both ends (x-rods at y = 0, z-rods at y = 5 mm, 10 mm
+    apart), each with bending links to every second neighbour; a grid of soft
+    cubes (cube_n^3 lattice, six tetrahedra per cell, 8 mm apart) over the
+    left half, whose boundary triangles are their collision surface, whose
+    inner edges are links and whose tetrahedra carry volume constraints; a
+    cloth over the same half with hinge bending links; particle layers over the
+    whole width, so that half of them land on the cloth and half directly on
+    the rods (point-edge pairs).  Every movable vertex starts falling at
+    `speed`; positions are jittered by U(-0.2, 0.2) mm.  r = 2 mm, xi = 1 mm.
+    """
+    rng = np.random.default_rng(seed)
+    h = 4e-3
+    W = rod_seg * h
+    parts_p, parts_w, parts_t, parts_e, links, lcomp, tets = [], [], [], [], [], [], []
+    base = 0
+
+    def add(P, w, t=None, e=None, lk=None, lc=0.0, tt=None):
+        nonlocal base
+        parts_p.append(P)
+        parts_w.append(w)
+        parts_t.append(t)
+        parts_e.append(e)
+        if lk is not None and len(lk):
+            links.append(np.asarray(lk) + base)
+            lcomp.append(np.full(len(lk), lc))
+        if tt is not None and len(tt):
+            tets.append(np.asarray(tt) + base)
+        base += len(P)
+
+    # rods: x-rods at y = 0 and z-rods at y = 5 mm, pinned at both ends
+    n_rods = max(2, int(W / 0.01))
+    zs = (np.arange(n_rods) - (n_rods - 1) / 2.0) * 0.01
+    u = np.arange(rod_seg + 1) * h - W / 2.0
+    for layer in range(2):
+        for z in zs:
+            P = np.zeros((rod_seg + 1, 3))
+            if layer == 0:
+                P[:, 0], P[:, 2] = u, z
+            else:
+                P[:, 0], P[:, 1], P[:, 2] = z, 5e-3, u
+            w = np.full(rod_seg + 1, 1.0 / 2e-4)
+            w[0] = w[-1] = 0.0
+            k = np.arange(rod_seg)
+            bend = np.stack([np.arange(rod_seg - 1), np.arange(rod_seg - 1) + 2], 1)
+            add(P, w, None, np.stack([k, k + 1], 1), bend, rod_bending)
+    # soft cubes over the left half
+    side = (cube_n - 1) * h
+    pitch = side + 8e-3
+    ncx = max(1, int((W / 2.0) // pitch))
+    ncz = max(1, int(W // pitch))
+    y_cube = 0.015
+    for a in range(ncx):
+        for b in range(ncz):
+            org = (-W / 2.0 + a * pitch + 4e-3, y_cube, -W / 2.0 + b * pitch + 4e-3)
+            P, tt = _tet_lattice(cube_n, h, org)
+            faces = _boundary_faces(tt)
+            e_surf = edges_of_tris(faces)
+            e_all = canonical_edges(np.concatenate([tt[:, [i, j]] for i in range(4) for j in range(i + 1, 4)], 0))
+            surf = set(map(tuple, e_surf.tolist()))
+            inner = np.array([e for e in e_all.tolist() if tuple(e) not in surf], np.int32).reshape(-1, 2)
+            add(P, np.full(len(P), 1.0 / 5e-4), faces, e_surf, inner, 0.0, tt)
+    # cloth over the left half
+    y_cloth = y_cube + side + 8e-3
+    nx, nz = rod_seg // 2 + 1, rod_seg + 1
+    gi, gj = np.meshgrid(np.arange(nx), np.arange(nz), indexing="ij")
+    P = np.zeros((nx * nz, 3))
+    P[:, 0] = -W / 2.0 + gi.ravel() * h
+    P[:, 1] = y_cloth
+    P[:, 2] = -W / 2.0 + gj.ravel() * h
+    ct = _grid_tris(nx, nz)
+    add(P, np.full(len(P), 1.0 / 1e-4), ct, edges_of_tris(ct), _hinge_links(ct), cloth_bending)
+    # particle layers over the whole width
+    y_part = y_cloth + 8e-3
+    pi, pk, pl = np.meshgrid(np.arange(rod_seg), np.arange(rod_seg), np.arange(particle_layers), indexing="ij")
+    P = np.zeros((pi.size, 3))
+    P[:, 0] = -W / 2.0 + (pi.ravel() + 0.5) * h
+    P[:, 1] = y_part + pl.ravel() * h
+    P[:, 2] = -W / 2.0 + (pk.ravel() + 0.5) * h
+    add(P, np.full(len(P), 1.0 / 2e-4))
+
+    params = default_params(2e-3, 1e-3, iters=iters, steps=steps, plane_capacity=plane_capacity)
+    allp = np.concatenate(parts_p, 0)
+    allw = np.concatenate(parts_w, 0)
+    allp = allp + rng.uniform(-2e-4, 2e-4, size=allp.shape) * (allw > 0)[:, None]
+    vel = np.zeros_like(allp)
+    vel[:, 1] = -speed * (allw > 0)
+    offs = np.cumsum([0] + [len(q) for q in parts_p])
+    sc = _assemble("codimensional", [allp[offs[i]:offs[i + 1]] for i in range(len(parts_p))], parts_w,
+                   parts_t, parts_e, params, v=vel)
+    sc.links = np.concatenate(links, 0).astype(np.int32) if links else np.zeros((0, 2), np.int32)
+    sc.link_compliance = np.concatenate(lcomp, 0).astype(np.float32) if lcomp else np.zeros(0, np.float32)
+    sc.tets = np.concatenate(tets, 0).astype(np.int32) if tets else np.zeros((0, 4), np.int32)
+    sc.volume_compliance = float(volume_compliance)
+    return sc
+
+
+def particles_on_rod(n_seg: int = 8, seg_len: float = 4e-3, n_particles: int = 12, height: float = 3e-3,
+                     pinned_rod: bool = True, cloth_patch: bool = False, speed: float = 0.3, seed: int = 8,
+                     iters: int = 10, steps: int = 20, plane_capacity: int = 64) -> Scene:
+    """Particles dropped just above a rod along x (point-edge pairs only, plus
+    point-point pairs between the particles).  The rod is pinned at both ends
+    (or wholly static with pinned_rod=False); the particles sit `height` above
+    it, spread along it with U(-1, 1) mm offsets in x and z.  cloth_patch adds
+    a small static cloth of 1 mm spacing far away, whose short edges shrink the
+    edge cell so that the rod's segments become oversized edges.
+    r = 2 mm, xi = 1 mm."""
+    rng = np.random.default_rng(seed)
+    L = n_seg * seg_len
+    P = np.zeros((n_seg + 1, 3))
+    P[:, 0] = np.arange(n_seg + 1) * seg_len - L / 2.0
+    w = np.full(n_seg + 1, 1.0 / 2e-4) if pinned_rod else np.zeros(n_seg + 1)
+    w[0] = w[-1] = 0.0
+    k = np.arange(n_seg)
+    parts_p, parts_w, parts_t, parts_e = [P], [w], [None], [np.stack([k, k + 1], 1)]
+    bend = np.stack([np.arange(n_seg - 1), np.arange(n_seg - 1) + 2], 1) if pinned_rod else np.zeros((0, 2))
+    Q = np.zeros((n_particles, 3))
+    Q[:, 0] = (np.arange(n_particles) + 0.5) / n_particles * L - L / 2.0 + rng.uniform(-1e-3, 1e-3, n_particles)
+    Q[:, 1] = height + 4e-3 * (np.arange(n_particles) % 2)
+    Q[:, 2] = rng.uniform(-1e-3, 1e-3, n_particles)
+    parts_p.append(Q)
+    parts_w.append(np.full(n_particles, 1.0 / 2e-4))
+    parts_t.append(None)
+    parts_e.append(None)
+    if cloth_patch:
+        C = _cloth_grid(12, 1e-3, (0.0, 0.05, 0.05), rng, 0.0)
+        ct = _grid_tris(12, 12)
+        parts_p.append(C)
+        parts_w.append(np.zeros(len(C)))
+        parts_t.append(ct)
+        parts_e.append(edges_of_tris(ct))
+    params = default_params(2e-3, 1e-3, iters=iters, steps=steps, plane_capacity=plane_capacity)
+    vel = np.zeros((sum(len(q) for q in parts_p), 3))
+    vel[n_seg + 1:n_seg + 1 + n_particles, 1] = -speed
+    sc = _assemble("particles_on_rod", parts_p, parts_w, parts_t, parts_e, params, v=vel)
+    sc.links = np.asarray(bend, np.int32).reshape(-1, 2)
+    sc.link_compliance = np.full(len(sc.links), 0.1, np.float32)
+    return sc
 
 
 def batch(n_scenes: int = 512, seed: int = 4, min_verts: int = 1024, max_verts: int = 65536,
