@@ -45,6 +45,11 @@ WORKLOADS = {
                                                           mu_s=0.3, mu_k=0.2),
                              "self-colliding stack with the contact response of Sec. 3.3 on: repulsion range "
                              "0.5 mm, k = 2 N/m, occlusion width 0.25 mm, friction mu_s 0.3 / mu_k 0.2"),
+    "codimensional": (lambda seed: S.codimensional(rod_seg=256, cube_n=5, seed=seed),
+                      "rods, soft volumes, cloth and particles in one simulation: two crossing layers of 102 pinned "
+                      "rods of 256 x 4 mm segments with bending links, 882 tetrahedral cubes (5^3 lattice, volume "
+                      "constraints), a 129x257 cloth with hinge bending, 65,536 particles (261,367 verts), "
+                      "r=2 mm, xi=1 mm, 10 iterations"),
     "cloth_stack_128": (lambda seed: S.cloth_stack(n_side=128, seed=seed),
                         "profiling case of the stack recipe: 4 layers of 128x128 cloth (65,536 verts)"),
     "wires_64": (lambda seed: S.wires(n_grid=64, seed=seed),

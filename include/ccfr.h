@@ -91,6 +91,34 @@ typedef struct {
                               them (may be NULL: rest lengths from the first step's x)      */
 } ccfr_mesh;
 
+/* A scene that mixes rods, cloth, volumes and particles in one simulation (the
+ * coupled codimensional scene of Sec. 5): the collision topology of ccfr_mesh
+ * plus XPBD constraints that are no collision primitives.  Alg. 4 solves "a
+ * set of XPBD constraints" without naming them; this library takes
+ *  - links: extra distance constraints (bending: the two vertices opposite an
+ *    interior cloth edge, every second rod neighbour; the inner edges of
+ *    tetrahedral volumes), each with its own compliance, rest lengths from
+ *    rest_x;
+ *  - tetrahedra: volume constraints C = 6 V - 6 V0, with 6 V = (x1 - x0) .
+ *    ((x2 - x0) x (x3 - x0)) signed and V0 from rest_x, one compliance.
+ * Each iteration sweeps the distance constraints (the edges in canonical
+ * order, then the links, coloured together first-fit, colours ascending) and
+ * then the tetrahedra (coloured first-fit in their order).  A vertex that
+ * belongs to links or tetrahedra only (the inside of a volume) takes no part
+ * in collision; the isolated points (no edge, link or tetrahedron) meet the
+ * free edges (edges of no triangle, i.e. rods) through point-edge pairs, which
+ * Alg. 3 lacks.  Arrays are device pointers (or host memory), read at
+ * ccfr_create_ext only. */
+typedef struct {
+    ccfr_mesh mesh;                /* collision topology, as for ccfr_create          */
+    int n_links;
+    const int* links;              /* n_links x 2 vertex ids, a != b                   */
+    const float* link_compliance;  /* n_links compliances (>= 0), XPBD alpha            */
+    int n_tets;
+    const int* tets;               /* n_tets x 4 distinct vertex ids                    */
+    float volume_compliance;       /* compliance of every volume constraint (>= 0)      */
+} ccfr_mesh_ext;
+
 /* Counters accumulated since the last ccfr_reset_stats (device-side, read by
  * ccfr_get_stats).  Per-iteration quantities are summed over iterations. */
 typedef struct {
@@ -127,6 +155,8 @@ typedef struct {
                                                          oversized primitives, [15] zero   */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
+    unsigned long long cand_ve, pairs_ve, planes_ve;  /* point-edge pairs (ccfr_mesh_ext):
+                                                         candidates, accepted, planes   */
 } ccfr_stats;
 
 typedef struct ccfr_ctx ccfr_ctx;
@@ -136,6 +166,14 @@ typedef struct ccfr_ctx ccfr_ctx;
  * multipliers).  No later call allocates device memory.  `stream` orders the
  * set-up copies.  On failure *out is NULL. */
 ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out);
+
+/* ccfr_create for a scene with links and tetrahedra (ccfr_mesh_ext above):
+ * the same context, whose substep also sweeps those constraints and whose
+ * region build adds the point-edge pairs.  Errors: CCFR_ERR_INVALID_ARG for a
+ * vertex id out of range, a link with equal ends or a negative compliance, a
+ * tetrahedron with a repeated vertex, more than 64 colours; otherwise as
+ * ccfr_create. */
+ccfr_status ccfr_create_ext(const ccfr_mesh_ext* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out);
 
 /* Release the context and all its device memory (synchronises the context's work). */
 ccfr_status ccfr_destroy(ccfr_ctx* ctx);

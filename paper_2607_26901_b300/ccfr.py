@@ -43,13 +43,20 @@ class Mesh(C.Structure):
                 ("edges", C.c_void_p), ("tris", C.c_void_p), ("rest_x", C.c_void_p)]
 
 
+class MeshExt(C.Structure):
+    """ccfr_mesh_ext: collision topology plus links and tetrahedra."""
+    _fields_ = [("mesh", Mesh), ("n_links", C.c_int), ("links", C.c_void_p), ("link_compliance", C.c_void_p),
+                ("n_tets", C.c_int), ("tets", C.c_void_p), ("volume_compliance", C.c_float)]
+
+
 class Stats(C.Structure):
     _fields_ = [(n, C.c_ulonglong) for n in
                 ("cand_vf", "cand_ee", "cand_vv", "pairs_vf", "pairs_ee", "pairs_vv", "planes_vf", "planes_ee",
                  "planes_vv", "planes",
                  "overflow_verts", "violated_verts", "halts", "ee_fp64", "feas_fp64", "feas_halts",
                  "iterations", "steps")] + [("aux", C.c_ulonglong * 16), ("max_planes", C.c_uint),
-                                            ("error_flags", C.c_uint)]
+                                            ("error_flags", C.c_uint), ("cand_ve", C.c_ulonglong),
+                                            ("pairs_ve", C.c_ulonglong), ("planes_ve", C.c_ulonglong)]
 
     def as_dict(self) -> dict:
         d = {n: getattr(self, n) for n, _ in self._fields_}
@@ -85,6 +92,7 @@ def lib():
         P = C.c_void_p
         sig = {
             "ccfr_create": [C.POINTER(Mesh), C.POINTER(Params), P, C.POINTER(P)],
+            "ccfr_create_ext": [C.POINTER(MeshExt), C.POINTER(Params), P, C.POINTER(P)],
             "ccfr_destroy": [P],
             "ccfr_build_regions": [P, P, P],
             "ccfr_project": [P, P, P, P, P],
@@ -129,7 +137,7 @@ def lib():
 
 
 def exported_symbols() -> list[str]:
-    return ["ccfr_create", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
+    return ["ccfr_create", "ccfr_create_ext", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
             "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
             "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
             "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune",
@@ -189,7 +197,8 @@ def project_static(x, x_io, planes, count, params: Params, dmin_drop=None, halt=
 class Context:
     """One scene on the current CUDA device (wraps a ccfr_ctx)."""
 
-    def __init__(self, edges, tris, n_verts: int, params: Params, rest_x=None, stream=None):
+    def __init__(self, edges, tris, n_verts: int, params: Params, rest_x=None, stream=None, links=None,
+                 link_compliance=None, tets=None, volume_compliance: float = 0.0):
         import torch
         self.torch = torch
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -205,7 +214,19 @@ class Context:
                  rest.data_ptr() if rest is not None else None)
         self.params = params
         h = C.c_void_p()
-        _check(lib().ccfr_create(C.byref(m), C.byref(params), _stream(stream), C.byref(h)), "ccfr_create")
+        if links is None and tets is None:
+            _check(lib().ccfr_create(C.byref(m), C.byref(params), _stream(stream), C.byref(h)), "ccfr_create")
+        else:
+            lk = torch.as_tensor(np.asarray(links if links is not None else np.zeros((0, 2)), np.int32)
+                                 .reshape(-1, 2)).to(dev).contiguous()
+            lc = torch.as_tensor(np.asarray(link_compliance if link_compliance is not None else np.zeros(len(lk)),
+                                            np.float32).reshape(-1)).to(dev).contiguous()
+            tt = torch.as_tensor(np.asarray(tets if tets is not None else np.zeros((0, 4)), np.int32)
+                                 .reshape(-1, 4)).to(dev).contiguous()
+            me = MeshExt(m, int(lk.shape[0]), lk.data_ptr() if lk.numel() else None,
+                         lc.data_ptr() if lc.numel() else None, int(tt.shape[0]), tt.data_ptr() if tt.numel() else None,
+                         float(volume_compliance))
+            _check(lib().ccfr_create_ext(C.byref(me), C.byref(params), _stream(stream), C.byref(h)), "ccfr_create_ext")
         self.h = h
         nv, cap, ncol = C.c_int(), C.c_int(), C.c_int()
         _check(lib().ccfr_get_info(h, C.byref(nv), C.byref(cap), C.byref(ncol)), "ccfr_get_info")
@@ -216,7 +237,11 @@ class Context:
     def from_scene(cls, scene, flags: int = 0, plane_capacity: int | None = None, iters: int | None = None,
                    cell_size: float = 0.0, cell_factor: float = 0.0, stream=None):
         p = make_params(scene.params, flags, plane_capacity, iters, cell_size, cell_factor)
-        return cls(scene.edges, scene.tris, scene.n_verts, p, rest_x=scene.x, stream=stream)
+        ext = {}
+        if len(getattr(scene, "links", ())) or len(getattr(scene, "tets", ())):
+            ext = dict(links=scene.links, link_compliance=scene.link_compliance, tets=scene.tets,
+                       volume_compliance=scene.volume_compliance)
+        return cls(scene.edges, scene.tris, scene.n_verts, p, rest_x=scene.x, stream=stream, **ext)
 
     @classmethod
     def from_scenes(cls, scenes, flags: int = 0, plane_capacity: int | None = None, stream=None):

@@ -1,5 +1,6 @@
 // C ABI of the CCFR library: context set-up, argument checks, launch
 // orchestration and CUDA-graph capture of the substep.  See include/ccfr.h.
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,14 @@ struct GraphEntry {
     cudaGraphExec_t exec;
 };
 
+// Constraints beyond the collision edges (ccfr_create_ext), on the host.
+struct Extras {
+    std::vector<int> links;         // 2 per link
+    std::vector<float> link_comp;   // per link
+    std::vector<int> tets;          // 4 per tetrahedron
+    float vol_comp = 0.f;
+};
+
 }  // namespace
 
 struct ccfr_ctx {
@@ -29,6 +38,8 @@ struct ccfr_ctx {
     unsigned* tile_sums = nullptr;
     std::vector<int> color_off;
     int n_colors = 0;
+    std::vector<int> tcolor_off;    // colours of the tetrahedra
+    int n_tcolors = 0;
     cudaStream_t cap_stream = nullptr;
     SideStream side;
     std::vector<GraphEntry> graphs;
@@ -106,7 +117,7 @@ void enqueue_step(ccfr_ctx* c, float4* x, float4* v, cudaStream_t st, StageTimer
     int early = (c->prm.flags & CCFR_FLAG_EARLY_EXIT) ? 1 : 0;
     for (int it = 0; it < c->prm.solver_iters; ++it)
         launch_iteration(c->dc, x, st, c->color_off.data(), c->n_colors, c->tile_sums, c->n_buckets_total, early, tm,
-                         &c->side);
+                         &c->side, c->tcolor_off.data(), c->n_tcolors);
     launch_update(c->dc, x, v, st);
     if (tm) tm->mark(ST_MISC, st);
 }
@@ -140,36 +151,96 @@ const char* ccfr_status_string(ccfr_status s) {
 static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int>& ht, int N,
                                const ccfr_params* params, const float* rest_x,
                                const std::vector<unsigned short>& vscene, const std::vector<float4>& sparams,
-                               cudaStream_t st, ccfr_ctx** out) {
+                               cudaStream_t st, ccfr_ctx** out, const Extras* ex = nullptr) {
     const int E = (int)(he.size() / 2), T = (int)(ht.size() / 3);
+    const int L = ex ? (int)(ex->links.size() / 2) : 0, Q = ex ? (int)(ex->tets.size() / 4) : 0;
+    // 1: in a collision edge; 2: only in links or tetrahedra (no collision)
     std::vector<char> used(N > 0 ? N : 1, 0);
     for (int e = 0; e < E; ++e) { used[he[2 * e]] = 1; used[he[2 * e + 1]] = 1; }
+    for (int i = 0; i < L; ++i)
+        for (int k = 0; k < 2; ++k) if (!used[ex->links[2 * i + k]]) used[ex->links[2 * i + k]] = 2;
+    for (int q = 0; q < Q; ++q)
+        for (int k = 0; k < 4; ++k) if (!used[ex->tets[4 * q + k]]) used[ex->tets[4 * q + k]] = 2;
     std::vector<int> pts;
-    for (int i = 0; i < N; ++i) if (!used[i]) pts.push_back(i);
-    // greedy first-fit edge colouring in canonical edge order
+    bool interior = false;
+    for (int i = 0; i < N; ++i) {
+        if (!used[i]) pts.push_back(i);
+        if (used[i] == 2) interior = true;
+    }
+    // free edges (of no triangle) meet the isolated points
+    std::vector<unsigned char> efree;
+    if (!pts.empty() && E > 0) {
+        efree.assign(E, 1);
+        for (int t = 0; t < T; ++t)
+            for (int k = 0; k < 3; ++k) {
+                int a = ht[3 * t + k], b = ht[3 * t + (k + 1) % 3];
+                if (a > b) std::swap(a, b);
+                int lo = 0, hi = E;
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if (he[2 * mid] < a || (he[2 * mid] == a && he[2 * mid + 1] < b)) lo = mid + 1; else hi = mid;
+                }
+                if (lo < E && he[2 * lo] == a && he[2 * lo + 1] == b) efree[lo] = 0;
+            }
+        bool any = false;
+        for (int e = 0; e < E; ++e) any |= efree[e] != 0;
+        if (!any) efree.clear();
+    }
+    // distance constraints: the edges in canonical order, then the links;
+    // greedy first-fit colouring in that order
+    const int ND = E + L;
+    auto dpair = [&](int i, int k) { return i < E ? he[2 * i + k] : ex->links[2 * (i - E) + k]; };
     std::vector<unsigned long long> vmask(N > 0 ? N : 1, 0ull);
-    std::vector<int> col(E > 0 ? E : 1, 0);
+    std::vector<int> col(ND > 0 ? ND : 1, 0);
     int ncol = 0;
-    for (int e = 0; e < E; ++e) {
-        unsigned long long m = vmask[he[2 * e]] | vmask[he[2 * e + 1]];
+    for (int e = 0; e < ND; ++e) {
+        unsigned long long m = vmask[dpair(e, 0)] | vmask[dpair(e, 1)];
         int k = 0;
         while (k < 64 && ((m >> k) & 1ull)) ++k;
         if (k == 64) return CCFR_ERR_INVALID_ARG;
         col[e] = k;
-        vmask[he[2 * e]] |= 1ull << k;
-        vmask[he[2 * e + 1]] |= 1ull << k;
+        vmask[dpair(e, 0)] |= 1ull << k;
+        vmask[dpair(e, 1)] |= 1ull << k;
         if (k + 1 > ncol) ncol = k + 1;
     }
     std::vector<int> coff(ncol + 1, 0);
-    for (int e = 0; e < E; ++e) coff[col[e] + 1]++;
+    for (int e = 0; e < ND; ++e) coff[col[e] + 1]++;
     for (int k = 0; k < ncol; ++k) coff[k + 1] += coff[k];
-    std::vector<int> ecol(2 * (size_t)E);
+    std::vector<int> ecol(2 * (size_t)ND);
+    std::vector<float> acol(ND > 0 ? ND : 1);
     {
         std::vector<int> fill(coff.begin(), coff.end() - 1);
-        for (int e = 0; e < E; ++e) {
+        for (int e = 0; e < ND; ++e) {
             int pos = fill[col[e]]++;
-            ecol[2 * pos] = he[2 * e];
-            ecol[2 * pos + 1] = he[2 * e + 1];
+            ecol[2 * pos] = dpair(e, 0);
+            ecol[2 * pos + 1] = dpair(e, 1);
+            acol[pos] = (e < E ? params->compliance : ex->link_comp[e - E]) / (params->dt * params->dt);
+        }
+    }
+    // tetrahedra: greedy first-fit colouring in their order
+    std::vector<int> tcoff(1, 0), tcol4;
+    int ntcol = 0;
+    if (Q > 0) {
+        std::fill(vmask.begin(), vmask.end(), 0ull);
+        std::vector<int> tc(Q);
+        for (int q = 0; q < Q; ++q) {
+            const int* Tq = &ex->tets[4 * q];
+            unsigned long long m = vmask[Tq[0]] | vmask[Tq[1]] | vmask[Tq[2]] | vmask[Tq[3]];
+            int k = 0;
+            while (k < 64 && ((m >> k) & 1ull)) ++k;
+            if (k == 64) return CCFR_ERR_INVALID_ARG;
+            tc[q] = k;
+            for (int j = 0; j < 4; ++j) vmask[Tq[j]] |= 1ull << k;
+            if (k + 1 > ntcol) ntcol = k + 1;
+        }
+        tcoff.assign(ntcol + 1, 0);
+        for (int q = 0; q < Q; ++q) tcoff[tc[q] + 1]++;
+        for (int k = 0; k < ntcol; ++k) tcoff[k + 1] += tcoff[k];
+        tcol4.resize(4 * (size_t)Q);
+        std::vector<int> fill(tcoff.begin(), tcoff.end() - 1);
+        for (int q = 0; q < Q; ++q) {
+            int pos = fill[tc[q]]++;
+            for (int j = 0; j < 4; ++j) tcol4[4 * pos + j] = ex->tets[4 * q + j];
         }
     }
 
@@ -179,6 +250,8 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     c->prm = *params;
     c->color_off = coff;
     c->n_colors = ncol;
+    c->tcolor_off = tcoff;
+    c->n_tcolors = ntcol;
     DevCtx& d = c->dc;
     d.n_verts = N;
     d.n_edges = E;
@@ -196,6 +269,9 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     d.p.gy = params->gravity[1];
     d.p.gz = params->gravity[2];
     d.p.alpha_tilde = params->compliance / (params->dt * params->dt);
+    d.n_dist = ND;
+    d.n_tets = Q;
+    d.alpha_vol = ex ? ex->vol_comp / (params->dt * params->dt) : 0.f;
     d.p.max_passes = params->max_passes;
     d.p.K = params->plane_capacity;
     d.p.cell_size = params->cell_size;
@@ -253,15 +329,29 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.x_tilde, N) == cudaSuccess;
     ok &= dalloc(c, &d.x_n, N) == cudaSuccess;
     ok &= dalloc(c, &d.x_s, N) == cudaSuccess;
-    ok &= dalloc(c, &d.lambda, E) == cudaSuccess;
+    ok &= dalloc(c, &d.lambda, ND) == cudaSuccess;
     int2* edges = nullptr;
     int2* edges_col = nullptr;
     int3* tris = nullptr;
     int* dpts = nullptr;
     float* rest = nullptr;
+    float* alpha = nullptr;
+    int4* tets_col = nullptr;
+    unsigned char* vcol = nullptr;
     ok &= dalloc(c, &edges, E) == cudaSuccess;
-    ok &= dalloc(c, &edges_col, E) == cudaSuccess;
-    ok &= dalloc(c, &rest, E) == cudaSuccess;
+    ok &= dalloc(c, &edges_col, ND) == cudaSuccess;
+    ok &= dalloc(c, &rest, ND) == cudaSuccess;
+    ok &= dalloc(c, &alpha, ND) == cudaSuccess;
+    if (Q > 0) {
+        ok &= dalloc(c, &tets_col, Q) == cudaSuccess;
+        ok &= dalloc(c, &d.vol6_col, Q) == cudaSuccess;
+        ok &= dalloc(c, &d.tlambda, Q) == cudaSuccess;
+    }
+    if (interior) ok &= dalloc(c, &vcol, N) == cudaSuccess;
+    std::vector<int> hfree;
+    for (size_t e = 0; e < efree.size(); ++e) if (efree[e]) hfree.push_back((int)e);
+    int* dflist = nullptr;
+    if (!hfree.empty()) ok &= dalloc(c, &dflist, hfree.size()) == cudaSuccess;
     ok &= dalloc(c, &tris, T) == cudaSuccess;
     ok &= dalloc(c, &dpts, pts.size()) == cudaSuccess;
     ok &= dalloc(c, &d.ext_bits, 3) == cudaSuccess;
@@ -296,14 +386,30 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     d.edges = edges;
     d.edges_col = edges_col;
     d.rest_col = rest;
+    d.alpha_col = alpha;
+    d.tets_col = tets_col;
+    d.vcollide = vcol;
+    d.free_list = dflist;
+    d.n_free = (int)hfree.size();
     d.tris = tris;
     d.pts = dpts;
 
     cudaError_t err = cudaSuccess;
-    if (E) {
-        err = cudaMemcpyAsync(edges, he.data(), he.size() * sizeof(int), cudaMemcpyHostToDevice, st);
-        if (err == cudaSuccess) err = cudaMemcpyAsync(edges_col, ecol.data(), ecol.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (E) err = cudaMemcpyAsync(edges, he.data(), he.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    if (err == cudaSuccess && ND) {
+        err = cudaMemcpyAsync(edges_col, ecol.data(), ecol.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemcpyAsync(alpha, acol.data(), (size_t)ND * sizeof(float), cudaMemcpyHostToDevice, st);
     }
+    if (err == cudaSuccess && Q)
+        err = cudaMemcpyAsync(tets_col, tcol4.data(), tcol4.size() * sizeof(int), cudaMemcpyHostToDevice, st);
+    std::vector<unsigned char> hvcol;
+    if (err == cudaSuccess && vcol) {
+        hvcol.resize(N);
+        for (int i = 0; i < N; ++i) hvcol[i] = used[i] == 2 ? 0 : 1;
+        err = cudaMemcpyAsync(vcol, hvcol.data(), (size_t)N, cudaMemcpyHostToDevice, st);
+    }
+    if (err == cudaSuccess && dflist)
+        err = cudaMemcpyAsync(dflist, hfree.data(), hfree.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess && T) err = cudaMemcpyAsync(tris, ht.data(), ht.size() * sizeof(int), cudaMemcpyHostToDevice, st);
     if (err == cudaSuccess && !pts.empty())
         err = cudaMemcpyAsync(dpts, pts.data(), pts.size() * sizeof(int), cudaMemcpyHostToDevice, st);
@@ -316,8 +422,8 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     if (err == cudaSuccess) err = cudaMemsetAsync(d.stats, 0, sizeof(DevStats), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.count, 0, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.dmin_drop, 0xFF, (size_t)(N > 0 ? N : 1) * sizeof(unsigned), st);
-    if (err == cudaSuccess && E) {
-        if (rest_x) launch_rest_lengths(edges_col, (const float4*)rest_x, rest, E, st);
+    if (err == cudaSuccess && (ND || Q)) {
+        if (rest_x) launch_rest_state(d, (const float4*)rest_x, st);
         else c->rest_pending = true;
         err = cudaGetLastError();
     }
@@ -332,7 +438,8 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     return CCFR_OK;
 }
 
-ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
+static ccfr_status create_single(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out,
+                                 const Extras* ex) {
     if (!out) return CCFR_ERR_INVALID_ARG;
     *out = nullptr;
     if (!mesh || check_params(params) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
@@ -361,7 +468,44 @@ ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* 
         if (a < 0 || b < 0 || d < 0 || a >= N || b >= N || d >= N || a == b || b == d || a == d)
             return CCFR_ERR_INVALID_ARG;
     }
-    return create_impl(he, ht, N, params, mesh->rest_x, {}, {}, st, out);
+    return create_impl(he, ht, N, params, mesh->rest_x, {}, {}, st, out, ex);
+}
+
+ccfr_status ccfr_create(const ccfr_mesh* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
+    return create_single(mesh, params, stream, out, nullptr);
+}
+
+ccfr_status ccfr_create_ext(const ccfr_mesh_ext* mesh, const ccfr_params* params, void* stream, ccfr_ctx** out) {
+    if (!out) return CCFR_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!mesh || check_params(params) != CCFR_OK) return CCFR_ERR_INVALID_ARG;
+    const int N = mesh->mesh.n_verts, L = mesh->n_links, Q = mesh->n_tets;
+    if (L < 0 || Q < 0 || L > (1 << 30) || Q > (1 << 28)) return CCFR_ERR_INVALID_ARG;
+    if ((L > 0 && (!mesh->links || !mesh->link_compliance)) || (Q > 0 && !mesh->tets)) return CCFR_ERR_INVALID_ARG;
+    if (!(mesh->volume_compliance >= 0.f)) return CCFR_ERR_INVALID_ARG;
+    Extras ex;
+    ex.links.resize(2 * (size_t)L);
+    ex.link_comp.resize(L);
+    ex.tets.resize(4 * (size_t)Q);
+    ex.vol_comp = mesh->volume_compliance;
+    if (L && (cudaMemcpy(ex.links.data(), mesh->links, ex.links.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess ||
+              cudaMemcpy(ex.link_comp.data(), mesh->link_compliance, (size_t)L * sizeof(float), cudaMemcpyDefault) !=
+                  cudaSuccess))
+        return CCFR_ERR_CUDA;
+    if (Q && cudaMemcpy(ex.tets.data(), mesh->tets, ex.tets.size() * sizeof(int), cudaMemcpyDefault) != cudaSuccess)
+        return CCFR_ERR_CUDA;
+    for (int i = 0; i < L; ++i) {
+        int a = ex.links[2 * i], b = ex.links[2 * i + 1];
+        if (a < 0 || b < 0 || a >= N || b >= N || a == b || !(ex.link_comp[i] >= 0.f)) return CCFR_ERR_INVALID_ARG;
+    }
+    for (int q = 0; q < Q; ++q) {
+        const int* T = &ex.tets[4 * q];
+        for (int j = 0; j < 4; ++j) {
+            if (T[j] < 0 || T[j] >= N) return CCFR_ERR_INVALID_ARG;
+            for (int k = j + 1; k < 4; ++k) if (T[j] == T[k]) return CCFR_ERR_INVALID_ARG;
+        }
+    }
+    return create_single(&mesh->mesh, params, stream, out, &ex);
 }
 
 ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params, int n_scenes, void* stream,
@@ -483,7 +627,7 @@ ccfr_status ccfr_step(ccfr_ctx* c, float* x, float* v, void* stream) {
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (c->rest_pending) {
-        launch_rest_lengths(c->dc.edges_col, (const float4*)x, (float*)c->dc.rest_col, c->dc.n_edges, st);
+        launch_rest_state(c->dc, (const float4*)x, st);
         c->rest_pending = false;
     }
     if (c->prm.flags & CCFR_FLAG_NO_GRAPH) {
@@ -521,7 +665,7 @@ ccfr_status ccfr_step_timed(ccfr_ctx* c, float* x, float* v, double* stage_ms, i
     DeviceGuard g(c->device);
     cudaStream_t st = (cudaStream_t)stream;
     if (c->rest_pending) {
-        launch_rest_lengths(c->dc.edges_col, (const float4*)x, (float*)c->dc.rest_col, c->dc.n_edges, st);
+        launch_rest_state(c->dc, (const float4*)x, st);
         c->rest_pending = false;
     }
     int cap = 16 + c->prm.solver_iters * 16;
@@ -760,6 +904,7 @@ ccfr_status ccfr_get_stats(ccfr_ctx* c, ccfr_stats* out) {
     if (err == cudaSuccess) err = cudaMemcpy(&s, c->dc.stats, sizeof(s), cudaMemcpyDeviceToHost);
     if (err != cudaSuccess) return CCFR_ERR_CUDA;
     out->cand_vf = s.cand[0]; out->cand_ee = s.cand[1]; out->cand_vv = s.cand[2];
+    out->cand_ve = s.cand[PAIR_VE]; out->pairs_ve = s.pairs[PAIR_VE]; out->planes_ve = s.planes_kind[PAIR_VE];
     out->pairs_vf = s.pairs[0]; out->pairs_ee = s.pairs[1]; out->pairs_vv = s.pairs[2];
     out->planes_vf = s.planes_kind[0]; out->planes_ee = s.planes_kind[1]; out->planes_vv = s.planes_kind[2];
     out->planes = s.planes;

@@ -45,10 +45,13 @@ constexpr float NEAR_PARALLEL = 1e-3f;
 // parallel (textbook clamped rule: s = 0, then t, then s again).
 constexpr double PARALLEL_EPS = 1e-12;
 
+// Pair kinds of the counters: 0 vertex-face, 1 edge-edge, 2 point-point,
+// 3 point-edge (isolated points against free edges).
+constexpr int PAIR_VE = 3;
 struct DevStats {
-    u64 cand[3];
-    u64 pairs[3];
-    u64 planes_kind[3];
+    u64 cand[4];
+    u64 pairs[4];
+    u64 planes_kind[4];
     u64 planes;
     u64 overflow_verts;
     u64 violated_verts;
@@ -80,10 +83,25 @@ struct DevCtx {
     const int2* edges;          // canonical order
     const int3* tris;
     const int* pts;             // isolated vertices
-    // XPBD (colour-sorted copies)
+    // XPBD (colour-sorted copies): distance constraints (the edges, then the
+    // extra links) with their rest lengths and compliances / dt^2, then the
+    // tetrahedra with their rest volumes (x 6)
     const int2* edges_col;
     const float* rest_col;
+    const float* alpha_col;
     float* lambda;
+    int n_dist;                 // edges + links
+    int n_tets;
+    const int4* tets_col;
+    float* vol6_col;
+    float* tlambda;
+    float alpha_vol;
+    // collision participation: a vertex of links or tetrahedra only (the
+    // interior of a volume) is no collision query (null: every vertex is);
+    // the free edges (of no triangle), which meet the isolated points
+    const unsigned char* vcollide;
+    const int* free_list;       // null: none
+    int n_free;
     // grid
     int n_items;                // n_tris + 2 n_edges + n_pts + n_verts
     int item_base[N_TABLES];    // first item of each table in the item space

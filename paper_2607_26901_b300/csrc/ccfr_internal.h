@@ -45,9 +45,9 @@ void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned cha
 void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st);
 void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* color_off, int n_colors,
                       unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm = nullptr,
-                      const SideStream* side = nullptr);
+                      const SideStream* side = nullptr, const int* tcolor_off = nullptr, int n_tcolors = 0);
 void launch_update(const DevCtx& c, const float4* x, float4* v, cudaStream_t st);
-void launch_rest_lengths(const int2* edges_col, const float4* x, float* rest, int ne, cudaStream_t st);
+void launch_rest_state(const DevCtx& c, const float4* x, cudaStream_t st);
 void launch_load_regions(const DevCtx& c, const float4* planes, const int* count, int cap, cudaStream_t st);
 void launch_dmin_export(const DevCtx& c, float* out, cudaStream_t st);
 

@@ -481,6 +481,38 @@ __device__ int narrow_pp(const DevCtx& c, int p, int q, float4 P, float4 Q) {
     return (int)op + (int)oq;
 }
 
+// Point-edge pair: isolated point p against free edge e = (a, b), a pair kind
+// that Alg. 3 lacks (a particle meets a wire through no vertex-face or
+// edge-edge pair).  Local coordinates centred at p; the closest point of the
+// segment by the clamped parameter t = -a.(b - a) / |b - a|^2, and the plane of
+// Alg. 3 with the segment point's inverse mass (1 - t) w_a + t w_b.
+__device__ int narrow_pe(const DevCtx& c, int p, float4 P, int e, int2 E, float4 A, float4 B) {
+    const SceneParams sp = scene_params(c, scene_of(c, p));
+    const f3 o = xyz(P);
+    const f3 a = sub(xyz(A), o), ab = sub(xyz(B), xyz(A));
+    const float l2 = dot(ab, ab);
+    const float t = l2 > 0.f ? fminf(fmaxf(-dot(a, ab) / l2, 0.f), 1.f) : 0.f;
+    const f3 q = axpy(t, ab, a);
+    const f3 diff = mk(-q.x, -q.y, -q.z);
+    const float dist = len(diff);
+    if (dist == 0.f) return 0;
+    const float phi = dist - sp.xi;
+    if (!(phi < sp.two_r)) return 0;
+    const float wf = (1.f - t) * A.w + t * B.w;
+    const float W = P.w + wf;
+    if (W == 0.f) return 0;
+    const f3 n = mk(diff.x / dist, diff.y / dist, diff.z / dist);
+    const f3 mn = mk(-n.x, -n.y, -n.z);
+    const u64 key = pair_key(PAIR_VE, p, e);
+    const bool op = P.w > 0.f, oa = A.w > 0.f, ob = B.w > 0.f;
+    const unsigned sp_ = reserve_slot(c, p, op), sa = reserve_slot(c, E.x, oa), sb = reserve_slot(c, E.y, ob);
+    const float df = (wf / W) * phi;
+    store_plane(c, p, op, sp_, n, (P.w / W) * phi, phi, key);
+    store_plane(c, E.x, oa, sa, mn, df, phi, key);
+    store_plane(c, E.y, ob, sb, mn, df, phi, key);
+    return (int)op + (int)oa + (int)ob;
+}
+
 // ------------------------------------------------------ neighbourhood scan
 //
 // Work is organised by grid cell.  A work unit is a run of up to 32 query
@@ -531,12 +563,24 @@ __global__ void k_make_units(DevCtx c) {
 
 struct EmitCounters { u64 cand, acc, planes, fp64; };
 
-// Narrow phase of one queued pair (a = query id, b = item id).
-template <int QK, int MODE>
+// Narrow phase of one queued pair (a = query id, b = item id).  VE: (isolated
+// point, free edge) pairs.
+template <int QK, int MODE, bool VE = false>
 __device__ __forceinline__ void process_pair(const DevCtx& c, const float4* __restrict__ x, const PairOut& po,
                                              int2 pr, EmitCounters& k) {
-    if (QK == KIND_TRI) {                          // (triangle, vertex)
+    if (VE) {                                      // (point, edge)
+        const int p = pr.x, e = pr.y;
+        const int2 E = c.edges[e];
+        const float4 P = x[p], A = x[E.x], B = x[E.y];
+        if (!(P.w > 0.f || A.w > 0.f || B.w > 0.f)) return;
+        ++k.cand;
+        if (MODE == MODE_PAIRS) return;
+        const int np = narrow_pe(c, p, P, e, E, A, B);
+        k.acc += (np > 0);
+        k.planes += np;
+    } else if (QK == KIND_TRI) {                   // (triangle, vertex)
         int t = pr.x, v = pr.y;
+        if (c.vcollide && !c.vcollide[v]) return;   // the interior of a volume: no collision query
         int3 T = c.tris[t];
         float4 P = x[v], A = x[T.x], B = x[T.y], C = x[T.z];
         if (!(P.w > 0.f || A.w > 0.f || B.w > 0.f || C.w > 0.f)) return;
@@ -745,7 +789,11 @@ __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __re
     return scene;
 }
 
-template <int QK, int MODE>
+// VE (QK = KIND_EDGE): every free edge against the isolated points of the
+// point-table cells its box reaches (pairs (point, edge)); one warp per free
+// edge, as for the oversized primitives, so that no point scans the far more
+// numerous edges of triangles.
+template <int QK, int MODE, bool VE = false>
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po) {
     if (c.flags[1]) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
@@ -754,7 +802,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     int qn = 0;
     EmitCounters k{0, 0, 0, 0};
     const int IK = (QK == KIND_TRI) ? KIND_VQ : KIND_EDGE;
-    const unsigned nbig = c.big_count[QK];
+    const unsigned nbig = VE ? (unsigned)c.n_free : c.big_count[QK];
     u64 big_cells = 0, big_scans = 0, big_items = 0, bige_items = 0;   // diagnostics
     const unsigned stride = gridDim.x * EMIT_WARPS;
     // append a hit to the warp queue; process 32 queued pairs at a time
@@ -765,7 +813,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         qn += __popc(hb);
         if (qn >= 32) {
             __syncwarp();
-            process_pair<QK, MODE>(c, x, po, q[lane], k);
+            process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
             int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
             __syncwarp();
             if (lane < qn - 32) q[lane] = rest;
@@ -774,7 +822,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         }
     };
     for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nbig; u += stride) {
-        const int o = c.big[c.big_base[QK] + u];
+        const int o = VE ? c.free_list[u] : c.big[c.big_base[QK] + u];
         float lo[3], hi[3];
         bool qimm;
         const unsigned qs = prim_box(c, x, QK, o, lo, hi, qimm);
@@ -842,6 +890,13 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             return pack_scene(__float_as_uint(i1.w)) == qs && lo[0] <= i1.x && i0.x <= hi[0] && lo[1] <= i1.y &&
                    i0.y <= hi[1] && lo[2] <= i1.z && i0.z <= hi[2];
         };
+        if (VE) {
+            u64 pt_items = 0;
+            scan_cells(KIND_PT, [&](float4 i0, float4 i1) -> int2 {
+                return overlaps(i0, i1) ? make_int2(__float_as_int(i0.w), o) : make_int2(-1, -1);
+            }, pt_items);
+            continue;
+        }
         // the fitting primitives of the item table
         scan_cells(IK, [&](float4 i0, float4 i1) -> int2 {
             const int iid = __float_as_int(i0.w);
@@ -925,10 +980,12 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         }
     }
     __syncwarp();
-    if (lane < qn) process_pair<QK, MODE>(c, x, po, q[lane], k);
-    warp_add_u64(&c.stats->cand[QK], k.cand);
-    warp_add_u64(&c.stats->pairs[QK], k.acc);
-    warp_add_u64(&c.stats->planes_kind[QK], k.planes);
+    if (lane < qn) process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
+    constexpr int SK = VE ? PAIR_VE : QK;
+    warp_add_u64(&c.stats->cand[SK], k.cand);
+    warp_add_u64(&c.stats->pairs[SK], k.acc);
+    warp_add_u64(&c.stats->planes_kind[SK], k.planes);
+    if (VE) return;
     if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
     warp_add_u64(&c.stats->aux[10], big_cells);
     warp_add_u64(&c.stats->aux[11], big_scans);
@@ -2184,7 +2241,7 @@ __global__ void k_xpbd_color(DevCtx c, int e0, int e1) {
     if (i >= e1) return;
     int2 e = c.edges_col[i];
     float4 A = c.x_s[e.x], B = c.x_s[e.y];
-    float at = c.p.alpha_tilde;
+    float at = c.alpha_col[i];
     float wsum = A.w + B.w + at;
     if (wsum == 0.f) return;
     f3 d = sub(xyz(A), xyz(B));
@@ -2197,6 +2254,31 @@ __global__ void k_xpbd_color(DevCtx c, int e0, int e1) {
     c.x_s[e.x] = make_float4(A.x + sa * nd.x, A.y + sa * nd.y, A.z + sa * nd.z, A.w);
     c.x_s[e.y] = make_float4(B.x - sb * nd.x, B.y - sb * nd.y, B.z - sb * nd.z, B.w);
     c.lambda[i] = lam + dl;
+}
+
+// One colour of the volume constraints: C = 6 V - 6 V0 per tetrahedron with
+// 6 V = (x1 - x0) . ((x2 - x0) x (x3 - x0)), whose gradients are the three
+// cross products and minus their sum; XPBD update with compliance alpha_vol.
+__global__ void k_xpbd_tet_color(DevCtx c, int q0, int q1) {
+    if (c.flags[1]) return;
+    int i = q0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= q1) return;
+    const int4 T = c.tets_col[i];
+    const float4 X0 = c.x_s[T.x], X1 = c.x_s[T.y], X2 = c.x_s[T.z], X3 = c.x_s[T.w];
+    const f3 e1 = sub(xyz(X1), xyz(X0)), e2 = sub(xyz(X2), xyz(X0)), e3 = sub(xyz(X3), xyz(X0));
+    const f3 g1 = cross(e2, e3), g2 = cross(e3, e1), g3 = cross(e1, e2);
+    const f3 g0 = mk(-(g1.x + g2.x + g3.x), -(g1.y + g2.y + g3.y), -(g1.z + g2.z + g3.z));
+    const float C = dot(e1, g1) - c.vol6_col[i];
+    const float at = c.alpha_vol;
+    const float den = at + X0.w * dot(g0, g0) + X1.w * dot(g1, g1) + X2.w * dot(g2, g2) + X3.w * dot(g3, g3);
+    if (den == 0.f) return;
+    const float lam = c.tlambda[i];
+    const float dl = (-C - at * lam) / den;
+    c.x_s[T.x] = make_float4(X0.x + X0.w * dl * g0.x, X0.y + X0.w * dl * g0.y, X0.z + X0.w * dl * g0.z, X0.w);
+    c.x_s[T.y] = make_float4(X1.x + X1.w * dl * g1.x, X1.y + X1.w * dl * g1.y, X1.z + X1.w * dl * g1.z, X1.w);
+    c.x_s[T.z] = make_float4(X2.x + X2.w * dl * g2.x, X2.y + X2.w * dl * g2.y, X2.z + X2.w * dl * g2.z, X2.w);
+    c.x_s[T.w] = make_float4(X3.x + X3.w * dl * g3.x, X3.y + X3.w * dl * g3.y, X3.z + X3.w * dl * g3.z, X3.w);
+    c.tlambda[i] = lam + dl;
 }
 
 // End of an iteration: count it, and with early exit stop once converged.
@@ -2221,6 +2303,14 @@ __global__ void k_rest_lengths(const int2* edges_col, const float4* __restrict__
     if (i >= ne) return;
     int2 e = edges_col[i];
     rest[i] = len(sub(xyz(x[e.x]), xyz(x[e.y])));
+}
+
+__global__ void k_tet_vol6(const int4* tets_col, const float4* __restrict__ x, float* vol6, int nt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const int4 T = tets_col[i];
+    const f3 a = xyz(x[T.x]);
+    vol6[i] = dot(sub(xyz(x[T.y]), a), cross(sub(xyz(x[T.z]), a), sub(xyz(x[T.w]), a)));
 }
 
 __global__ void k_load_regions(DevCtx c, const float4* planes, const int* count, int cap) {
@@ -2295,6 +2385,7 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
         if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE_BIG, st);
         if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
+        if (c.n_pts > 0 && c.n_free > 0) k_emit_big<KIND_EDGE, MODE_PLANES, true><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_PP, st);
         if (fork) {
             cudaEventRecord(side->join, sb);
@@ -2351,19 +2442,24 @@ void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned cha
 }
 
 void launch_predict(const DevCtx& c, const float4* x, const float4* v, cudaStream_t st) {
-    cudaMemsetAsync(c.lambda, 0, (size_t)(c.n_edges > 0 ? c.n_edges : 1) * sizeof(float), st);
+    cudaMemsetAsync(c.lambda, 0, (size_t)(c.n_dist > 0 ? c.n_dist : 1) * sizeof(float), st);
+    if (c.n_tets > 0) cudaMemsetAsync(c.tlambda, 0, (size_t)c.n_tets * sizeof(float), st);
     cudaMemsetAsync(c.flags, 0, 2 * sizeof(int), st);
     if (c.n_verts > 0) k_predict<<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, v);
 }
 
 void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* color_off, int n_colors,
                       unsigned* tile_sums, int n_buckets_total, int early_exit, StageTimer* tm,
-                      const SideStream* side) {
+                      const SideStream* side, const int* tcolor_off, int n_tcolors) {
     if (c.n_verts > 0) k_iter_begin<<<nblk(c.n_verts, 256), 256, 0, st>>>(c);
     launch_build(c, x, st, MODE_PLANES, nullptr, tile_sums, n_buckets_total, tm, side);
     for (int k = 0; k < n_colors; ++k) {
         int e0 = color_off[k], e1 = color_off[k + 1];
         if (e1 > e0) k_xpbd_color<<<nblk(e1 - e0, 256), 256, 0, st>>>(c, e0, e1);
+    }
+    for (int k = 0; k < n_tcolors; ++k) {
+        int q0 = tcolor_off[k], q1 = tcolor_off[k + 1];
+        if (q1 > q0) k_xpbd_tet_color<<<nblk(q1 - q0, 256), 256, 0, st>>>(c, q0, q1);
     }
     if (tm) tm->mark(ST_XPBD, st);
     if (c.p.delta > 0.f && c.phi && c.n_verts > 0)
@@ -2385,8 +2481,9 @@ void launch_update(const DevCtx& c, const float4* x, float4* v, cudaStream_t st)
     else k_update<<<1, 32, 0, st>>>(c, x, v);
 }
 
-void launch_rest_lengths(const int2* edges_col, const float4* x, float* rest, int ne, cudaStream_t st) {
-    if (ne > 0) k_rest_lengths<<<nblk(ne, 256), 256, 0, st>>>(edges_col, x, rest, ne);
+void launch_rest_state(const DevCtx& c, const float4* x, cudaStream_t st) {
+    if (c.n_dist > 0) k_rest_lengths<<<nblk(c.n_dist, 256), 256, 0, st>>>(c.edges_col, x, (float*)c.rest_col, c.n_dist);
+    if (c.n_tets > 0) k_tet_vol6<<<nblk(c.n_tets, 256), 256, 0, st>>>(c.tets_col, x, c.vol6_col, c.n_tets);
 }
 
 void launch_load_regions(const DevCtx& c, const float4* planes, const int* count, int cap, cudaStream_t st) {

@@ -393,7 +393,7 @@ def _hinge_links(tris: np.ndarray) -> np.ndarray:
 
 
 def codimensional(rod_seg: int = 16, cube_n: int = 3, particle_layers: int = 1, seed: int = 6,
-                  iters: int = 10, steps: int = 20, plane_capacity: int = 128, speed: float = 0.5,
+                  iters: int = 10, steps: int = 20, plane_capacity: int = 768, speed: float = 0.5,
                   cloth_bending: float = 1.0, rod_bending: float = 0.1, volume_compliance: float = 0.0) -> Scene:
     """Rods, soft volumes, a cloth and particles in one simulation (a synthetic
     stand-in for the paper's coupled codimensional scene, Sec. 5).

@@ -1,0 +1,175 @@
+"""GPU parity of mixed scenes (rods, soft volumes, cloth and particles in one
+simulation; readings X1-X5): the library's regions, candidate counts and
+substeps against the FP64 oracle, through ccfr_create_ext.
+
+- regions: per-vertex plane counts and pair keys identical, plane values
+  within 1e-5 L, outside the oracle's decision bands; the four candidate
+  counts (vertex-face, edge-edge, point-point, point-edge) identical;
+- the oversized rod edges reach the points through the oversized pass;
+- one full substep (XPBD with links and volumes, projection) within 1e-5 L;
+- several substeps of the mixed scene keep every edge off every triangle and
+  every particle at least xi from every rod.
+"""
+import numpy as np
+import pytest
+
+from paper_2607_26901_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26901_b300 import ccfr  # noqa: E402
+from tests.helpers import dev_scene, gpu_regions_by_vertex  # noqa: E402
+
+TOL_REL = 1e-5
+BAND_REL = 1e-7
+
+SCENES = {
+    "rod": lambda: S.particles_on_rod(),
+    "rod_oversized": lambda: S.particles_on_rod(cloth_patch=True),
+    "codimensional": lambda: S.codimensional(rod_seg=16, cube_n=3),
+}
+
+
+def extra_of(orc, sc):
+    return orc.Extra(sc.x[:, :3].astype(np.float64), sc.links, sc.link_compliance, sc.tets, sc.volume_compliance)
+
+
+def capacity(orc, sc, ex):
+    R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris,
+                          orc.make_params(sc.params, capacity=0), extra=ex)
+    k = int(np.diff(R["offs"]).max() * 1.5) + 8
+    return max(32, (k + 31) // 32 * 32)
+
+
+@pytest.mark.parametrize("name", list(SCENES))
+def test_mixed_regions_and_candidate_counts(orc, name):
+    sc = SCENES[name]()
+    ex = extra_of(orc, sc)
+    L = orc.scene_scale(sc.x)
+    K = capacity(orc, sc, ex)
+    x, v = dev_scene(sc)
+    ctx = ccfr.Context.from_scene(sc, flags=ccfr.FLAG_STORE_KEYS, plane_capacity=K)
+    ctx.reset_stats()
+    ctx.build_regions(x)
+    st = ctx.stats()
+    reg = ctx.regions(keys=True)
+    g = gpu_regions_by_vertex(reg)
+    gcount = reg["count"].cpu().numpy()
+    P = orc.make_params(sc.params, band=BAND_REL * L, capacity=K)
+    R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, P, extra=ex)
+    cand = [st["cand_vf"], st["cand_ee"], st["cand_vv"], st["cand_ve"]]
+    np.testing.assert_array_equal(cand, R["cand"])
+    if name.startswith("rod"):
+        assert R["cand"][3] > 0 and st["pairs_ve"] == R["acc"][3]
+    if name == "rod_oversized":
+        assert st["aux"][4] > 0          # the rod's segments were oversized edges
+    offs = R["offs"]
+    band = (R["vflag"] & 2) != 0
+    r2 = 2.0 * sc.params["r"]
+    checked = 0
+    for vtx in range(sc.n_verts):
+        if band[vtx]:
+            continue
+        n_ref = offs[vtx + 1] - offs[vtx]
+        assert gcount[vtx] == n_ref, (vtx, gcount[vtx], n_ref)
+        if n_ref == 0:
+            continue
+        gp, gk = g[vtx]
+        rp = R["planes"][offs[vtx]:offs[vtx + 1]]
+        rk = R["key"][offs[vtx]:offs[vtx + 1]]
+        og, orr = np.argsort(gk, kind="stable"), np.argsort(rk, kind="stable")
+        np.testing.assert_array_equal(gk[og], rk[orr])
+        e = np.abs(gp[og, :3] - rp[orr, :3]).max(axis=1) * r2 + np.abs(gp[og, 3] - rp[orr, 3])
+        assert e.max() <= TOL_REL * L, (vtx, float(e.max()))
+        checked += 1
+    assert checked > 0 and band.mean() < 0.05
+    ctx.close()
+
+
+def parts_of(sc):
+    """Vertex role: rod, particle, volume interior (links and tetrahedra only),
+    or a triangle vertex (cloth or volume surface)."""
+    n = sc.n_verts
+    in_tris = np.zeros(n, bool)
+    in_tris[sc.tris.ravel()] = True
+    in_edges = np.zeros(n, bool)
+    in_edges[sc.edges.ravel()] = True
+    in_cons = np.zeros(n, bool)
+    in_cons[sc.links.ravel()] = True
+    in_cons[sc.tets.ravel()] = True
+    return {"rod": in_edges & ~in_tris, "particle": ~in_edges & ~in_cons & ~in_tris,
+            "interior": in_cons & ~in_edges & ~in_tris, "surface": in_tris}
+
+
+def substep_error(orc, sc, iters):
+    ex = extra_of(orc, sc)
+    L = orc.scene_scale(sc.x)
+    K = capacity(orc, sc, ex)
+    P = orc.make_params(sc.params, band=BAND_REL * L, capacity=K, iters=iters)
+    x3 = sc.x[:, :3].astype(np.float64)
+    xo, vo, info, vband = orc.step(x3, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris,
+                                   orc.rest_lengths(x3, sc.edges), P, extra=ex)
+    x, v = dev_scene(sc)
+    ctx = ccfr.Context.from_scene(sc, plane_capacity=K, iters=iters)
+    ctx.step(x, v)
+    st = ctx.stats()
+    ctx.close()
+    assert st["status"] == 0 and st["iterations"] == iters
+    got = x.cpu().numpy()[:, :3].astype(np.float64)
+    ok = vband == 0
+    assert ok.mean() > 0.5
+    return np.abs(got - xo).max(axis=1) / L, ok
+
+
+@pytest.mark.parametrize("name", ["rod", "rod_oversized"])
+def test_rod_scenes_full_substep(orc, name):
+    sc = SCENES[name]()
+    err, ok = substep_error(orc, sc, sc.params["iters"])
+    assert err[ok].max() <= TOL_REL
+
+
+def test_mixed_scene_substeps(orc):
+    """Two iterations: every vertex outside the bands within the bar.  Ten
+    iterations (the full substep): the self-colliding volume surfaces and the
+    cloth go through many halts, and a halt taken differently in binary32 and
+    FP64 moves that vertex by up to the step bound (as in the cloth stack's
+    full-substep case); the rods, particles and volume interiors, driven by the
+    links, the point-edge pairs and the volume constraints, stay within the bar
+    everywhere, and the median stays at the rounding level."""
+    sc = SCENES["codimensional"]()
+    err, ok = substep_error(orc, sc, 2)
+    assert err[ok].max() <= TOL_REL
+    err, ok = substep_error(orc, sc, sc.params["iters"])
+    parts = parts_of(sc)
+    for name in ("rod", "particle", "interior"):
+        m = parts[name] & ok
+        assert m.sum() > 0 and err[m].max() <= TOL_REL, name
+    assert np.mean(err[ok] <= TOL_REL) >= 0.97 and np.median(err[ok]) <= 1e-7
+
+
+def test_mixed_scene_stays_free_of_intersections(orc):
+    sc = S.codimensional(rod_seg=16, cube_n=3)
+    x, v = dev_scene(sc)
+    ctx = ccfr.Context.from_scene(sc)
+    in_tris = set(sc.tris.ravel().tolist())
+    free = np.array([e for e in sc.edges.tolist() if e[0] not in in_tris and e[1] not in in_tris])   # the rods
+    iso = np.setdiff1d(np.arange(sc.n_verts), np.unique(np.concatenate([sc.edges.ravel(), sc.links.ravel(),
+                                                                           sc.tets.ravel()])))       # the particles
+    assert len(free) > 0 and len(iso) > 0
+    xi = sc.params["xi"]
+    for _ in range(12):
+        ctx.step(x, v)
+        p = x.cpu().numpy()[:, :3].astype(np.float64)
+        assert orc.count_edge_triangle_intersections(p, sc.edges, sc.tris) == 0
+        a, b = p[free[:, 0]], p[free[:, 1]]
+        for q in iso:
+            t = np.clip(np.einsum("ij,ij->i", p[q] - a, b - a) / np.einsum("ij,ij->i", b - a, b - a), 0, 1)
+            d = np.linalg.norm(p[q] - (a + t[:, None] * (b - a)), axis=1).min()
+            assert d >= xi * (1 - 1e-5), (q, d)
+    st = ctx.stats()
+    ctx.close()
+    assert st["status"] == 0 and st["cand_ve"] > 0
