@@ -1,8 +1,9 @@
 /*
  * ccfr.h - C ABI of the B300 (sm_103a) implementation of Convex Collision-Free
  * Regions (CCFR): per-vertex convex regions built from nearby vertex-face,
- * edge-edge and point-point pairs, projection of XPBD iterates into them, and
- * the XPBD substep that runs both inside every solver iteration.
+ * edge-edge and point-point pairs (and point-edge pairs in mixed scenes, see
+ * ccfr_mesh_ext), projection of XPBD iterates into them, and the XPBD substep
+ * that runs both inside every solver iteration.
  *
  * Conventions shared by every call
  * --------------------------------
