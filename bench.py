@@ -137,21 +137,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2):
-    """Bounded CPU sample of the stack workload run by the FP64 oracle:
-    4 layers of n_side^2 vertices, one substep of `iters` iterations."""
+def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str = "cloth_stack"):
+    """Bounded CPU sample of the workload run by the FP64 oracle, one substep
+    of `iters` iterations: the stack recipe at 4 layers of n_side^2 vertices
+    (every stack variant), the mixed codimensional recipe at 96 rod segments,
+    or the wires recipe at 64x64 strands of 32 segments."""
     from oracle import oracle as O
-    sc = S.cloth_stack(n_side=n_side, seed=seed)
+    ex = None
+    if workload == "codimensional":
+        sc = S.codimensional(rod_seg=96, cube_n=3, seed=6)
+        x0 = sc.x[:, :3].astype(np.float64)
+        ex = O.Extra(x0, sc.links, sc.link_compliance, sc.tets, sc.volume_compliance)
+        what = f"codimensional recipe at 96 rod segments, 3^3 cubes ({sc.n_verts} verts)"
+    elif workload.startswith("wires"):
+        sc = S.wires(n_grid=64, n_seg=32, seed=3)
+        what = f"wires recipe at 64x64 strands of 32 segments ({sc.n_verts} verts)"
+    else:
+        sc = S.cloth_stack(n_side=n_side, seed=seed)
+        what = f"cloth stack recipe at 4 layers x {n_side}x{n_side} ({sc.n_verts} verts)"
     P = O.make_params(sc.params, iters=iters)
     x = sc.x[:, :3].astype(np.float64)
     v = sc.v[:, :3].astype(np.float64)
     rest = O.rest_lengths(x, sc.edges)
     t0 = time.perf_counter()
-    O.step(x, v, sc.x, sc.edges, sc.tris, rest, P)
+    O.step(x, v, sc.x, sc.edges, sc.tris, rest, P, extra=ex)
     dt = time.perf_counter() - t0
     units = sc.n_movable * iters
-    return units / dt, dt, f"cloth stack recipe at 4 layers x {n_side}x{n_side} ({sc.n_verts} verts), " \
-                           f"1 substep x {iters} iterations, seed {seed}"
+    return units / dt, dt, f"{what}, 1 substep x {iters} iterations"
 
 
 def max_over_ranks(v: float, dist=None, device=None) -> float:
@@ -338,7 +350,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        val, secs, sample = oracle_sample()
+        val, secs, sample = oracle_sample(workload=args.workload)
         cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                "seconds": round(secs, 2)}
 
@@ -614,7 +626,7 @@ def run_reference(args, ws, rank, desc):
     vals = []
     sample = None
     for i in range(args.warmup + args.steps):
-        val, secs, sample = oracle_sample(iters=1, n_side=48)
+        val, secs, sample = oracle_sample(iters=1, n_side=48, workload=args.workload)
         if i >= args.warmup:
             vals.append((val, secs))
     total_units = sum(v * s for v, s in vals)
