@@ -12,7 +12,8 @@ appended to that file.
 Cases: the 1,024-vertex cloth over the sphere (full substep, 10 iterations);
 the cloth stack and the wires at sizes the oracle steps in seconds (full
 substeps) and at full size (oracle projection of sampled vertices on the
-GPU's own planes); a batch of uneven scenes (each scene's full substep).
+GPU's own planes); the mixed codimensional scene (full substep); a batch of
+uneven scenes (each scene's full substep).
 """
 import json
 import os
@@ -51,9 +52,16 @@ def report(case, err_rel, n_cmp, n_band, extra=None):
     return line
 
 
+def extra_of(orc, sc):
+    """Links and tetrahedra of a mixed scene (None for the others)."""
+    if not (len(sc.links) or len(sc.tets)):
+        return None
+    return orc.Extra(sc.x[:, :3].astype(np.float64), sc.links, sc.link_compliance, sc.tets, sc.volume_compliance)
+
+
 def oracle_capacity(orc, sc, margin=1.5):
     P = orc.make_params(sc.params, capacity=1 << 20)
-    R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, P)
+    R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, P, extra=extra_of(orc, sc))
     k = int(np.diff(R["offs"]).max() * margin) + 8
     return max(32, (k + 31) // 32 * 32)          # the library takes multiples of 32
 
@@ -65,7 +73,8 @@ def full_step_error(orc, sc, case, iters=None):
     P = orc.make_params(sc.params, band=BAND_REL * L, iters=iters, capacity=K)
     x3 = sc.x[:, :3].astype(np.float64)
     rest = orc.rest_lengths(x3, sc.edges)
-    xo, vo, info, vband = orc.step(x3, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, rest, P)
+    xo, vo, info, vband = orc.step(x3, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, rest, P,
+                                   extra=extra_of(orc, sc))
     x, v = dev_scene(sc)
     ctx = ccfr.Context.from_scene(sc, plane_capacity=K, iters=iters)
     ctx.step(x, v)
@@ -105,6 +114,15 @@ def test_precision_small_wires(orc):
     sc = S.wires(n_grid=6, n_seg=32, seed=3)
     line = full_step_error(orc, sc, "wires 6x6x32, full substep")
     assert line["max_err_rel"] <= TOL_REL
+
+
+def test_precision_mixed_scene(orc):
+    """Rods, soft volumes, cloth and particles (829 verts), full substep: the
+    self-colliding volume surfaces and cloth are chaotic over ten iterations
+    like the stack (see tests/test_gpu_mixed.py for the per-part bars)."""
+    sc = S.codimensional(rod_seg=16, cube_n=3)
+    line = full_step_error(orc, sc, "codimensional 829 verts (rods, volumes, cloth, particles), full substep")
+    assert line["frac_within"] >= 0.97 and line["median_err_rel"] <= 1e-7
 
 
 def test_precision_batch(orc):
