@@ -52,3 +52,14 @@ def test_host_checks_reject_bad_arguments_without_gpu():
     assert lib.ccfr_create(C.byref(m), C.byref(p), None, C.byref(h)) == 1
     assert lib.ccfr_destroy(None) == 1
     assert lib.ccfr_step(None, None, None, None) == 1
+    # mixed scenes: the extension is checked before any copy to or from the device
+    p.plane_capacity = 64
+    assert lib.ccfr_create_ext(None, C.byref(p), None, C.byref(h)) == 1
+    me = ccfr.MeshExt(m, -1, None, None, 0, None, 0.0)          # negative link count
+    assert lib.ccfr_create_ext(C.byref(me), C.byref(p), None, C.byref(h)) == 1
+    me = ccfr.MeshExt(m, 2, None, None, 0, None, 0.0)           # links announced, none given
+    assert lib.ccfr_create_ext(C.byref(me), C.byref(p), None, C.byref(h)) == 1
+    me = ccfr.MeshExt(m, 0, None, None, 3, None, 0.0)           # tetrahedra announced, none given
+    assert lib.ccfr_create_ext(C.byref(me), C.byref(p), None, C.byref(h)) == 1
+    me = ccfr.MeshExt(m, 0, None, None, 0, None, -1.0)          # negative volume compliance
+    assert lib.ccfr_create_ext(C.byref(me), C.byref(p), None, C.byref(h)) == 1
