@@ -166,6 +166,40 @@ def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str
     return units / dt, dt, f"{what}, 1 substep x {iters} iterations"
 
 
+def has_free_edges(sc) -> bool:
+    """Whether some edge belongs to no triangle (a rod): the point-edge
+    kernel is launched only then."""
+    if len(sc.edges) == 0:
+        return False
+    if len(sc.tris) == 0:
+        return True
+    t = np.asarray(sc.tris, np.int64)
+    te = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]], 0), axis=1)
+    m = int(max(te.max(), np.asarray(sc.edges).max())) + 1
+    return not np.isin(sc.edges[:, 0].astype(np.int64) * m + sc.edges[:, 1], te[:, 0] * m + te[:, 1]).all()
+
+
+def tet_colour_count(sc) -> int:
+    """Colours of the tetrahedra under the library's documented rule (greedy
+    first-fit in tetrahedron order), i.e. its volume-constraint launches per
+    iteration."""
+    tets = np.asarray(getattr(sc, "tets", np.zeros((0, 4))), np.int64)
+    if len(tets) == 0:
+        return 0
+    used = [0] * sc.n_verts
+    ncol = 0
+    for a, b, c, d in tets.tolist():
+        m = used[a] | used[b] | used[c] | used[d]
+        k = (~m & (m + 1)).bit_length() - 1
+        bit = 1 << k
+        used[a] |= bit
+        used[b] |= bit
+        used[c] |= bit
+        used[d] |= bit
+        ncol = max(ncol, k + 1)
+    return ncol
+
+
 def max_over_ranks(v: float, dist=None, device=None) -> float:
     """Largest value over the ranks (the job's time is its slowest rank)."""
     if dist is None:
@@ -285,7 +319,7 @@ def main():
     planes_ee = st["planes_ee"] / per_iter
     planes_vv = st["planes_vv"] / per_iter
     planes_stored = st["planes"] / per_iter
-    n_pts = len(S.isolated_points(sc.x, sc.edges))
+    n_pts = len(S.isolated_points(sc.x, sc.edges, sc.links, sc.tets))
     # algorithmic bytes per launch (one launch per iteration), per kernel
     n_s = st["aux"][8] / per_iter                  # violated vertices with short plane lists
     planes_s = st["aux"][9] / per_iter             # their planes
@@ -344,8 +378,11 @@ def main():
                "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": 2 * N * 16}
 
     n_emit = (2 if T > 0 else 0) + (2 if E > 0 else 0) + (1 if n_pts > 1 else 0)
-    # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours, 3 project, iter_end
-    launches_per_iter = 1 + 1 + 1 + 3 + 1 + 1 + n_emit + ctx.n_colors + 3 + 1  # noqa: E501
+    if n_pts > 0 and has_free_edges(sc):
+        n_emit += 1                                   # point-edge pairs (one warp per free edge)
+    # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours of the
+    # distance constraints and of the tetrahedra, 3 project, iter_end
+    launches_per_iter = 1 + 1 + 1 + 3 + 1 + 1 + n_emit + ctx.n_colors + tet_colour_count(sc) + 3 + 1
     gpu_launches = args.steps * (2 + iters * launches_per_iter)
 
     cpu = None

@@ -684,9 +684,11 @@ def triangle_soup(n_tris: int = 60, box: float = 0.05, size: float = 0.01, seed:
     return _assemble("triangle_soup", parts_p, parts_w, parts_t, parts_e, params)
 
 
-def isolated_points(x: np.ndarray, edges: np.ndarray) -> np.ndarray:
-    """Indices of vertices that belong to no edge (the point primitives)."""
+def isolated_points(x: np.ndarray, edges: np.ndarray, links=None, tets=None) -> np.ndarray:
+    """Indices of vertices that belong to no edge, link or tetrahedron (the
+    point primitives)."""
     used = np.zeros(len(x), bool)
-    if len(edges):
-        used[edges.ravel()] = True
+    for a in (edges, links, tets):
+        if a is not None and len(a):
+            used[np.asarray(a).ravel()] = True
     return np.nonzero(~used)[0].astype(np.int32)
