@@ -166,6 +166,35 @@ def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str
     return units / dt, dt, f"{what}, 1 substep x {iters} iterations"
 
 
+# Informational binary32 operation counts per unit of work: a vertex-face
+# candidate (closest point on a triangle, normal, gap, shares), an edge-edge
+# candidate (segment closest points, normal, gap, shares) and a violated plane
+# visited by the projection (Alg. 1 step or retraction).
+FLOPS_PER_VF, FLOPS_PER_EE, FLOPS_PER_VIOLATED_PLANE = 120.0, 150.0, 60.0
+
+
+def fp32_report(stage: dict, st: dict, per_iter: float, iters: float, clocks) -> dict:
+    """Achieved binary32 TFLOP/s of the vertex-face and edge-edge emission and
+    of the projection (the counts above over their stage times), against a
+    peak of SMs x 128 FP32 lanes x 2 flops x the sampled maximum SM clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2032.0
+    peak = n_sm * 128 * 2 * mhz * 1e6 / 1e12
+    work = {"emit_vf": (FLOPS_PER_VF * st["cand_vf"] / per_iter, ("emit_vf", "emit_vf_big")),
+            "emit_ee": (FLOPS_PER_EE * st["cand_ee"] / per_iter, ("emit_ee", "emit_ee_big")),
+            "project": (FLOPS_PER_VIOLATED_PLANE * st["aux"][2] / per_iter,
+                        ("project", "project_heavy", "project_short"))}
+    out = {"peak_tflops": round(peak, 1), "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+           "flops_per_unit": {"vf_candidate": FLOPS_PER_VF, "ee_candidate": FLOPS_PER_EE,
+                              "violated_plane": FLOPS_PER_VIOLATED_PLANE}}
+    for name, (flops, stages) in work.items():
+        ms = sum(stage.get(k, 0.0) for k in stages) / max(iters, 1)
+        tf = flops / (ms / 1e3) / 1e12 if ms > 0 else 0.0
+        out[name] = {"tflops": round(tf, 3), "frac": round(tf / peak, 4)}
+    return out
+
+
 def has_free_edges(sc) -> bool:
     """Whether some edge belongs to no triangle (a rod): the point-edge
     kernel is launched only then."""
@@ -406,6 +435,7 @@ def main():
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "fp32": fp32_report(stage, st, per_iter, iters_timed, clocks),
             "stage_ms_per_step": {k: round(v_, 4) for k, v_ in stage.items()},
             "stats_per_iter": {"cand_vf": st["cand_vf"] / per_iter, "cand_ee": st["cand_ee"] / per_iter,
                                "pairs_vf": st["pairs_vf"] / per_iter, "pairs_ee": st["pairs_ee"] / per_iter,
