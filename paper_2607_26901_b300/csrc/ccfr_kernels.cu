@@ -1185,6 +1185,45 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
     W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
 }
 
+// walk_visit for a warp that works on one vertex (every lane holds the same
+// walk): the extended-precision Alg. 1 step runs on lane 0 alone, and the new
+// iterate and line count are broadcast.  The result is the one every lane
+// would compute; only lane 0's call frame and Alg. 1 state are written, where
+// 32 lanes would otherwise write 32 copies of them to local memory.
+__device__ __forceinline__ void walk_visit_warp(Walk<double>& W, float4 P, float eps, float eps_dep, int lane) {
+    ++W.nv;
+    if (W.S.m == 0) {
+        const f3 n = xyz(P);
+        const float beta0 = dot(n, n);
+        if (!(fabsf(beta0) < eps_dep)) {
+            W.y = sub(W.y, mul(n, rho_at(W.y, P) / beta0));
+            W.P0 = P;
+            W.lazy0 = true;
+            W.S.m = 1;
+        }
+    } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
+        if (lane == 0) {
+            const V3<double> yp = v3_of<double>(W.ypass);
+            if (W.lazy0) {
+                W.S.A[0] = xyz(W.P0);
+                W.S.V[0] = v3_of<double>(xyz(W.P0));
+                W.S.B[0] = plane_b<double>(W.P0, yp);
+            }
+            V3<double> zt = v3_diff<double>(W.y, W.ypass);
+            ortho_step<double>(zt, xyz(P), plane_b<double>(P, yp), W.S, eps_dep);
+            const V3<double> yn = v3_add(yp, zt);
+            W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
+        }
+        W.lazy0 = false;
+        W.y = mk(__shfl_sync(FULL, W.y.x, 0), __shfl_sync(FULL, W.y.y, 0), __shfl_sync(FULL, W.y.z, 0));
+        W.S.m = __shfl_sync(FULL, W.S.m, 0);
+    }
+    const float L = len(W.y);
+    W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
+    const f3 dz = sub(W.y, W.ypass);
+    W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
+}
+
 // 16-bit hash of a plane's bits: the second sort key, which splits runs of
 // equal rho keys on distinct planes (near-duplicate contacts reached through
 // several pairs) without a comparison sort.  Any fixed function of the bits
@@ -1313,7 +1352,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
         cur = best;
         first = false;
         const float4 P = tup_plane(best);
-        walk_visit(W, P, c.p.eps, c.p.eps_dep);
+        walk_visit_warp(W, P, c.p.eps, c.p.eps_dep, lane);
     }
     y_out = W.y;
     Dmax = sqrtf(W.dmax2);
@@ -1443,7 +1482,7 @@ __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, 
             const int f = __ffs(bal) - 1;
             const float4 Pf = make_float4(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f),
                                           __shfl_sync(FULL, P.z, f), __shfl_sync(FULL, P.w, f));
-            walk_visit(W, Pf, c.p.eps, c.p.eps_dep);
+            walk_visit_warp(W, Pf, c.p.eps, c.p.eps_dep, lane);
             lo = f + 1;
         }
     }
