@@ -222,6 +222,16 @@ ccfr_status ccfr_step_timed(ccfr_ctx* ctx, float* x, float* v, double* stage_ms,
 /* Name of stage i of ccfr_step_timed (static string; "" when out of range). */
 const char* ccfr_stage_name(int i);
 
+/* ccfr_step launched kernel by kernel (the same kernels in the same order),
+ * recording the substep's intermediate states for tests and tooling: the
+ * prediction x~ = x + dt v + dt^2 g of Alg. 4 into x_tilde_out (device,
+ * n_verts x 4 floats, or NULL) and, after every solver iteration i, the
+ * collision-free iterate x_c into iterates_out + i * n_verts * 4 (device,
+ * solver_iters x n_verts x 4 floats, or NULL).  x and v are updated as by
+ * ccfr_step.  Both outputs must be 16-byte aligned. */
+ccfr_status ccfr_step_record(ccfr_ctx* ctx, float* x, float* v, float* x_tilde_out, float* iterates_out,
+                             void* stream);
+
 /* ccfr_step on host buffers: copies x and v (host, n_verts x 4 floats each,
  * preferably pinned) to the context's device buffers, steps, copies them back,
  * and synchronises `stream` before returning. */

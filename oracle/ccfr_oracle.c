@@ -74,6 +74,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef unsigned long long u64;
 
@@ -84,6 +87,8 @@ typedef struct {
     double eps_dep;      /* Alg. 1 dependence tolerance */
     double tau_feas;     /* final feasibility tolerance */
     double band;         /* width of the decision bands reported to tests */
+    double dep_band;     /* factor of the dependence-test band: |beta| in [eps_dep / f, eps_dep f]
+                            is reported (f > 1; 0 = 10) */
     int n_max;           /* Alg. 2 n_maxIterations */
     int iters;           /* Alg. 4 solver iterations */
     int capacity;        /* plane capacity K per vertex, 0 = unbounded */
@@ -145,6 +150,11 @@ static void pv_push(pairvec *pv, int a, int b) {
     pv->v[pv->n].a = a;
     pv->v[pv->n].b = b;
     pv->n++;
+}
+
+/* Append b's pairs to a (b is left untouched). */
+static void pv_append(pairvec *a, const pairvec *b) {
+    for (long i = 0; i < b->n; ++i) pv_push(a, b->v[i].a, b->v[i].b);
 }
 
 static int cmp_pair(const void *x, const void *y) {
@@ -317,19 +327,29 @@ static void broad_kind(const topo *t, const float *x4, float pad, int kind, int 
             if (e > maxext) maxext = e;
         }
         qsort(sk, ni, sizeof(sortkey), cmp_sk);
-        for (int i = 0; i < nq; ++i) {
-            fbox q = kind_query_box(t, x4, kind, i, pad);
-            double from = (double)q.lo[0] - maxext;
-            int lo = 0, hi = ni;  /* first index with sk.lo >= from */
-            while (lo < hi) {
-                int mid = (lo + hi) / 2;
-                if ((double)sk[mid].lo < from) lo = mid + 1; else hi = mid;
+        /* queries are independent: each thread collects its own pairs; the
+         * result is sorted below, so it does not depend on the threads */
+#pragma omp parallel
+        {
+            pairvec mine = {0, 0, 0};
+#pragma omp for schedule(dynamic, 256)
+            for (int i = 0; i < nq; ++i) {
+                fbox q = kind_query_box(t, x4, kind, i, pad);
+                double from = (double)q.lo[0] - maxext;
+                int lo = 0, hi = ni;  /* first index with sk.lo >= from */
+                while (lo < hi) {
+                    int mid = (lo + hi) / 2;
+                    if ((double)sk[mid].lo < from) lo = mid + 1; else hi = mid;
+                }
+                for (int s = lo; s < ni && sk[s].lo <= q.hi[0]; ++s) {
+                    int j = sk[s].idx;
+                    if (overlap(&q, &ib[j]) && kind_ok(t, kind, i, j))
+                        pv_push(&mine, kind >= 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
+                }
             }
-            for (int s = lo; s < ni && sk[s].lo <= q.hi[0]; ++s) {
-                int j = sk[s].idx;
-                if (overlap(&q, &ib[j]) && kind_ok(t, kind, i, j))
-                    pv_push(out, kind >= 2 ? t->iso[i] : i, kind == 2 ? t->iso[j] : j);
-            }
+#pragma omp critical
+            pv_append(out, &mine);
+            free(mine.v);
         }
         free(sk);
     }
@@ -454,6 +474,18 @@ typedef struct {
 
 typedef struct { plane_rec *p; long n, cap; } planevec;
 
+static void plv_push(planevec *pv, int v, const double *n, double d, double phi, u64 key);
+
+/* Append b's planes to a. */
+static void plv_append(planevec *a, const planevec *b) {
+    if (a->n + b->n > a->cap) {
+        a->cap = a->n + b->n;
+        a->p = (plane_rec *)realloc(a->p, sizeof(plane_rec) * (a->cap > 0 ? a->cap : 1));
+    }
+    if (b->n) memcpy(a->p + a->n, b->p, sizeof(plane_rec) * b->n);
+    a->n += b->n;
+}
+
 static void plv_push(planevec *pv, int v, const double *n, double d, double phi, u64 key) {
     if (pv->n == pv->cap) {
         pv->cap = pv->cap ? 2 * pv->cap : 4096;
@@ -474,8 +506,14 @@ static int emit_pair(planevec *out, const double *w, const double *A, const doub
     double dist = norm3(diff);
     double phi = dist - P->xi;
     if (vflag && fabs(phi - 2.0 * P->r) <= P->band) {
-        for (int i = 0; i < na; ++i) vflag[va[i]] |= 2;
-        for (int i = 0; i < nb; ++i) vflag[vb[i]] |= 2;
+        for (int i = 0; i < na; ++i) {
+#pragma omp atomic
+            vflag[va[i]] |= 2;
+        }
+        for (int i = 0; i < nb; ++i) {
+#pragma omp atomic
+            vflag[vb[i]] |= 2;
+        }
     }
     if (dist == 0.0) return 0;            /* touching at build time: skipped (Sec. 4.1) */
     if (!(phi < 2.0 * P->r)) return 0;
@@ -567,14 +605,25 @@ static orc_regions *build_regions(const double *x3, const double *w, const topo 
         pairvec c = {0, 0, 0};
         broad_kind(t, x4, P->pad, kind, 0, &c);
         R->cand[kind] = c.n;
-        for (long i = 0; i < c.n; ++i) {
-            int acc;
-            if (kind == 0) acc = narrow_vf(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
-            else if (kind == 1) acc = narrow_ee(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
-            else if (kind == 2) acc = narrow_vv(&pv, x3, w, c.v[i].a, c.v[i].b, P, R->vflag);
-            else acc = narrow_ve(&pv, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
-            R->acc[kind] += acc;
+        long acc_k = 0;
+        /* pairs are independent; the planes are sorted by (vertex, key) below */
+#pragma omp parallel reduction(+ : acc_k)
+        {
+            planevec mine = {0, 0, 0};
+#pragma omp for schedule(dynamic, 1024)
+            for (long i = 0; i < c.n; ++i) {
+                int acc;
+                if (kind == 0) acc = narrow_vf(&mine, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
+                else if (kind == 1) acc = narrow_ee(&mine, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
+                else if (kind == 2) acc = narrow_vv(&mine, x3, w, c.v[i].a, c.v[i].b, P, R->vflag);
+                else acc = narrow_ve(&mine, x3, w, t, c.v[i].a, c.v[i].b, P, R->vflag);
+                acc_k += acc;
+            }
+#pragma omp critical
+            plv_append(&pv, &mine);
+            free(mine.p);
         }
+        R->acc[kind] += acc_k;
         free(c.v);
     }
     free(x4);
@@ -637,6 +686,20 @@ void orc_regions_export(const orc_regions *R, long *offs, double *planes4, doubl
     for (int k = 0; k < N_PAIR_KINDS; ++k) { cand_acc[k] = R->cand[k]; cand_acc[N_PAIR_KINDS + k] = R->acc[k]; }
 }
 
+/* Threads of the parallel loops (<= 0: all host cores); returns the count
+ * in use.  Results do not depend on it: every loop is over independent
+ * queries, pairs or vertices, and every output is sorted or per vertex. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n <= 0) n = omp_get_num_procs();
+    omp_set_num_threads(n);
+    return n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* ------------------------------------------------------------- Alg. 1 */
 
 typedef struct {
@@ -644,16 +707,20 @@ typedef struct {
     double V[3][3], A[3][3], B[3];
 } ero_state;
 
-static int near_eps(double v, double eps) { v = fabs(v); return v >= 0.1 * eps && v <= 10.0 * eps; }
+static int near_eps(double v, double eps, double f) {
+    if (!(f > 1.0)) f = 10.0;
+    v = fabs(v);
+    return v >= eps / f && v <= eps * f;
+}
 
 /* Plesnik's orthogonal projection step (Alg. 1; R7, R8).  xt is updated in
  * place; x0 is the pass's starting point.  *band is set when a dependence
  * test falls within a factor 10 of eps_dep. */
 static void ortho_projection(double *xt, const double *x0, const double *n, double b, ero_state *S,
-                             double eps_dep, int *band) {
+                             double eps_dep, double dep_band, int *band) {
     if (S->m == 0) {
         double beta0 = dot3(n, n);
-        if (near_eps(beta0, eps_dep)) *band = 1;
+        if (near_eps(beta0, eps_dep, dep_band)) *band = 1;
         if (fabs(beta0) < eps_dep) return;
         double a = (b - dot3(n, xt)) / beta0;
         for (int i = 0; i < 3; ++i) xt[i] += a * n[i];
@@ -669,7 +736,7 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
     sub3(n, n0, dn);
     double beta_u = dot3(dn, S->V[m - 1]);
     double alpha_u = b - dot3(n, xt);
-    if (near_eps(beta_u, eps_dep)) *band = 1;
+    if (near_eps(beta_u, eps_dep, dep_band)) *band = 1;
     if (fabs(beta_u) < eps_dep) return;
     double u[3], wv[3];
     for (int i = 0; i < 3; ++i) u[i] = xt[i] + (alpha_u / beta_u) * S->V[m - 1][i];
@@ -680,7 +747,7 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
         double dnj[3];
         sub3(nj, n0, dnj);
         double beta_w = dot3(dnj, S->V[j - 1]);
-        if (near_eps(beta_w, eps_dep)) *band = 1;
+        if (near_eps(beta_w, eps_dep, dep_band)) *band = 1;
         if (fabs(beta_w) > eps_dep) {
             double alpha_w = bj - b0 - dot3(dnj, wv);
             for (int i = 0; i < 3; ++i) wv[i] += (alpha_w / beta_w) * S->V[j - 1][i];
@@ -689,10 +756,10 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
     double vnew[3];
     sub3(wv, u, vnew);
     double vn = norm3(vnew);
-    if (near_eps(vn, eps_dep)) *band = 1;
+    if (near_eps(vn, eps_dep, dep_band)) *band = 1;
     if (vn > eps_dep) {
         double beta_new = dot3(n0, vnew);
-        if (near_eps(beta_new, eps_dep)) *band = 1;
+        if (near_eps(beta_new, eps_dep, dep_band)) *band = 1;
         if (fabs(beta_new) < eps_dep) {
             for (int i = 0; i < 3; ++i) xt[i] = u[i];
         } else {
@@ -717,7 +784,7 @@ void orc_ortho_sequence(const double *x0, const double *normals, const double *b
     int band = 0;
     for (int i = 0; i < k; ++i) {
         if (S.m >= 3) break;
-        ortho_projection(xt, x0, normals + 3 * i, b[i], &S, eps_dep, &band);
+        ortho_projection(xt, x0, normals + 3 * i, b[i], &S, eps_dep, 0.0, &band);
     }
     out[0] = xt[0]; out[1] = xt[1]; out[2] = xt[2];
 }
@@ -737,7 +804,8 @@ static int cmp_ord(const void *x, const void *y) {
  * planes4[k] = (n_k, d_k).  Returns 1 on halt.  nviol receives the number of
  * violated planes seen in the first pass.  *band is set when a decision of
  * the algorithm falls inside a band (rho near 0, near-tied sort keys of
- * distinct planes, dependence tests near eps_dep, |dx| near eps). */
+ * distinct planes, dependence tests within a factor dep_band of eps_dep,
+ * |dx| near eps). */
 static int project_vertex(const double *x, double *xp, const double *planes4, const u64 *keys, long np,
                           const orc_params *P, int *nviol, int *band) {
     *nviol = 0;
@@ -778,7 +846,7 @@ static int project_vertex(const double *x, double *xp, const double *planes4, co
             }
             double b = dot3(pl, x) - pl[3];
             nv++;
-            if (S.m < 3) ortho_projection(xt, x0, pl, b, &S, P->eps_dep, band);
+            if (S.m < 3) ortho_projection(xt, x0, pl, b, &S, P->eps_dep, P->dep_band, band);
             double dn[3];
             sub3(xt, x, dn);
             double L = norm3(dn);
@@ -824,6 +892,7 @@ long orc_project(const double *x3, double *xp3, const double *w, int n, const lo
                  const double *planes4, const u64 *keys, const double *dlimit, const orc_params *P,
                  unsigned char *halt, unsigned char *band, int *nviol) {
     long halts = 0;
+#pragma omp parallel for reduction(+ : halts) schedule(dynamic, 64)
     for (int v = 0; v < n; ++v) {
         int h = 0, bd = 0, nv = 0;
         if (w[v] > 0) {
@@ -1017,9 +1086,9 @@ void orc_response(double *y, const double *x, const double *xn, const double *pl
  * constraints in ex).  x3, v3 are updated in place (FP64).  x4w supplies
  * inverse masses; rest[e] the edges' rest lengths.  vband (optional, per
  * vertex) collects band flags over all iterations. */
-int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
-                 const int *tris, int nt, const double *rest, const orc_extra *ex, const orc_params *P,
-                 unsigned char *vband, orc_step_info *info) {
+static int step_impl(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
+                     const int *tris, int nt, const double *rest, const orc_extra *ex, const orc_params *P,
+                     unsigned char *vband, orc_step_info *info, unsigned char *halt_iter) {
     topo t;
     topo_init_ext(&t, n, edges, ne, tris, nt, x4w, ex);
     double *w = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
@@ -1066,6 +1135,8 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
         memcpy(xs, xt, N3);
         /* XPBD sweep of the distance constraints, colours ascending (R15, X3) */
         for (int c = 0; c < ncol; ++c) {
+            /* constraints of one colour share no vertex */
+#pragma omp parallel for schedule(static)
             for (int e = 0; e < nd; ++e) {
                 if (color[e] != c) continue;
                 int a = dpair[2 * e], b = dpair[2 * e + 1];
@@ -1087,6 +1158,7 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
         }
         /* then the volume constraints of the tetrahedra, colours ascending (X2, X3) */
         for (int c = 0; c < ntcol; ++c) {
+#pragma omp parallel for schedule(static)
             for (int q = 0; q < ntet; ++q) {
                 if (tcolor[q] != c) continue;
                 const int *T = ex->tets + 4 * q;
@@ -1110,6 +1182,7 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
         }
         /* contact response on every movable vertex, then the projection */
         if (P->delta > 0.0) {
+#pragma omp parallel for schedule(dynamic, 64)
             for (int v = 0; v < n; ++v) {
                 if (!(w[v] > 0) || isfinite(R->dlimit[v])) continue;
                 long o = R->offs[v], np = R->offs[v + 1] - R->offs[v];
@@ -1131,6 +1204,10 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
         }
         memcpy(pre, xs, N3);
         int shortened = 0;
+        long n_over = 0, n_viol = 0, n_halt = 0, n_short = 0;
+        /* vertices are independent (each reads its own planes and iterate) */
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : n_over, n_viol, n_halt, n_short) \
+    reduction(| : shortened)
         for (int v = 0; v < n; ++v) {
             double *y = xs + 3 * v;
             const double *x = xc + 3 * v;
@@ -1148,7 +1225,7 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
             int h = 0, nv = 0, bd = 0;
             if (isfinite(R->dlimit[v])) {
                 clamp_len(x, y, R->dlimit[v]);
-                info->overflow++;
+                n_over++;
             } else {
                 h = project_vertex(x, y, planes4, keys, np, P, &nv, &bd);
             }
@@ -1157,15 +1234,20 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
                 h = 1;
                 y[0] = x[0]; y[1] = x[1]; y[2] = x[2];
             }
-            if (nv) info->violated++;
-            info->halts += h;
+            if (nv) n_viol++;
+            n_halt += h;
+            if (halt_iter) halt_iter[(size_t)it * n + v] = (unsigned char)h;
             double dd[3];
             sub3(y, pre + 3 * v, dd);
-            if (norm3(dd) > 2.0 * P->eps) { shortened = 1; info->shortened++; }
+            if (norm3(dd) > 2.0 * P->eps) { shortened = 1; n_short++; }
             if (bd || (R->vflag[v] & 2)) bflag[v] = 1;
             free(planes4);
             free(keys);
         }
+        info->overflow += n_over;
+        info->violated += n_viol;
+        info->halts += n_halt;
+        info->shortened += n_short;
         orc_regions_free(R);
         memcpy(xc, xs, N3);
         info->iters_run = it + 1;
@@ -1184,6 +1266,20 @@ int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edg
     free(tlambda); free(tcolor); free(dpair); free(drest); free(dcomp);
     topo_free(&t);
     return 0;
+}
+
+int orc_step_ext(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
+                 const int *tris, int nt, const double *rest, const orc_extra *ex, const orc_params *P,
+                 unsigned char *vband, orc_step_info *info) {
+    return step_impl(x3, v3, x4w, n, edges, ne, tris, nt, rest, ex, P, vband, info, NULL);
+}
+
+/* orc_step_ext that also records, per iteration and vertex, whether the
+ * vertex halted (halt_iter[it * n + v], iters x n bytes; observability only). */
+int orc_step_hist(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,
+                  const int *tris, int nt, const double *rest, const orc_extra *ex, const orc_params *P,
+                  unsigned char *vband, orc_step_info *info, unsigned char *halt_iter) {
+    return step_impl(x3, v3, x4w, n, edges, ne, tris, nt, rest, ex, P, vband, info, halt_iter);
 }
 
 int orc_step(double *x3, double *v3, const float *x4w, int n, const int *edges, int ne,

@@ -28,7 +28,7 @@ class OrcParams(C.Structure):
         ("r", C.c_double), ("xi", C.c_double), ("delta", C.c_double),
         ("pad", C.c_float),
         ("eps", C.c_double), ("eps_dep", C.c_double), ("tau_feas", C.c_double),
-        ("band", C.c_double),
+        ("band", C.c_double), ("dep_band", C.c_double),
         ("n_max", C.c_int), ("iters", C.c_int), ("capacity", C.c_int), ("early_exit", C.c_int),
         ("dt", C.c_double), ("g", C.c_double * 3), ("compliance", C.c_double),
         ("k_resp", C.c_double), ("delta_v", C.c_double), ("mu_s", C.c_double), ("mu_k", C.c_double),
@@ -53,12 +53,14 @@ class OrcStepInfo(C.Structure):
 
 
 def build(force: bool = False) -> Path:
-    """Compile the oracle with gcc (no fast-math, no FMA contraction)."""
+    """Compile the oracle with gcc (no fast-math, no FMA contraction; OpenMP
+    over independent queries, pairs and vertices, which leaves every result
+    bitwise the same for any thread count)."""
     if _LIB.exists() and not force and _LIB.stat().st_mtime >= _SRC.stat().st_mtime:
         return _LIB
     _LIB.parent.mkdir(parents=True, exist_ok=True)
     tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
                            "-fPIC", "-shared", "-o", str(tmp), str(_SRC), "-lm"])
     os.replace(tmp, _LIB)
     return _LIB
@@ -94,6 +96,11 @@ def lib():
         _lib.orc_step_ext.restype = C.c_int
         _lib.orc_step_ext.argtypes = [P, P, P, C.c_int, P, C.c_int, P, C.c_int, P, C.POINTER(OrcExtra),
                                       C.POINTER(OrcParams), P, C.POINTER(OrcStepInfo)]
+        _lib.orc_step_hist.restype = C.c_int
+        _lib.orc_step_hist.argtypes = [P, P, P, C.c_int, P, C.c_int, P, C.c_int, P, C.POINTER(OrcExtra),
+                                       C.POINTER(OrcParams), P, C.POINTER(OrcStepInfo), P]
+        _lib.orc_set_threads.restype = C.c_int
+        _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_tet_colors.restype = C.c_int
         _lib.orc_tet_colors.argtypes = [P, C.c_int, C.c_int, P]
         _lib.orc_tet_volumes6.argtypes = [P, P, C.c_int, P]
@@ -120,13 +127,14 @@ def _c(a, dt):
 
 def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
                 iters: int | None = None, early_exit: bool = False,
-                eps_dep: float | None = None) -> OrcParams:
+                eps_dep: float | None = None, dep_band: float = 10.0) -> OrcParams:
     g = p.get("gravity", (0.0, -9.81, 0.0))
     o = OrcParams()
     o.r, o.xi, o.delta = p["r"], p["xi"], p.get("delta", 0.0)
     o.pad = np.float32(p["pad"])
     o.eps, o.eps_dep, o.tau_feas = p["eps"], p["eps_dep"] if eps_dep is None else eps_dep, p["tau_feas"]
     o.band = band
+    o.dep_band = dep_band
     o.n_max = p["n_max"]
     o.iters = p["iters"] if iters is None else iters
     o.capacity = p.get("plane_capacity", 0) if capacity is None else capacity
@@ -267,6 +275,12 @@ def response(y, x, xn, planes4, phi, keys, w, params: OrcParams):
     return y, band.value
 
 
+def set_threads(n: int = 0) -> int:
+    """Threads of the oracle's parallel loops (0: all host cores); returns
+    the number in use."""
+    return int(lib().orc_set_threads(int(n)))
+
+
 def edge_colors(edges, n):
     L = lib()
     e = _c(edges, np.int32)
@@ -309,9 +323,12 @@ def rest_lengths(x3, edges):
     return out[: len(e)]
 
 
-def step(x3, v3, x4w, edges, tris, rest, params: OrcParams, extra: Extra | None = None):
+def step(x3, v3, x4w, edges, tris, rest, params: OrcParams, extra: Extra | None = None,
+         halt_history: bool = False):
     """One substep of Alg. 4 (with the links and tetrahedra of X1-X3 when
-    extra is given).  Returns (x, v, info, vband)."""
+    extra is given).  Returns (x, v, info, vband), plus with halt_history a
+    (iterations, n) uint8 array of the vertices that halted in each
+    iteration."""
     L = lib()
     x = _c(x3, np.float64).copy()
     v = _c(v3, np.float64).copy()
@@ -321,10 +338,14 @@ def step(x3, v3, x4w, edges, tris, rest, params: OrcParams, extra: Extra | None 
     rest = _c(rest, np.float64)
     vband = np.zeros(len(x), np.uint8)
     info = OrcStepInfo()
-    rc = L.orc_step_ext(_p(x), _p(v), _p(x4w), len(x), _p(e), len(e), _p(t), len(t), _p(rest), _xref(extra),
-                        C.byref(params), _p(vband), C.byref(info))
+    hist = np.zeros((max(params.iters, 1), len(x)), np.uint8) if halt_history else None
+    args = (_p(x), _p(v), _p(x4w), len(x), _p(e), len(e), _p(t), len(t), _p(rest), _xref(extra),
+            C.byref(params), _p(vband), C.byref(info))
+    rc = L.orc_step_hist(*args, _p(hist)) if halt_history else L.orc_step_ext(*args)
     if rc != 0:
         raise RuntimeError("oracle step failed (edge colouring needs more than 64 colours)")
+    if halt_history:
+        return x, v, info, vband, hist[: info.iters_run]
     return x, v, info, vband
 
 

@@ -99,6 +99,7 @@ def lib():
             "ccfr_step": [P, P, P, P],
             "ccfr_step_host": [P, P, P, P],
             "ccfr_step_timed": [P, P, P, P, C.c_int, P],
+            "ccfr_step_record": [P, P, P, P, P, P],
             "ccfr_get_candidates": [P, P, P, C.c_long, P, C.c_long, P, C.c_long, P, P],
             "ccfr_copy_regions": [P, P, P, P, P, P],
             "ccfr_load_regions": [P, P, P, C.c_int, P],
@@ -138,7 +139,7 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["ccfr_create", "ccfr_create_ext", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
-            "ccfr_step_host", "ccfr_step_timed", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
+            "ccfr_step_host", "ccfr_step_timed", "ccfr_step_record", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
             "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
             "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune",
             "ccfr_server_create", "ccfr_server_add_scene", "ccfr_server_submit", "ccfr_server_start",
@@ -321,6 +322,17 @@ class Context:
         out = (C.c_double * n)()
         _check(lib().ccfr_step_timed(self.h, _ptr(x), _ptr(v), out, n, _stream(stream)), "ccfr_step_timed")
         return {lib().ccfr_stage_name(i).decode(): out[i] for i in range(n)}
+
+    def step_record(self, x, v, iters: int, stream=None):
+        """ccfr_step_record: one substep that also returns the prediction x~
+        and the collision-free iterate after each of the `iters` solver
+        iterations (device tensors, (N, 4) and (iters, N, 4))."""
+        torch = self.torch
+        xt = torch.empty_like(x)
+        its = torch.empty((iters,) + tuple(x.shape), dtype=x.dtype, device=x.device)
+        _check(lib().ccfr_step_record(self.h, _ptr(x), _ptr(v), _ptr(xt), _ptr(its), _stream(stream)),
+               "ccfr_step_record")
+        return xt, its
 
     def step_host(self, x_host: np.ndarray, v_host: np.ndarray, stream=None):
         assert x_host.dtype == np.float32 and x_host.flags.c_contiguous

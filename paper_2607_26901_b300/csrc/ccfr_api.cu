@@ -692,6 +692,34 @@ ccfr_status ccfr_step_timed(ccfr_ctx* c, float* x, float* v, double* stage_ms, i
 
 const char* ccfr_stage_name(int i) { return (i >= 0 && i < N_STAGES) ? kStageNames[i] : ""; }
 
+ccfr_status ccfr_step_record(ccfr_ctx* c, float* x, float* v, float* x_tilde_out, float* iterates_out,
+                             void* stream) {
+    if (!c || !x || !v || !aligned16(x) || !aligned16(v)) return CCFR_ERR_INVALID_ARG;
+    if ((x_tilde_out && !aligned16(x_tilde_out)) || (iterates_out && !aligned16(iterates_out)))
+        return CCFR_ERR_INVALID_ARG;
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c->rest_pending) {
+        launch_rest_state(c->dc, (const float4*)x, st);
+        c->rest_pending = false;
+    }
+    const size_t bytes = (size_t)c->dc.n_verts * sizeof(float4);
+    launch_predict(c->dc, (float4*)x, (float4*)v, st);
+    cudaError_t err = cudaSuccess;
+    if (x_tilde_out && bytes) err = cudaMemcpyAsync(x_tilde_out, c->dc.x_tilde, bytes, cudaMemcpyDeviceToDevice, st);
+    const int early = (c->prm.flags & CCFR_FLAG_EARLY_EXIT) ? 1 : 0;
+    for (int it = 0; it < c->prm.solver_iters && err == cudaSuccess; ++it) {
+        launch_iteration(c->dc, (float4*)x, st, c->color_off.data(), c->n_colors, c->tile_sums, c->n_buckets_total,
+                         early, nullptr, &c->side, c->tcolor_off.data(), c->n_tcolors);
+        if (iterates_out && bytes)
+            err = cudaMemcpyAsync((char*)iterates_out + (size_t)it * bytes, x, bytes, cudaMemcpyDeviceToDevice, st);
+    }
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    launch_update(c->dc, (float4*)x, (float4*)v, st);
+    c->regions_valid = true;
+    return from_cuda(cudaGetLastError());
+}
+
 ccfr_status ccfr_step_host(ccfr_ctx* c, float* x_host, float* v_host, void* stream) {
     if (!c || !x_host || !v_host) return CCFR_ERR_INVALID_ARG;
     DeviceGuard g(c->device);

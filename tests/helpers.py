@@ -50,3 +50,31 @@ def csr_to_padded(offs, planes4, K):
         out[v, :c] = planes4[o0:o0 + c]
         cnt[v] = o1 - o0
     return out, cnt
+
+
+def band_vertices_valid(orc, sc, P, x_build, y, band_mask, L, tol_rel=1e-5, step_bound=None):
+    """Validity of the GPU's result at vertices the oracle excludes from the
+    position comparison (a decision inside a band, where either branch is a
+    correct outcome of the method).  Each such movable vertex must either have
+    halted (y equal to its build position, bitwise) or satisfy every plane of
+    its oracle region, except planes of band pairs, within the final-check
+    tolerance tau plus tol_rel L (the plane parity bar), and move at most
+    step_bound when given.  Returns the list of violating vertex ids."""
+    x_build = np.asarray(x_build, np.float64)
+    R = orc.build_regions(x_build, sc.x, sc.edges, sc.tris, P)
+    r2 = 2.0 * P.r
+    bad = []
+    for v in np.nonzero(band_mask & (sc.x[:, 3] > 0))[0]:
+        d = y[v] - x_build[v]
+        if np.all(d == 0.0):
+            continue
+        if step_bound is not None and np.linalg.norm(d) > step_bound * (1 + 1e-6):
+            bad.append(int(v))
+            continue
+        o0, o1 = R["offs"][v], R["offs"][v + 1]
+        keep = np.abs(R["phi"][o0:o1] - r2) > P.band
+        pl = R["planes"][o0:o1][keep]
+        rho = pl[:, :3] @ d + pl[:, 3]
+        if len(rho) and rho.min() < -(P.tau_feas + tol_rel * L):
+            bad.append(int(v))
+    return bad
