@@ -137,12 +137,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str = "cloth_stack"):
+def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str = "cloth_stack",
+                  threads: int = 0):
     """Bounded CPU sample of the workload run by the FP64 oracle, one substep
     of `iters` iterations: the stack recipe at 4 layers of n_side^2 vertices
     (every stack variant), the mixed codimensional recipe at 96 rod segments,
-    or the wires recipe at 64x64 strands of 32 segments."""
+    or the wires recipe at 64x64 strands of 32 segments.  threads: the
+    oracle's OpenMP threads (0 = every host core).  Returns (vertex-iterations
+    per second, seconds, description, threads used)."""
     from oracle import oracle as O
+    used = O.set_threads(threads)
     ex = None
     if workload == "codimensional":
         sc = S.codimensional(rod_seg=96, cube_n=3, seed=6)
@@ -163,7 +167,18 @@ def oracle_sample(iters: int = 5, n_side: int = 48, seed: int = 2, workload: str
     O.step(x, v, sc.x, sc.edges, sc.tris, rest, P, extra=ex)
     dt = time.perf_counter() - t0
     units = sc.n_movable * iters
-    return units / dt, dt, f"{what}, 1 substep x {iters} iterations"
+    return units / dt, dt, f"{what}, 1 substep x {iters} iterations", used
+
+
+def cpu_baseline(workload: str) -> dict:
+    """The FP64 oracle on the host's cores (OpenMP over independent queries,
+    pairs and vertices: the same results for any thread count), on a bounded
+    sample of the workload, at every core and at one core."""
+    val, secs, sample, used = oracle_sample(iters=3, n_side=64, workload=workload, threads=0)
+    val1, secs1, _, _ = oracle_sample(iters=3, n_side=64, workload=workload, threads=1)
+    return {"value": val, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+            "seconds": round(secs, 2), "host_cores": os.cpu_count(),
+            "one_core": {"value": val1, "seconds": round(secs1, 2)}}
 
 
 # Informational binary32 operation counts per unit of work: a vertex-face
@@ -318,6 +333,8 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    # state at the start of the timed region: the e2e leg replays the same substeps
+    x_start, v_start = x.cpu().clone(), v.cpu().clone()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evs[0].record(stream)
     for k in range(args.steps):
@@ -384,16 +401,18 @@ def main():
                 "traffic": traffic, "algorithmic_bytes_per_launch": int(alg[dom]),
                 "launch_ms": round(kernel_ms[dom], 4)}
 
-    # e2e through the C ABI with host buffers
+    # e2e through the C ABI with host buffers: the same K substeps as the timed
+    # region, replayed from its start state (host -> device copy of x and v, the
+    # substep, device -> host copy, every step)
     e2e = None
     if not args.no_e2e:
         xh = torch.empty((N, 4), dtype=torch.float32).pin_memory()
         vh = torch.empty((N, 4), dtype=torch.float32).pin_memory()
-        xh.copy_(x.cpu())
-        vh.copy_(v.cpu())
+        xh.copy_(x_start)
+        vh.copy_(v_start)
         xa, va = xh.numpy(), vh.numpy()
-        ke = max(1, min(args.steps, 5))
-        ctx.step_host(xa, va)
+        ke = args.steps
+        torch.cuda.synchronize()
         ctx.reset_stats()
         if dist:
             dist.barrier()
@@ -416,9 +435,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        val, secs, sample = oracle_sample(workload=args.workload)
-        cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-               "seconds": round(secs, 2)}
+        cpu = cpu_baseline(args.workload)
 
     if rank == 0:
         line = {
@@ -435,6 +452,9 @@ def main():
             "e2e": e2e,
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "halt_frac": {"of_violated": st["halts"] / max(st["violated_verts"], 1),
+                          "of_movable": st["halts"] / max(sc.n_movable * st["iterations"], 1),
+                          "n_max": int(sc.params["n_max"])},
             "fp32": fp32_report(stage, st, per_iter, iters_timed, clocks),
             "stage_ms_per_step": {k: round(v_, 4) for k, v_ in stage.items()},
             "stats_per_iter": {"cand_vf": st["cand_vf"] / per_iter, "cand_ee": st["cand_ee"] / per_iter,
@@ -463,13 +483,25 @@ def main():
 def run_batch(args, ws, rank, local, desc):
     """Batched step: all scenes in one context (one graph-captured launch
     sequence per substep), after the autotuner; compared with the same scenes
-    stepped one context at a time on the same GPU and stream."""
+    stepped one context at a time on the same GPU and stream.  With several
+    GPUs the 512 scenes are partitioned across the ranks (balanced by vertex
+    count, paper_2607_26901_b300.shard); each rank steps its share in its own
+    batched context, with no exchange on the data path, and the job time is
+    the slowest rank's (strong scaling: the total work is fixed)."""
     import numpy as np
     import torch
     from paper_2607_26901_b300 import ccfr
+    from paper_2607_26901_b300.shard import shard_scenes
 
     torch.cuda.set_device(local)
-    scenes = S.batch(seed=4 + rank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    all_scenes = S.batch(seed=4)
+    shards = shard_scenes([sc.n_verts for sc in all_scenes], ws)
+    scenes = [all_scenes[i] for i in shards[rank]]
+    movable_all = sum(sc.n_movable for sc in all_scenes)
     x = torch.as_tensor(np.concatenate([sc.x for sc in scenes])).cuda().contiguous()
     v = torch.as_tensor(np.concatenate([sc.v for sc in scenes])).cuda().contiguous()
     movable = sum(sc.n_movable for sc in scenes)
@@ -482,15 +514,20 @@ def run_batch(args, ws, rank, local, desc):
     torch.cuda.synchronize()
     ctx.reset_stats()
     stream = torch.cuda.current_stream()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evs[0].record(stream)
     for k in range(args.steps):
         ctx.step(x, v)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
-    ms = evs[0].elapsed_time(evs[-1])
+    if dist:
+        dist.barrier()
+    ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), dist, "cuda")
     st = ctx.stats()
-    value = movable * st["iterations"] / (ms / 1e3)
+    value = movable_all * st["iterations"] / (ms / 1e3)
     stage = {}
     for _ in range(2):
         for kname, kms in ctx.step_timed(x, v).items():
@@ -518,18 +555,20 @@ def run_batch(args, ws, rank, local, desc):
             c1.step(xx, vv)
     e1.record(stream)
     torch.cuda.synchronize()
-    pms = e0.elapsed_time(e1)
+    pms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
     iters = scenes[0].params["iters"]
-    plain_value = movable * iters * pl_steps / (pms / 1e3)
+    plain_value = movable_all * iters * pl_steps / (pms / 1e3)
     for c1 in ctxs:
         c1.close()
     if rank == 0:
         print(json.dumps({
-            "metric": METRIC, "value": value * ws, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batch", "description": desc, "scenes": len(scenes), "verts": int(x.shape[0]),
-                       "movable": movable, "tuning": tuning, "autotune_s": round(tune_s, 2),
+            "config": {"workload": "batch", "description": desc, "scenes": len(all_scenes),
+                       "scenes_rank0": len(scenes), "verts_rank0": int(x.shape[0]), "movable": movable_all,
+                       "parallelism": f"scene shards x{ws}", "tuning": tuning, "autotune_s": round(tune_s, 2),
                        "autotune_best_ms": round(tuned_ms, 3)},
             "plain_per_scene": {"value": plain_value, "unit": UNIT, "ms_per_step": pms / pl_steps,
                                 "launch": "512 contexts, one ccfr_step each, one stream"},
@@ -543,6 +582,8 @@ def run_batch(args, ws, rank, local, desc):
                                    (("big_tris", 3), ("big_edges", 4), ("big_cells", 10), ("big_table_scans", 11),
                                     ("big_items", 12), ("bige_items", 13), ("big_cand", 14))},
         }), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_cards(args, ws, rank, local, desc):
@@ -609,16 +650,28 @@ def run_serve(args, ws, rank, local, desc):
        for the whole trace and latency is mostly waiting; the run gives the
        saturated service rate mu (completed requests / span).
     2. A trace at 0.7 mu (a sustainable load), with args.slots slots and with
-       one slot, for latencies that measure the service itself."""
+       one slot, for latencies that measure the service itself.
+
+    With several GPUs the scene pool is partitioned across the ranks
+    (paper_2607_26901_b300.shard); every rank replays the same trace and
+    serves the requests for its own scenes with its own server and HBM-budget
+    admission.  Latencies are gathered for the percentiles; the service rate
+    is the completed work over the slowest rank's span."""
     import numpy as np
     import torch
     from paper_2607_26901_b300 import ccfr
+    from paper_2607_26901_b300.shard import owner_of, shard_requests, shard_scenes
 
     torch.cuda.set_device(local)
-    small, big = serve_pool(5 + rank)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    small, big = serve_pool(5)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
     scenes_all = small + big
+    owner = owner_of(shard_scenes([sc.n_verts for sc in scenes_all], ws), len(scenes_all))
     nv = np.array([sc.n_movable for sc in scenes_all])
     iters = small[0].params["iters"]
 
@@ -628,61 +681,85 @@ def run_serve(args, ws, rank, local, desc):
         t_arr -= t_arr[0]
         pick_big = rng.uniform(size=n) < 0.05
         which = np.where(pick_big, rng.integers(0, len(big), n), rng.integers(0, len(small), n))
-        return t_arr, pick_big, which
+        gid = np.where(pick_big, len(small) + which, which)        # index into scenes_all
+        return t_arr, gid
 
-    def serve(slots, t_arr, pick_big, which):
-        n = len(t_arr)
+    def gather(obj):
+        if dist is None:
+            return [obj]
+        out = [None] * ws
+        dist.all_gather_object(out, obj)
+        return out
+
+    def serve(slots, t_arr, gid):
+        mine = shard_requests(gid, owner, rank)
         sv = ccfr.Server(budget, n_slots=slots, timeout_s=300.0)
-        ids_small = [sv.add_scene(sc) for sc in small]
-        ids_big = [sv.add_scene(sc) for sc in big]
-        sid = np.where(pick_big, np.array(ids_big)[np.minimum(which, len(big) - 1)],
-                       np.array(ids_small)[np.minimum(which, len(small) - 1)])
-        for i in range(n):
-            sv.submit(int(sid[i]), float(t_arr[i]))
+        sid_of = {}
+        for g in np.nonzero(owner == rank)[0]:
+            sid_of[int(g)] = sv.add_scene(scenes_all[int(g)])
+        for i in mine:
+            sv.submit(sid_of[int(gid[i])], float(t_arr[i]))
         t_pre = time.perf_counter()
         preloaded = sv.preload(0.9)
         t_pre = time.perf_counter() - t_pre
+        if dist:
+            dist.barrier()
         t0 = time.perf_counter()
         sv.start()
         done = sv.wait(1800.0)
         wall = time.perf_counter() - t0
-        res = sv.results(n)
+        res = sv.results(len(mine))
         info = sv.info()
         sv.close()
         ok = res["status"] == 0
-        lat = (res["t_done"] - res["t_arrival"])[ok] * 1e3
-        span = float(res["t_done"][ok].max() - res["t_arrival"].min()) if ok.any() else float("nan")
-        vert_updates = float(nv[sid[ok]].sum()) * iters
+        part = {"lat_ms": ((res["t_done"] - res["t_arrival"])[ok] * 1e3).tolist(),
+                "t_done_max": float(res["t_done"][ok].max()) if ok.any() else float("nan"),
+                "t_arr_min": float(res["t_arrival"].min()) if len(mine) else float("nan"),
+                "completed": int(ok.sum()), "failed": int((~ok).sum()), "done": int(done),
+                "vert_updates": float(nv[gid[mine][ok]].sum()) * iters, "wall_s": wall,
+                "admissions": info["admissions"], "evictions": info["evictions"],
+                "peak_resident_gb": info["peak_resident_bytes"] / 1e9, "preloaded": preloaded,
+                "preload_s": round(t_pre, 2)}
+        parts = gather(part)
+        lat = np.concatenate([np.asarray(q["lat_ms"]) for q in parts]) if parts else np.zeros(0)
+        span = max(q["t_done_max"] for q in parts) - min(q["t_arr_min"] for q in parts)
+        completed = sum(q["completed"] for q in parts)
         return {"p50_ms": float(np.percentile(lat, 50)) if len(lat) else None,
                 "p99_ms": float(np.percentile(lat, 99)) if len(lat) else None,
                 "mean_ms": float(lat.mean()) if len(lat) else None,
-                "completed": int(ok.sum()), "failed": int((~ok).sum()), "done": int(done),
-                "throughput_req_s": ok.sum() / span, "value": vert_updates / span,
-                "span_s": span, "wall_s": wall, "admissions": info["admissions"],
-                "evictions": info["evictions"], "peak_resident_gb": info["peak_resident_bytes"] / 1e9,
-                "preloaded": preloaded, "preload_s": round(t_pre, 2)}
+                "completed": completed, "failed": sum(q["failed"] for q in parts),
+                "done": sum(q["done"] for q in parts),
+                "throughput_req_s": completed / span, "value": sum(q["vert_updates"] for q in parts) / span,
+                "span_s": span, "wall_s": max(q["wall_s"] for q in parts),
+                "admissions": sum(q["admissions"] for q in parts), "evictions": sum(q["evictions"] for q in parts),
+                "peak_resident_gb_rank0": parts[0]["peak_resident_gb"],
+                "preloaded": sum(q["preloaded"] for q in parts), "preload_s": parts[0]["preload_s"]}
 
-    cfg = serve(args.slots, *trace(args.requests, args.rate, 50 + rank))
+    cfg = serve(args.slots, *trace(args.requests, args.rate, 50))
     mu = cfg["throughput_req_s"]
     rate_sub = 0.7 * mu
     n_sub = min(args.requests, 2000)
-    tr = trace(n_sub, rate_sub, 60 + rank)
+    tr = trace(n_sub, rate_sub, 60)
     sub = {"rate_per_s": rate_sub, "requests": n_sub, f"slots{args.slots}": serve(args.slots, *tr)}
     if args.slots != 1:
         sub["slots1"] = serve(1, *tr)
     if rank == 0:
         best = sub[f"slots{args.slots}"]
         print(json.dumps({
-            "metric": METRIC, "value": cfg["value"] * ws, "unit": UNIT, "n_gpus": ws, "steps": args.requests,
-            "warmup": 0, "ms_per_step": cfg["mean_ms"], "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": cfg["value"], "unit": UNIT, "n_gpus": ws, "steps": args.requests,
+            "warmup": 0, "ms_per_step": cfg["mean_ms"], "higher_is_better": True,
+            "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "serve", "description": desc, "requests": args.requests, "rate_per_s": args.rate,
-                       "slots": args.slots, "hbm_budget_gb": budget / 1e9, "scenes": len(scenes_all)},
+                       "slots": args.slots, "hbm_budget_gb_per_gpu": budget / 1e9, "scenes": len(scenes_all),
+                       "parallelism": f"scene shards x{ws}, one server per GPU"},
             "served_at_config_rate": cfg, "sub_saturation": sub,
             "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"],
             "latency_note": "p50/p99 at 0.7 x the saturated service rate (the configured rate exceeds it; "
                             "there latency is queueing, see served_at_config_rate)",
         }), flush=True)
+    if dist:
+        dist.destroy_process_group()
 
 
 def run_reference(args, ws, rank, desc):
@@ -692,8 +769,9 @@ def run_reference(args, ws, rank, desc):
         return
     vals = []
     sample = None
+    used = 1
     for i in range(args.warmup + args.steps):
-        val, secs, sample = oracle_sample(iters=1, n_side=48, workload=args.workload)
+        val, secs, sample, used = oracle_sample(iters=1, n_side=64, workload=args.workload, threads=0)
         if i >= args.warmup:
             vals.append((val, secs))
     total_units = sum(v * s for v, s in vals)
@@ -705,7 +783,8 @@ def run_reference(args, ws, rank, desc):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "description": desc, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+                         "host_cores": os.cpu_count()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

@@ -33,7 +33,15 @@
  *   R7  Alg. 1 uses the new (n, b) for j = m and appends the new (n, b).
  *   R8  one tolerance eps_dep for every test in Alg. 1, on absolute values;
  *       at most 3 ERO directions (a fourth normal in 3-D is dependent).
- *   R9  retraction after every Alg. 1 call, measured from the build position.
+ *   R9  one retraction per pass: the pass's result (the projected boundary
+ *       position x* of Sec. 3.2) is shifted back by eps towards the build
+ *       position x (reset to x when closer than eps).  Alg. 2's listing places
+ *       the retraction after every Alg. 1 call; but Alg. 1 assumes its iterate
+ *       lies on the planes already taken, and a retraction between calls moves
+ *       it off them, so the next call misses its own plane by about
+ *       eps d / |y| and the final check halts the vertex.  Sec. 3.2 describes
+ *       the retraction as a numerical margin applied to the projected position,
+ *       which is what this reading does (see the halting study).
  *   R10 planes are sorted once by (rho, key) at the pass input.
  *   R11 final check rho_k >= -tau_feas on the result, else halt.
  *   R12 every iteration restarts the XPBD candidate from the prediction and
@@ -89,6 +97,8 @@ typedef struct {
     double band;         /* width of the decision bands reported to tests */
     double dep_band;     /* factor of the dependence-test band: |beta| in [eps_dep / f, eps_dep f]
                             is reported (f > 1; 0 = 10) */
+    double cond_band;    /* an Alg. 1 division by beta with |beta| / |direction| below this is
+                            reported (an ill-conditioned step; 0 = none) */
     int n_max;           /* Alg. 2 n_maxIterations */
     int iters;           /* Alg. 4 solver iterations */
     int capacity;        /* plane capacity K per vertex, 0 = unbounded */
@@ -152,16 +162,37 @@ static void pv_push(pairvec *pv, int a, int b) {
     pv->n++;
 }
 
+static int cmp_int(const void *x, const void *y) {
+    int a = *(const int *)x, b = *(const int *)y;
+    return (a > b) - (a < b);
+}
+
+/* Sort pairs lexicographically: a counting sort on the first element (range
+ * [0, na)), then each run sorted by the second element (runs in parallel).
+ * The same order as one lexicographic sort of the pairs. */
+static void sort_pairs(pairvec *pv, int na) {
+    long n = pv->n;
+    if (n <= 1) return;
+    long *start = (long *)calloc((size_t)na + 1, sizeof(long));
+    for (long i = 0; i < n; ++i) start[pv->v[i].a + 1]++;
+    for (int a = 0; a < na; ++a) start[a + 1] += start[a];
+    long *fill = (long *)malloc(sizeof(long) * (size_t)(na > 0 ? na : 1));
+    memcpy(fill, start, sizeof(long) * (size_t)na);
+    int *b = (int *)malloc(sizeof(int) * (size_t)n);
+    for (long i = 0; i < n; ++i) b[fill[pv->v[i].a]++] = pv->v[i].b;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int a = 0; a < na; ++a) {
+        if (start[a + 1] - start[a] > 1) qsort(b + start[a], (size_t)(start[a + 1] - start[a]), sizeof(int), cmp_int);
+        for (long i = start[a]; i < start[a + 1]; ++i) { pv->v[i].a = a; pv->v[i].b = b[i]; }
+    }
+    free(b);
+    free(fill);
+    free(start);
+}
+
 /* Append b's pairs to a (b is left untouched). */
 static void pv_append(pairvec *a, const pairvec *b) {
     for (long i = 0; i < b->n; ++i) pv_push(a, b->v[i].a, b->v[i].b);
-}
-
-static int cmp_pair(const void *x, const void *y) {
-    const ipair *p = (const ipair *)x, *q = (const ipair *)y;
-    if (p->a != q->a) return p->a < q->a ? -1 : 1;
-    if (p->b != q->b) return p->b < q->b ? -1 : 1;
-    return 0;
 }
 
 /* Constraints beyond the collision edges (readings X1-X3): distance links
@@ -354,7 +385,7 @@ static void broad_kind(const topo *t, const float *x4, float pad, int kind, int 
         free(sk);
     }
     free(ib);
-    qsort(out->v, out->n, sizeof(ipair), cmp_pair);
+    sort_pairs(out, kind == 0 ? t->n : (kind == 1 ? t->ne : t->n));
 }
 
 /* Candidate sets C_VF, C_EE, C_VV, C_VE.  Two-call protocol: with out == NULL
@@ -627,12 +658,24 @@ static orc_regions *build_regions(const double *x3, const double *w, const topo 
         free(c.v);
     }
     free(x4);
-    qsort(pv.p, pv.n, sizeof(plane_rec), cmp_plane);
-    R->p = pv.p;
+    /* CSR by receiving vertex (a counting sort), each vertex's planes sorted
+     * by key: the order of one sort by (vertex, key), which is unique */
     R->total = pv.n;
     R->offs = (long *)calloc(n + 1, sizeof(long));
     for (long i = 0; i < pv.n; ++i) R->offs[pv.p[i].v + 1]++;
     for (int i = 0; i < n; ++i) R->offs[i + 1] += R->offs[i];
+    R->p = (plane_rec *)malloc(sizeof(plane_rec) * (pv.n > 0 ? pv.n : 1));
+    {
+        long *fill = (long *)malloc(sizeof(long) * (n > 0 ? n : 1));
+        memcpy(fill, R->offs, sizeof(long) * (size_t)n);
+        for (long i = 0; i < pv.n; ++i) R->p[fill[pv.p[i].v]++] = pv.p[i];
+        free(fill);
+    }
+    free(pv.p);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int i = 0; i < n; ++i)
+        if (R->offs[i + 1] - R->offs[i] > 1)
+            qsort(R->p + R->offs[i], (size_t)(R->offs[i + 1] - R->offs[i]), sizeof(plane_rec), cmp_plane);
     R->dlimit = (double *)malloc(sizeof(double) * (n > 0 ? n : 1));
     for (int i = 0; i < n; ++i) {
         R->dlimit[i] = INFINITY;
@@ -716,8 +759,16 @@ static int near_eps(double v, double eps, double f) {
 /* Plesnik's orthogonal projection step (Alg. 1; R7, R8).  xt is updated in
  * place; x0 is the pass's starting point.  *band is set when a dependence
  * test falls within a factor 10 of eps_dep. */
+/* An Alg. 1 step moving along `dir` by (numerator / beta): its result
+ * changes by |dir| / |beta| times any error of the numerator (the planes' and
+ * the iterate's rounding), so a small |beta| / |dir| is an ill-conditioned
+ * step, reported as a band. */
+static int ill_conditioned(double beta, const double *dir, double cond_band) {
+    return cond_band > 0.0 && fabs(beta) < cond_band * norm3(dir);
+}
+
 static void ortho_projection(double *xt, const double *x0, const double *n, double b, ero_state *S,
-                             double eps_dep, double dep_band, int *band) {
+                             double eps_dep, double dep_band, double cond_band, int *band) {
     if (S->m == 0) {
         double beta0 = dot3(n, n);
         if (near_eps(beta0, eps_dep, dep_band)) *band = 1;
@@ -739,6 +790,7 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
     if (near_eps(beta_u, eps_dep, dep_band)) *band = 1;
     if (fabs(beta_u) < eps_dep) return;
     double u[3], wv[3];
+    if (ill_conditioned(beta_u, S->V[m - 1], cond_band)) *band = 1;
     for (int i = 0; i < 3; ++i) u[i] = xt[i] + (alpha_u / beta_u) * S->V[m - 1][i];
     for (int i = 0; i < 3; ++i) wv[i] = x0[i] + n[i];
     for (int j = 1; j <= m; ++j) {
@@ -750,6 +802,7 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
         if (near_eps(beta_w, eps_dep, dep_band)) *band = 1;
         if (fabs(beta_w) > eps_dep) {
             double alpha_w = bj - b0 - dot3(dnj, wv);
+            if (ill_conditioned(beta_w, S->V[j - 1], cond_band)) *band = 1;
             for (int i = 0; i < 3; ++i) wv[i] += (alpha_w / beta_w) * S->V[j - 1][i];
         }
     }
@@ -764,6 +817,7 @@ static void ortho_projection(double *xt, const double *x0, const double *n, doub
             for (int i = 0; i < 3; ++i) xt[i] = u[i];
         } else {
             double alpha_new = b0 - dot3(n0, u);
+            if (ill_conditioned(beta_new, vnew, cond_band)) *band = 1;
             for (int i = 0; i < 3; ++i) xt[i] = u[i] + (alpha_new / beta_new) * vnew[i];
         }
         if (m < 3) {
@@ -784,7 +838,7 @@ void orc_ortho_sequence(const double *x0, const double *normals, const double *b
     int band = 0;
     for (int i = 0; i < k; ++i) {
         if (S.m >= 3) break;
-        ortho_projection(xt, x0, normals + 3 * i, b[i], &S, eps_dep, 0.0, &band);
+        ortho_projection(xt, x0, normals + 3 * i, b[i], &S, eps_dep, 0.0, 0.0, &band);
     }
     out[0] = xt[0]; out[1] = xt[1]; out[2] = xt[2];
 }
@@ -800,11 +854,33 @@ static int cmp_ord(const void *x, const void *y) {
     return 0;
 }
 
+/* Whether the decision "plane pl violated or not" at the iterate xt can
+ * change the pass's result (used only to report band decisions): the plane
+ * would be the pass's first violation (which decides between returning x'
+ * and retracting the pass result), or Alg. 1 would store it or move the
+ * iterate.  A plane identical to one already taken, met with rho = 0 up to
+ * rounding right after the iterate was projected onto that plane, is a no-op
+ * either way. */
+static int decision_matters(const double *xt, const double *x0, const double *pl, double b, const ero_state *S,
+                            int nv, const orc_params *P) {
+    if (nv == 0) return 1;
+    if (S->m >= 3) return 0;
+    double xc[3] = {xt[0], xt[1], xt[2]};
+    ero_state Sc = *S;
+    int unused = 0;
+    ortho_projection(xc, x0, pl, b, &Sc, P->eps_dep, P->dep_band, 0.0, &unused);
+    if (Sc.m != S->m) return 1;
+    double d[3];
+    sub3(xc, xt, d);
+    return norm3(d) > P->band;
+}
+
 /* projectOntoConvexRegion for one vertex (Alg. 2; R6, R9, R10, R11).
  * planes4[k] = (n_k, d_k).  Returns 1 on halt.  nviol receives the number of
  * violated planes seen in the first pass.  *band is set when a decision of
- * the algorithm falls inside a band (rho near 0, near-tied sort keys of
- * distinct planes, dependence tests within a factor dep_band of eps_dep,
+ * the algorithm falls inside a band (rho near 0 where the decision can change
+ * the result, near-tied sort keys of distinct planes, dependence tests within
+ * a factor dep_band of eps_dep, ill-conditioned Alg. 1 steps (cond_band),
  * |dx| near eps). */
 static int project_vertex(const double *x, double *xp, const double *planes4, const u64 *keys, long np,
                           const orc_params *P, int *nviol, int *band) {
@@ -830,7 +906,7 @@ static int project_vertex(const double *x, double *xp, const double *planes4, co
             double dx[3];
             sub3(xt, x, dx);
             double rho = dot3(dx, pl) + pl[3];
-            if (fabs(rho) <= P->band) *band = 1;
+            if (fabs(rho) <= P->band && decision_matters(xt, x0, pl, dot3(pl, x) - pl[3], &S, nv, P)) *band = 1;
             if (rho >= 0.0) continue;
             /* a near-tie in the sort order between distinct planes changes the
              * visiting order on a lower-precision replay */
@@ -846,7 +922,12 @@ static int project_vertex(const double *x, double *xp, const double *planes4, co
             }
             double b = dot3(pl, x) - pl[3];
             nv++;
-            if (S.m < 3) ortho_projection(xt, x0, pl, b, &S, P->eps_dep, P->dep_band, band);
+            if (S.m < 3) ortho_projection(xt, x0, pl, b, &S, P->eps_dep, P->dep_band, P->cond_band, band);
+        }
+        /* R9: the pass result (the projected boundary position) is retracted
+         * once by eps towards the build position x, or reset to x when it is
+         * closer to x than eps (Sec. 3.2) */
+        if (nv > 0) {
             double dn[3];
             sub3(xt, x, dn);
             double L = norm3(dn);

@@ -16,12 +16,12 @@ markdown table row per (scene, variant):
   - halts / movable: halted vertex-iterations over movable vertex-iterations.
 
 Variants: the pass budget n_max (reading R6 runs n_max + 1 passes); the
-dependence tolerance eps_dep of Alg. 1 (reading R8); one retraction per pass
-instead of after every Alg. 1 call (the alternative to reading R9, from the
-wording of Sec. 3.2); near-duplicate planes merged (a violated plane whose
-normal and offset equal those of a plane visited before it, within 1e-9 and
-1e-12 m, is skipped).  The last two are compiled copies of the oracle with
-the change applied (oracle/variants.py).
+dependence tolerance eps_dep of Alg. 1 (reading R8); the retraction after
+every Alg. 1 call, where Alg. 2's listing places it, instead of once per
+pass (reading R9, from the wording of Sec. 3.2); near-duplicate planes merged
+(a violated plane whose normal and offset equal those of a plane visited
+before it, within 1e-9 and 1e-12 m, is skipped).  The last two are compiled
+copies of the oracle with the change applied (oracle/variants.py).
 
 Usage: python -m oracle.halt_study [--steps 2]
 """
@@ -42,7 +42,12 @@ from oracle import oracle as O  # noqa: E402
 from oracle import variants  # noqa: E402
 from paper_2607_26901_b300 import scenes as S  # noqa: E402
 
-RETRACT_EACH_CALL = """            double dn[3];
+RETRACT_ONCE_PER_PASS = """        }
+        /* R9: the pass result (the projected boundary position) is retracted
+         * once by eps towards the build position x, or reset to x when it is
+         * closer to x than eps (Sec. 3.2) */
+        if (nv > 0) {
+            double dn[3];
             sub3(xt, x, dn);
             double L = norm3(dn);
             if (fabs(L - P->eps) <= P->band) *band = 1;
@@ -53,9 +58,7 @@ RETRACT_EACH_CALL = """            double dn[3];
             }
         }
         if (pass == 0) *nviol = nv;"""
-RETRACT_ONCE_PER_PASS = """        }
-        if (nv > 0) {
-            double dn[3];
+RETRACT_EACH_CALL = """            double dn[3];
             sub3(xt, x, dn);
             double L = norm3(dn);
             if (L > P->eps) {
@@ -84,21 +87,22 @@ SCENES = {
 }
 
 VARIANTS = [
-    ("R9 per call, n_max 1 (the build's reading)", "call", 1, 1e-6),
-    ("R9 per call, n_max 2", "call", 2, 1e-6),
-    ("R9 per call, n_max 4", "call", 4, 1e-6),
-    ("R9 per call, n_max 1, eps_dep 1e-9", "call", 1, 1e-9),
-    ("R9 per call, n_max 1, eps_dep 1e-12", "call", 1, 1e-12),
-    ("R9 per call, n_max 1, duplicates merged", "merge", 1, 1e-6),
-    ("one retraction per pass, n_max 1", "once", 1, 1e-6),
-    ("one retraction per pass, n_max 2", "once", 2, 1e-6),
+    ("once per pass, n_max 1 (the build's reading R9)", "once", 1, 1e-6),
+    ("once per pass, n_max 2", "once", 2, 1e-6),
+    ("once per pass, n_max 4", "once", 4, 1e-6),
+    ("once per pass, n_max 1, eps_dep 1e-9", "once", 1, 1e-9),
+    ("once per pass, n_max 1, eps_dep 1e-12", "once", 1, 1e-12),
+    ("once per pass, n_max 1, duplicates merged", "merge", 1, 1e-6),
+    ("after every Alg. 1 call (the listing), n_max 1", "call", 1, 1e-6),
+    ("after every Alg. 1 call, n_max 2", "call", 2, 1e-6),
+    ("after every Alg. 1 call, n_max 4", "call", 4, 1e-6),
 ]
 
 
 def libraries():
     return {
-        "call": O,
-        "once": variants.load("retract_once", [(RETRACT_EACH_CALL, RETRACT_ONCE_PER_PASS)]),
+        "once": O,
+        "call": variants.load("retract_each_call", [(RETRACT_ONCE_PER_PASS, RETRACT_EACH_CALL)]),
         "merge": variants.load("merge_dup", [(SKIP_VIOLATED, SKIP_VIOLATED_OR_DUPLICATE)]),
     }
 

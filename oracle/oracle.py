@@ -28,7 +28,7 @@ class OrcParams(C.Structure):
         ("r", C.c_double), ("xi", C.c_double), ("delta", C.c_double),
         ("pad", C.c_float),
         ("eps", C.c_double), ("eps_dep", C.c_double), ("tau_feas", C.c_double),
-        ("band", C.c_double), ("dep_band", C.c_double),
+        ("band", C.c_double), ("dep_band", C.c_double), ("cond_band", C.c_double),
         ("n_max", C.c_int), ("iters", C.c_int), ("capacity", C.c_int), ("early_exit", C.c_int),
         ("dt", C.c_double), ("g", C.c_double * 3), ("compliance", C.c_double),
         ("k_resp", C.c_double), ("delta_v", C.c_double), ("mu_s", C.c_double), ("mu_k", C.c_double),
@@ -127,7 +127,7 @@ def _c(a, dt):
 
 def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
                 iters: int | None = None, early_exit: bool = False,
-                eps_dep: float | None = None, dep_band: float = 10.0) -> OrcParams:
+                eps_dep: float | None = None, dep_band: float = 10.0, cond_band: float = 0.0) -> OrcParams:
     g = p.get("gravity", (0.0, -9.81, 0.0))
     o = OrcParams()
     o.r, o.xi, o.delta = p["r"], p["xi"], p.get("delta", 0.0)
@@ -135,6 +135,7 @@ def make_params(p: dict, *, band: float = 0.0, capacity: int | None = None,
     o.eps, o.eps_dep, o.tau_feas = p["eps"], p["eps_dep"] if eps_dep is None else eps_dep, p["tau_feas"]
     o.band = band
     o.dep_band = dep_band
+    o.cond_band = cond_band
     o.n_max = p["n_max"]
     o.iters = p["iters"] if iters is None else iters
     o.capacity = p.get("plane_capacity", 0) if capacity is None else capacity

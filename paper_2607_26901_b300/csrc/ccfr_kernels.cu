@@ -13,6 +13,8 @@
 //   resolution    k_project: Alg. 2 calling Alg. 1 per vertex, one warp per
 //                 vertex streaming its plane list
 //   XPBD          k_predict, k_xpbd_color, k_update (Alg. 4)
+#include <atomic>
+
 #include "ccfr_device.cuh"
 #include "ccfr_internal.h"
 #include "ccfr_df.cuh"
@@ -1118,19 +1120,34 @@ __device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float e
 
 __device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
 
+// Bitwise-identical planes (one contact reached through several pairs).  In
+// the pass order they are adjacent (equal key, hash and bits), and a copy of
+// the plane just visited is a no-op for Alg. 1 (beta = 0: the iterate is
+// already on it) and for the pass result (its violation was counted with the
+// first copy), so the walks skip it.
+__device__ __forceinline__ bool same_bits(float4 a, float4 b) {
+    return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y) &&
+           __float_as_uint(a.z) == __float_as_uint(b.z) && __float_as_uint(a.w) == __float_as_uint(b.w);
+}
+
 // One pass of Alg. 2 in progress: the pass input, the binary32 iterate y
-// (offset from the build position), the largest squared distance of y from
-// the pass input so far, the number of violated planes met and the ERO state.
-// The first Alg. 1 step of a pass (|V| = 0) is a plain orthogonal projection
-// onto one plane, with no division by a dependence measure: it runs in
-// binary32 (as accurate as the binary32 iterate it produces), and its ERO
-// entry is formed from the stored plane P0 only when a second step needs it.
+// (offset from the build position) on which the planes are tested, the
+// largest squared distance of y from the pass input so far, the number of
+// violated planes met and the ERO state.  The first Alg. 1 step of a pass
+// (|V| = 0) is a plain orthogonal projection onto one plane, with no division
+// by a dependence measure: it runs in binary32, and its ERO entry (and its
+// result in R) is formed from the stored plane P0 only when a second step
+// needs it.  Later steps carry their iterate z = y - ypass in R from step to
+// step (y is its binary32 rounding): Alg. 1 divides by dependence measures
+// beta, and restarting each step from the rounded y would amplify that
+// rounding by 1 / beta.
 template <typename R> struct Walk {
     f3 ypass, y;
     float dmax2;
     int nv;
     bool lazy0;
     float4 P0;
+    V3<R> z;
     Ero<R> S;
 };
 
@@ -1148,11 +1165,22 @@ template <typename R> __device__ __forceinline__ R plane_b(float4 P, const V3<R>
     return XP<R>::neg(XP<R>::add(XP<R>::make(P.w), v3_dot(v3_of<R>(xyz(P)), yp)));
 }
 
-// A plane violated at the current iterate: Alg. 1 (while |V| < 3), then the
-// retraction by eps towards the build position (Sec. 3.2).  Steps with
-// |V| >= 1 work in R on z = y - ypass (exact) and round their result once to
-// binary32; with |V| = 3 the iterate only retracts, in binary32.  A binary32
-// scaling is accurate to ~u |y| here (no cancellation).
+// The first step's ERO entry and its iterate in R (z = (b0 / |n0|^2) n0 in
+// coordinates centred at the pass input), formed when a second step needs them.
+template <typename R> __device__ __forceinline__ void walk_lazy0(Walk<R>& W, const V3<R>& yp) {
+    W.S.A[0] = xyz(W.P0);
+    W.S.V[0] = v3_of<R>(xyz(W.P0));
+    W.S.B[0] = plane_b<R>(W.P0, yp);
+    const R beta0 = v3_dot(W.S.V[0], W.S.V[0]);
+    const R s0 = XP<R>::div(W.S.B[0], beta0);
+    W.z = v3<R>(XP<R>::mul(s0, W.S.V[0].x), XP<R>::mul(s0, W.S.V[0].y), XP<R>::mul(s0, W.S.V[0].z));
+}
+
+// A plane violated at the current iterate: Alg. 1 (while |V| < 3; with
+// |V| = 3 the plane is counted and the iterate stays).  Steps with |V| >= 1
+// work in R on z (kept in R across steps) and round each result to binary32
+// for the tests.  The retraction follows once, at the end of the pass
+// (walk_end).
 template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, float4 P, float eps, float eps_dep) {
     ++W.nv;
     if (W.S.m == 0) {
@@ -1169,18 +1197,13 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
         // exactly, and Alg. 1 leaves the iterate unchanged: skipped)
         const V3<R> yp = v3_of<R>(W.ypass);
         if (W.lazy0) {
-            W.S.A[0] = xyz(W.P0);
-            W.S.V[0] = v3_of<R>(xyz(W.P0));
-            W.S.B[0] = plane_b<R>(W.P0, yp);
+            walk_lazy0(W, yp);
             W.lazy0 = false;
         }
-        V3<R> zt = v3_diff<R>(W.y, W.ypass);
-        ortho_step<R>(zt, xyz(P), plane_b<R>(P, yp), W.S, eps_dep);
-        const V3<R> yn = v3_add(yp, zt);
+        ortho_step<R>(W.z, xyz(P), plane_b<R>(P, yp), W.S, eps_dep);
+        const V3<R> yn = v3_add(yp, W.z);
         W.y = mk(XP<R>::to_float(yn.x), XP<R>::to_float(yn.y), XP<R>::to_float(yn.z));
     }
-    const float L = len(W.y);
-    W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
     const f3 dz = sub(W.y, W.ypass);
     W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
 }
@@ -1204,24 +1227,26 @@ __device__ __forceinline__ void walk_visit_warp(Walk<double>& W, float4 P, float
     } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
         if (lane == 0) {
             const V3<double> yp = v3_of<double>(W.ypass);
-            if (W.lazy0) {
-                W.S.A[0] = xyz(W.P0);
-                W.S.V[0] = v3_of<double>(xyz(W.P0));
-                W.S.B[0] = plane_b<double>(W.P0, yp);
-            }
-            V3<double> zt = v3_diff<double>(W.y, W.ypass);
-            ortho_step<double>(zt, xyz(P), plane_b<double>(P, yp), W.S, eps_dep);
-            const V3<double> yn = v3_add(yp, zt);
+            if (W.lazy0) walk_lazy0(W, yp);
+            ortho_step<double>(W.z, xyz(P), plane_b<double>(P, yp), W.S, eps_dep);
+            const V3<double> yn = v3_add(yp, W.z);
             W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
         }
         W.lazy0 = false;
         W.y = mk(__shfl_sync(FULL, W.y.x, 0), __shfl_sync(FULL, W.y.y, 0), __shfl_sync(FULL, W.y.z, 0));
         W.S.m = __shfl_sync(FULL, W.S.m, 0);
     }
-    const float L = len(W.y);
-    W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
     const f3 dz = sub(W.y, W.ypass);
     W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
+}
+
+// End of a pass: the pass result (the projected boundary position) is
+// shifted back by eps towards the build position, or reset to it when it is
+// closer than eps (Sec. 3.2), once per pass that met a violated plane.
+template <typename R> __device__ __forceinline__ void walk_end(Walk<R>& W, float eps) {
+    if (W.nv == 0) return;
+    const float L = len(W.y);
+    W.y = (L > eps) ? mul(W.y, (L - eps) / L) : mk(0.f, 0.f, 0.f);
 }
 
 // 16-bit hash of a plane's bits: the second sort key, which splits runs of
@@ -1323,10 +1348,11 @@ __device__ __forceinline__ float warp_max(float v) {
 
 // One pass of Alg. 2 from the pass input ypass: visit the planes in ascending
 // order of the sort key (rho at the first input y0, then the plane's own bits
-// and slot), call Alg. 1 on each plane violated at the current iterate and
-// retract by eps towards the build position.  `get(e, P, key, j)` yields
-// source entry e of n.  Returns the number of violated planes; y_out receives
-// the pass result and Dmax the largest distance of the iterate from ypass.
+// and slot), call Alg. 1 on each plane violated at the current iterate, and
+// retract the result by eps towards the build position.  `get(e, P, key, j)`
+// yields source entry e of n.  Returns the number of violated planes; y_out
+// receives the pass result and Dmax the largest distance from ypass of the
+// iterates at which planes were tested.
 template <typename Get>
 __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get get, f3 ypass, f3& y_out, float& Dmax) {
     Walk<double> W;
@@ -1342,7 +1368,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
             float key;
             int j;
             get(e, P, key, j);
-            if (rho_at(W.y, P) < 0.f) {
+            if (rho_at(W.y, P) < 0.f && (first || !same_bits(P, tup_plane(cur)))) {
                 Tup t = make_tup(key, P, j);
                 if ((first || tless(cur, t)) && tless(t, best)) best = t;
             }
@@ -1354,8 +1380,9 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
         const float4 P = tup_plane(best);
         walk_visit_warp(W, P, c.p.eps, c.p.eps_dep, lane);
     }
-    y_out = W.y;
     Dmax = sqrtf(W.dmax2);
+    walk_end(W, c.p.eps);
+    y_out = W.y;
     return W.nv;
 }
 
@@ -1465,29 +1492,33 @@ __device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
 
 // One pass of Alg. 2 over the sorted candidates sb.idx[0][0..m): walk
 // the list in order, 32 planes per chunk held one per lane; the first plane of
-// the chunk violated at the current iterate is handled (Alg. 1 + retraction)
-// and the walk resumes with the chunk's later planes, tested at the new iterate.
+// the chunk violated at the current iterate is handled (Alg. 1) and the walk
+// resumes with the chunk's later planes, tested at the new iterate; the pass
+// result is retracted at the end.
 __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, const float4* pl, f3 ypass,
                            f3& y_out, float& Dmax) {
     Walk<double> W;
     walk_begin(W, ypass);
+    float4 Plast = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);   // no plane visited yet (a NaN)
     for (int pos = 0; pos < m; pos += 32) {
         const int e = pos + lane;
         const float4 P = (e < m) ? pl[sb.idx[0][e]] : make_float4(0.f, 0.f, 0.f, 0.f);
         int lo = 0;   // lanes below lo are already behind the walk
         for (;;) {
-            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f;
+            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f && !same_bits(P, Plast);
             const unsigned bal = __ballot_sync(FULL, viol);
             if (!bal) break;
             const int f = __ffs(bal) - 1;
             const float4 Pf = make_float4(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f),
                                           __shfl_sync(FULL, P.z, f), __shfl_sync(FULL, P.w, f));
             walk_visit_warp(W, Pf, c.p.eps, c.p.eps_dep, lane);
+            Plast = Pf;
             lo = f + 1;
         }
     }
-    y_out = W.y;
     Dmax = sqrtf(W.dmax2);
+    walk_end(W, c.p.eps);
+    y_out = W.y;
     return W.nv;
 }
 
@@ -1910,9 +1941,10 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
             bool first = true;
             for (;;) {
                 Tup best = tup_none();
+                const float4 Pcur = tup_plane(cur);
                 for (int j = 0; j < np; ++j) {
                     const float4 P = pl[j];
-                    if (rho_at(W.y, P) < 0.f) {
+                    if (rho_at(W.y, P) < 0.f && (first || !same_bits(P, Pcur))) {
                         const Tup t = make_tup(rho_at(y0, P), P, j);
                         if ((first || tless(cur, t)) && tless(t, best)) best = t;
                     }
@@ -1922,6 +1954,7 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
                 first = false;
                 walk_visit(W, tup_plane(best), c.p.eps, c.p.eps_dep);
             }
+            walk_end(W, c.p.eps);
             atomicAdd(&bc.glob_pass, 1u);
             atomicAdd(&bc.nviol, (unsigned)W.nv);
             ypass = W.y;
@@ -2445,10 +2478,12 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
 
 // persistent blocks of k_project_short per SM (128 threads each): as many as
 // are resident at once, found by configure_kernels
-static int g_short_blocks_per_sm = 4;
-#define SHORT_BLOCKS_PER_SM g_short_blocks_per_sm
-static int g_heavy_blocks_per_sm = 4;
-#define HEAVY_BLOCKS_PER_SM g_heavy_blocks_per_sm
+// (atomic: contexts may be created, and the static projection set up, on
+// other threads while launches read them)
+static std::atomic<int> g_short_blocks_per_sm{4};
+#define SHORT_BLOCKS_PER_SM g_short_blocks_per_sm.load(std::memory_order_relaxed)
+static std::atomic<int> g_heavy_blocks_per_sm{4};
+#define HEAVY_BLOCKS_PER_SM g_heavy_blocks_per_sm.load(std::memory_order_relaxed)
 
 cudaError_t configure_kernels() {
     cudaError_t e = cudaFuncSetAttribute(k_project_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2457,11 +2492,11 @@ cudaError_t configure_kernels() {
         e = cudaFuncSetAttribute(k_project_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJ_SMEM);
     int nb = 0;
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_short<true>, 128, 0);
-    if (e == cudaSuccess && nb > 0) g_short_blocks_per_sm = nb;
+    if (e == cudaSuccess && nb > 0) g_short_blocks_per_sm.store(nb, std::memory_order_relaxed);
     nb = 0;
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_heavy<true>, PROJ_WARPS * 32, PROJ_SMEM);
-    if (e == cudaSuccess && nb > 0) g_heavy_blocks_per_sm = nb;
+    if (e == cudaSuccess && nb > 0) g_heavy_blocks_per_sm.store(nb, std::memory_order_relaxed);
     return e;
 }
 

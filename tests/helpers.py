@@ -59,22 +59,26 @@ def band_vertices_valid(orc, sc, P, x_build, y, band_mask, L, tol_rel=1e-5, step
     halted (y equal to its build position, bitwise) or satisfy every plane of
     its oracle region, except planes of band pairs, within the final-check
     tolerance tau plus tol_rel L (the plane parity bar), and move at most
-    step_bound when given.  Returns the list of violating vertex ids."""
+    step_bound when given (plus the binary32 rounding of the positions).
+    Returns a list of (vertex, reason, amount) for the violations."""
     x_build = np.asarray(x_build, np.float64)
     R = orc.build_regions(x_build, sc.x, sc.edges, sc.tris, P)
     r2 = 2.0 * P.r
+    u32 = 2.0 ** -24
     bad = []
     for v in np.nonzero(band_mask & (sc.x[:, 3] > 0))[0]:
         d = y[v] - x_build[v]
         if np.all(d == 0.0):
             continue
-        if step_bound is not None and np.linalg.norm(d) > step_bound * (1 + 1e-6):
-            bad.append(int(v))
-            continue
+        if step_bound is not None:
+            slack = 1e-6 * step_bound + 4 * u32 * (np.abs(x_build[v]).sum() + step_bound)
+            if np.linalg.norm(d) > step_bound + slack:
+                bad.append((int(v), "step", float(np.linalg.norm(d) - step_bound)))
+                continue
         o0, o1 = R["offs"][v], R["offs"][v + 1]
         keep = np.abs(R["phi"][o0:o1] - r2) > P.band
         pl = R["planes"][o0:o1][keep]
         rho = pl[:, :3] @ d + pl[:, 3]
         if len(rho) and rho.min() < -(P.tau_feas + tol_rel * L):
-            bad.append(int(v))
+            bad.append((int(v), "plane", float(rho.min())))
     return bad

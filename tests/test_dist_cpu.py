@@ -36,7 +36,7 @@ def _worker(rank, ws, port, out):
 def test_two_rank_gloo_bookkeeping():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
     assert out[0][0] == out[1][0] == 150.0

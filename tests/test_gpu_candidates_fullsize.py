@@ -1,0 +1,57 @@
+"""Exact candidate sets at the benchmarked sizes: the 262,144-vertex cloth
+stack and the 1,201,202-vertex wires, in the launch configuration bench.py
+times (one context per scene, default tuning).
+
+The candidate predicate (padded-AABB overlap in binary32 with the pair
+filters of Alg. 3) is evaluated on both sides on the same binary32
+positions: by the GPU's grid emission (ccfr_get_candidates) and by the
+oracle's sort-and-sweep (orc_candidates, OpenMP over the queries).  The
+vertex-face and edge-edge sets must be equal after sorting, bit for bit, at
+the initial state and again after one full substep on the GPU (the oracle
+then reads the GPU's positions)."""
+import numpy as np
+import pytest
+
+from paper_2607_26901_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26901_b300 import ccfr  # noqa: E402
+
+
+def _sorted_on_device(pairs: np.ndarray, n_second: int) -> np.ndarray:
+    """Lexicographic sort of (a, b) pairs (torch on the GPU; plain ordering)."""
+    if len(pairs) == 0:
+        return pairs.reshape(-1, 2)
+    t = torch.as_tensor(pairs.astype(np.int64)).cuda()
+    key = t[:, 0] * (n_second + 1) + t[:, 1]
+    order = torch.argsort(key)
+    return t[order].cpu().numpy().astype(np.int32)
+
+
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_candidate_sets_bit_exact_at_bench_size(orc, cfg):
+    sc = S.config(cfg)
+    x = torch.as_tensor(sc.x).cuda().contiguous()
+    v = torch.as_tensor(sc.v).cuda().contiguous()
+    ctx = ccfr.Context.from_scene(sc)
+    n_second = max(len(sc.tris), len(sc.edges), sc.n_verts)
+    for stage in ("initial state", "after one substep"):
+        got = ctx.candidates(x, cap=1 << 24)
+        xs = x.cpu().numpy()
+        ref = orc.candidates(xs, sc.edges, sc.tris, sc.params["pad"])
+        for k in ("vf", "ee", "vv"):
+            g = _sorted_on_device(np.asarray(got[k]).reshape(-1, 2), n_second)
+            r = ref[k].reshape(-1, 2)
+            assert g.shape == r.shape, (stage, k, g.shape, r.shape)
+            assert np.array_equal(g, r), (stage, k)
+        assert len(ref["ee"]) > 0
+        if stage == "initial state":
+            ctx.step(x, v)
+            st = ctx.stats()
+            assert st["status"] == 0 and st["iterations"] == sc.params["iters"]
+    ctx.close()

@@ -3,7 +3,8 @@ per scene, default tuning): the 262,144-vertex cloth stack and the
 1,201,202-vertex wires.  The oracle cannot run these whole, so (a) properties
 that hold at any size are checked on every vertex, and (b) sampled vertices
 are projected by the oracle on the GPU's own planes and compared within
-1e-5 L (band cases excluded, as in the small parity tests)."""
+1e-5 L (band cases excluded, as in the small parity tests, and checked to be
+valid outcomes)."""
 import numpy as np
 import pytest
 
@@ -74,7 +75,9 @@ def test_full_regions_and_sampled_projection(full, orc):
     xp = xg.cpu().numpy()[sample, :3].astype(np.float64)
     offs = np.concatenate([[0], np.cumsum(count[sample])]).astype(np.int64)
     flat = np.concatenate([planes[i, :count[vtx]] for i, vtx in enumerate(sample)])
-    keys = np.arange(len(flat), dtype=np.uint64)       # ties broken by slot, as on the GPU
+    # exact FP64 key ties are bitwise-identical planes, whose order does not
+    # change the result (near-ties of distinct planes are band cases)
+    keys = np.arange(len(flat), dtype=np.uint64)
     P = orc.make_params(sc.params, band=BAND_REL * L, capacity=0)
     out, halt, band, nviol = orc.project(xb, xp, np.ones(len(sample)), offs, flat, keys, None, P)
     ok = band == 0
@@ -82,4 +85,11 @@ def test_full_regions_and_sampled_projection(full, orc):
     assert (nviol > 0).sum() > 0
     assert ok.mean() > 0.3 and ok.sum() >= 100
     bad = np.nonzero(ok & (err > TOL_REL * L))[0]
-    assert len(bad) <= max(1, int(0.005 * len(sample))), [(int(sample[b]), float(err[b])) for b in bad[:5]]
+    assert len(bad) == 0, [(int(sample[b]), float(err[b])) for b in bad[:5]]
+    # excluded (band) vertices: halted at the build position or inside every plane
+    for i in np.nonzero(~ok)[0]:
+        d = got[i] - xb[i]
+        if np.all(d == 0.0):
+            continue
+        p = flat[offs[i]:offs[i + 1]]
+        assert (p[:, :3] @ d + p[:, 3]).min() >= -(P.tau_feas + TOL_REL * L), int(sample[i])

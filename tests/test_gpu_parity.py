@@ -8,13 +8,16 @@ distance dist carries a binary32 error ~ u * size / dist, so the bound is
 stated where the projection uses the plane: within |x' - x| <= 2r); projected
 and stepped positions within 1e-5 L per coordinate (L = scene bounding-box
 diagonal), excluding only vertices whose decisions the oracle reports inside
-a decision band (|rho| or |phi - 2r| within BAND_REL L, dependence tests
-within a factor 10 of eps_dep, near-tied sort keys of distinct planes)."""
+a decision band (|rho| or |phi - 2r| within BAND_REL L where the decision
+can change the result, dependence tests within a factor 10 of eps_dep,
+near-tied sort keys of distinct planes); each excluded vertex must still be a
+valid outcome (halted at its build position, or inside every plane of its
+oracle region within tau + 1e-5 L, and within the step bound in a step)."""
 import numpy as np
 import pytest
 
 from paper_2607_26901_b300 import scenes as S
-from tests.helpers import csr_to_padded, dev_scene, gpu_regions_by_vertex, sort_pairs
+from tests.helpers import band_vertices_valid, csr_to_padded, dev_scene, gpu_regions_by_vertex, sort_pairs
 
 pytestmark = pytest.mark.gpu
 
@@ -192,6 +195,9 @@ def test_project_parity_on_oracle_planes(orc, name):
     bad = np.nonzero(ok & (err > TOL_REL * L))[0]
     assert len(bad) == 0, [(int(b), float(err[b]), int(nviol[b]), int(halt[b]), int(cnt[b])) for b in bad[:5]]
     np.testing.assert_array_equal(h.cpu().numpy()[ok], halt[ok])
+    # band-excluded vertices: a valid outcome (halted at x, or inside every plane)
+    invalid = band_vertices_valid(orc, sc, P, x3, got, band != 0, L)
+    assert not invalid, invalid[:10]
     ctx.close()
 
 
@@ -219,6 +225,8 @@ def test_build_and_project_parity(orc, name):
     assert len(bad) == 0, [(int(b), float(err[b]), int(nviol[b]), int(halt[b])) for b in bad[:5]]
     viol = nviol > 0
     assert (viol & ok).sum() >= 0.5 * viol.sum()
+    invalid = band_vertices_valid(orc, sc, P, x3, got, ~ok, L)
+    assert not invalid, invalid[:10]
     ctx.close()
 
 
@@ -245,6 +253,10 @@ def test_single_iteration_step_parity(orc, name):
     assert err <= TOL_REL * L, (err, TOL_REL * L, int((~ok).sum()))
     gv = v.cpu().numpy()[:, :3].astype(np.float64)
     assert np.abs(gv - vo)[ok].max() <= TOL_REL * L / sc.params["dt"]
+    P = orc.make_params(sc.params, band=BAND_REL * L, iters=1, capacity=capacity_for(sc))
+    invalid = band_vertices_valid(orc, sc, P, sc.x[:, :3].astype(np.float64), got, ~ok, L,
+                                  step_bound=sc.params["r"])
+    assert not invalid, invalid[:10]
     ctx.close()
 
 
@@ -258,10 +270,8 @@ def test_full_step_parity_config1(orc):
     ctx.step(x, v)
     got = x.cpu().numpy()[:, :3].astype(np.float64)
     err_all = np.abs(got - xo).max(axis=1)
-    if not info.any_band:
-        assert err_all.max() <= TOL_REL * L
-    else:
-        assert err_all[vband == 0].max() <= TOL_REL * L or np.mean(err_all <= TOL_REL * L) > 0.99
+    assert err_all[vband == 0].max() <= TOL_REL * L
+    assert (vband != 0).sum() <= 0.01 * sc.n_verts
     ctx.close()
 
 

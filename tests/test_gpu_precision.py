@@ -99,15 +99,18 @@ def test_precision_small_stack_one_iteration(orc):
     assert line["max_err_rel"] <= TOL_REL
 
 
-def test_precision_small_stack_full_substep(orc):
-    """20 iterations of the chaotic stack: a decision taken differently in
-    binary32 and in FP64 (a violation test, a halt, the order of
-    near-duplicate planes whose binary32 sort keys tie) changes that vertex's
-    later iterates by up to the step bound.  The median stays at the
-    rounding level; the bar is met by at least 99% of the vertices."""
+def test_precision_small_stack_full_substep_report(orc):
+    """20 iterations of the chaotic stack compared in one shot (report only):
+    a decision taken differently in binary32 and in FP64 inside a band (a
+    violation test, a halt, a dependence test) changes that vertex's later
+    iterates by up to the step bound, and the difference spreads through the
+    XPBD sweep and the regions of later iterations.  The substep itself is
+    asserted iteration by iteration in tests/test_gpu_iterations.py, each
+    iteration replayed by the oracle from the GPU's own state.  Here only the
+    median, which stays at the rounding level, is asserted."""
     sc = S.cloth_stack(n_side=24, layers=4, seed=2, plane_capacity=1024)
-    line = full_step_error(orc, sc, "cloth_stack 4x24x24, full substep")
-    assert line["frac_within"] >= 0.99 and line["median_err_rel"] <= 1e-7
+    line = full_step_error(orc, sc, "cloth_stack 4x24x24, full substep (one-shot report)")
+    assert line["median_err_rel"] <= 1e-7
 
 
 def test_precision_small_wires(orc):
@@ -157,8 +160,10 @@ def test_precision_full_size_sampled_projection(orc, cfg):
     noise = torch.as_tensor(rng.normal(scale=0.6 * sc.params["r"], size=(sc.n_verts, 3)).astype(np.float32)).cuda()
     xg[:, :3] += noise * (xg[:, 3:4] > 0)
     xio = xg.clone()
-    ctx.project(x, xio)
+    hg = torch.zeros(sc.n_verts, dtype=torch.uint8, device="cuda")
+    ctx.project(x, xio, hg)
     got = xio.cpu().numpy()[sample, :3].astype(np.float64)
+    hgot = hg.cpu().numpy()[sample]
     xb = x.cpu().numpy()[sample, :3].astype(np.float64)
     xp = xg.cpu().numpy()[sample, :3].astype(np.float64)
     offs = np.concatenate([[0], np.cumsum(count[sample])]).astype(np.int64)
@@ -168,10 +173,20 @@ def test_precision_full_size_sampled_projection(orc, cfg):
     out, halt, band, nviol = orc.project(xb, xp, np.ones(len(sample)), offs, flat, keys, None, P)
     ctx.close()
     ok = band == 0
-    err = np.abs(got - out).max(axis=1)[ok] / L
+    err_all = np.abs(got - out).max(axis=1) / L
+    err = err_all[ok]
+    miss = np.nonzero(ok & (err_all > TOL_REL))[0]
     name = "cloth_stack 4x256x256" if cfg == 2 else "wires 128x128x64"
     line = report(f"{name}, sampled projection after one substep", err, ok.sum(), (~ok).sum(),
-                  {"verts": sc.n_verts, "sample": int(len(sample))})
-    # the oracle breaks equal sort keys by slot here; a handful of vertices whose
-    # walks meet equal keys on distinct planes may differ beyond the bar
-    assert np.mean(err <= TOL_REL) >= 0.995
+                  {"verts": sc.n_verts, "sample": int(len(sample)),
+                   "misses": [{"vertex": int(sample[i]), "err_rel": float(err_all[i]), "planes": int(count[sample[i]]),
+                               "nviol": int(nviol[i]), "halt_oracle": int(halt[i]), "halt_gpu": int(hgot[i])}
+                              for i in miss[:10]]})
+    assert len(miss) == 0, line["misses"]
+    # excluded (band) vertices: halted at the build position or inside every plane
+    for i in np.nonzero(~ok)[0]:
+        d = got[i] - xb[i]
+        if np.all(d == 0.0):
+            continue
+        p = flat[offs[i]:offs[i + 1]]
+        assert (p[:, :3] @ d + p[:, 3]).min() >= -(P.tau_feas + TOL_REL * L), int(sample[i])

@@ -2,17 +2,18 @@
 that those pins catch plausible mistakes.
 
 - Hand-derived multi-plane cases (tests/golden/alg2_multiplane.json): the
-  visiting order (ascending rho at the input), the retraction after every
-  Alg. 1 call, the n_max + 1 pass budget ending in the halt, and the return of
-  an unviolated candidate unchanged.
+  corner point of Alg. 1 followed by one retraction per pass, the visiting
+  order (ascending rho at the input), the n_max + 1 pass budget, the halt when
+  a fourth violated plane meets three stored lines, and the return of an
+  unviolated candidate unchanged.
 - Three mutually perpendicular planes: the result is the corner point of
   Alg. 1 (the exact closest point of the region, Sec. 3.2) moved by at most a
   few retractions of eps, inside every plane.
 - Mutations: each plausible mistake in a copy of the oracle's Alg. 2 / Alg. 1
-  (descending sort, one retraction per pass, n_max passes, no halt fallback,
-  retraction measured from the pass input, the auxiliary point of Alg. 1
-  started from the iterate, the sort key taken at the build position) makes
-  at least one pin fail.
+  (descending sort, a retraction after every Alg. 1 call, n_max passes, no
+  halt fallback, retraction measured from the pass input, the sort key taken
+  at the build position, Alg. 1's first dependence measure on the first
+  stored line) makes at least one pin fail.
 """
 import json
 from pathlib import Path
@@ -101,10 +102,25 @@ def test_alg2_three_plane_corner(orc):
     check_three_plane_corner(orc)
 
 
-RETRACT_EACH_CALL = """            double dn[3];
+RETRACT_ONCE_PER_PASS = """        }
+        /* R9: the pass result (the projected boundary position) is retracted
+         * once by eps towards the build position x, or reset to x when it is
+         * closer to x than eps (Sec. 3.2) */
+        if (nv > 0) {
+            double dn[3];
             sub3(xt, x, dn);
             double L = norm3(dn);
             if (fabs(L - P->eps) <= P->band) *band = 1;
+            if (L > P->eps) {
+                for (int i = 0; i < 3; ++i) xt[i] = x[i] + (L - P->eps) * dn[i] / L;
+            } else {
+                for (int i = 0; i < 3; ++i) xt[i] = x[i];
+            }
+        }
+        if (pass == 0) *nviol = nv;"""
+RETRACT_EACH_CALL = """            double dn[3];
+            sub3(xt, x, dn);
+            double L = norm3(dn);
             if (L > P->eps) {
                 for (int i = 0; i < 3; ++i) xt[i] = x[i] + (L - P->eps) * dn[i] / L;
             } else {
@@ -116,24 +132,12 @@ RETRACT_EACH_CALL = """            double dn[3];
 MUTATIONS = {
     "sort descending": [("    if (p->rho < q->rho) return -1;\n    if (p->rho > q->rho) return 1;",
                          "    if (p->rho > q->rho) return -1;\n    if (p->rho < q->rho) return 1;")],
-    "one retraction per pass": [(RETRACT_EACH_CALL, """        }
-        if (nv > 0) {
-            double dn[3];
-            sub3(xt, x, dn);
-            double L = norm3(dn);
-            if (L > P->eps) {
-                for (int i = 0; i < 3; ++i) xt[i] = x[i] + (L - P->eps) * dn[i] / L;
-            } else {
-                for (int i = 0; i < 3; ++i) xt[i] = x[i];
-            }
-        }
-        if (pass == 0) *nviol = nv;""")],
+    "retraction after every Alg. 1 call": [(RETRACT_ONCE_PER_PASS, RETRACT_EACH_CALL)],
     "n_max passes": [("pass < P->n_max + 1; ++pass", "pass < P->n_max; ++pass")],
     "no halt fallback": [("    if (halted) { xp[0] = x[0]; xp[1] = x[1]; xp[2] = x[2]; }", "")],
-    "retraction from the pass input": [(RETRACT_EACH_CALL, RETRACT_EACH_CALL.replace(
+    "retraction from the pass input": [(RETRACT_ONCE_PER_PASS, RETRACT_ONCE_PER_PASS.replace(
         "sub3(xt, x, dn);", "sub3(xt, x0, dn);").replace("xt[i] = x[i] + (L", "xt[i] = x0[i] + (L").replace(
         "for (int i = 0; i < 3; ++i) xt[i] = x[i];", "for (int i = 0; i < 3; ++i) xt[i] = x0[i];"))],
-    "Alg. 1 w from the iterate": [("wv[i] = x0[i] + n[i];", "wv[i] = xt[i] + n[i];")],
     "sort key at the build position": [("ord[k].rho = dot3(y, planes4 + 4 * k) + planes4[4 * k + 3];",
                                         "ord[k].rho = planes4[4 * k + 3];")],
     "Alg. 1 beta_u on the first line": [("double beta_u = dot3(dn, S->V[m - 1]);",
