@@ -298,6 +298,14 @@ ccfr_status ccfr_project_static(const float* x, float* x_io, const float* planes
 ccfr_status ccfr_create_batch(const ccfr_mesh* meshes, const ccfr_params* params, int n_scenes, void* stream,
                               ccfr_ctx** out);
 
+/* One substep of a batched context in which only the scenes whose byte in
+ * `active` (device, n_scenes bytes, scene order of ccfr_create_batch) is
+ * nonzero advance; the others keep their positions and velocities bitwise.
+ * Each active scene's result equals ccfr_step of that scene alone.  (A serving
+ * loop steps the scenes that have a request due in one launch.)  Returns
+ * CCFR_ERR_INVALID_ARG for a context not made by ccfr_create_batch. */
+ccfr_status ccfr_step_active(ccfr_ctx* ctx, float* x, float* v, const unsigned char* active, void* stream);
+
 /* Performance knobs: grid cell size in mean padded primitive extents and
  * emission blocks per SM (no effect on results), and plane capacity (a
  * multiple of 32; changing it reallocates the plane lists; results change
@@ -339,6 +347,7 @@ typedef struct ccfr_server ccfr_server;
 typedef struct {
     long scenes, requests, done, failed, admissions, evictions;
     size_t resident_bytes, peak_resident_bytes, budget_bytes;
+    long pools, pool_launches;     /* batching: pools formed, batched launches issued */
 } ccfr_server_info;
 
 ccfr_status ccfr_server_create(size_t hbm_budget_bytes, int n_slots, double timeout_s, ccfr_server** out);
@@ -353,6 +362,17 @@ ccfr_status ccfr_server_submit(ccfr_server* sv, int scene_id, double t_arrival, 
 /* Before start: admit registered scenes, in order, while the resident bytes
  * stay within `fraction` of the budget (first requests then skip admission). */
 ccfr_status ccfr_server_preload(ccfr_server* sv, double fraction, int* n_admitted);
+/* Continuous batching (before ccfr_server_start or _preload): scenes of at
+ * most max_scene_verts vertices whose settings agree except for r, xi, delta
+ * and pad are grouped, in registration order, into pools of at most
+ * max_pool_verts vertices (and 2048 scenes), each resident as one batched
+ * context (ccfr_create_batch) and admitted or evicted as a unit.  A pool's
+ * launch steps, in one graph-captured substep (ccfr_step_active), every member
+ * with a request due when the launch starts (its oldest one); requests that
+ * arrive while the pool is on the GPU join its next launch.  Larger scenes are
+ * served alone as before.  Results are those of ccfr_step alone.  The stall
+ * test hook applies to scenes served alone.  0 vertices: no batching. */
+ccfr_status ccfr_server_set_batching(ccfr_server* sv, int max_pool_verts, int max_scene_verts);
 ccfr_status ccfr_server_start(ccfr_server* sv);
 /* Wait (at most timeout_s) until every submitted request is done. */
 ccfr_status ccfr_server_wait(ccfr_server* sv, double timeout_s, long* n_done);

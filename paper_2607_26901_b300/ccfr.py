@@ -73,7 +73,8 @@ class Tuning(C.Structure):
 
 class ServerInfo(C.Structure):
     _fields_ = [(n, C.c_long) for n in ("scenes", "requests", "done", "failed", "admissions", "evictions")] + \
-               [(n, C.c_size_t) for n in ("resident_bytes", "peak_resident_bytes", "budget_bytes")]
+               [(n, C.c_size_t) for n in ("resident_bytes", "peak_resident_bytes", "budget_bytes")] + \
+               [(n, C.c_long) for n in ("pools", "pool_launches")]
 
     def as_dict(self) -> dict:
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -100,6 +101,7 @@ def lib():
             "ccfr_step_host": [P, P, P, P],
             "ccfr_step_timed": [P, P, P, P, C.c_int, P],
             "ccfr_step_record": [P, P, P, P, P, P],
+            "ccfr_step_active": [P, P, P, P, P],
             "ccfr_get_candidates": [P, P, P, C.c_long, P, C.c_long, P, C.c_long, P, P],
             "ccfr_copy_regions": [P, P, P, P, P, P],
             "ccfr_load_regions": [P, P, P, C.c_int, P],
@@ -115,6 +117,7 @@ def lib():
             "ccfr_server_add_scene": [P, C.c_int, C.c_int, C.c_int, P, P, P, P, C.POINTER(Params), C.POINTER(C.c_int)],
             "ccfr_server_submit": [P, C.c_int, C.c_double, C.POINTER(C.c_long)],
             "ccfr_server_start": [P],
+            "ccfr_server_set_batching": [P, C.c_int, C.c_int],
             "ccfr_server_preload": [P, C.c_double, C.POINTER(C.c_int)],
             "ccfr_server_wait": [P, C.c_double, C.POINTER(C.c_long)],
             "ccfr_server_results": [P, C.c_long, P, P, P, P],
@@ -139,10 +142,11 @@ def lib():
 
 def exported_symbols() -> list[str]:
     return ["ccfr_create", "ccfr_create_ext", "ccfr_destroy", "ccfr_build_regions", "ccfr_project", "ccfr_step",
-            "ccfr_step_host", "ccfr_step_timed", "ccfr_step_record", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
+            "ccfr_step_host", "ccfr_step_timed", "ccfr_step_record", "ccfr_step_active", "ccfr_stage_name", "ccfr_get_candidates", "ccfr_copy_regions", "ccfr_load_regions",
             "ccfr_get_info", "ccfr_get_stats", "ccfr_reset_stats", "ccfr_status_string",
             "ccfr_project_static", "ccfr_create_batch", "ccfr_set_tuning", "ccfr_get_tuning", "ccfr_autotune",
             "ccfr_server_create", "ccfr_server_add_scene", "ccfr_server_submit", "ccfr_server_start",
+            "ccfr_server_set_batching",
             "ccfr_server_preload",
             "ccfr_server_wait", "ccfr_server_results", "ccfr_server_get_state", "ccfr_server_get_info",
             "ccfr_server_set_stall", "ccfr_server_stop", "ccfr_server_destroy", "ccfr_estimate_bytes"]
@@ -316,6 +320,11 @@ class Context:
     def step(self, x, v, stream=None):
         _check(lib().ccfr_step(self.h, _ptr(x), _ptr(v), _stream(stream)), "ccfr_step")
 
+    def step_active(self, x, v, active, stream=None):
+        """ccfr_step_active: step only the scenes whose byte in `active`
+        (uint8 CUDA tensor, one per scene) is nonzero (batched contexts)."""
+        _check(lib().ccfr_step_active(self.h, _ptr(x), _ptr(v), _ptr(active), _stream(stream)), "ccfr_step_active")
+
     def step_timed(self, x, v, stream=None) -> dict:
         """One step launched kernel by kernel; returns {stage: ms}."""
         n = 17
@@ -422,6 +431,12 @@ class Server:
         rid = C.c_long()
         _check(lib().ccfr_server_submit(self.h, scene_id, t_arrival, C.byref(rid)), "ccfr_server_submit")
         return rid.value
+
+    def set_batching(self, max_pool_verts: int, max_scene_verts: int):
+        """Continuous batching: small scenes grouped into pools stepped by one
+        batched launch each (ccfr_server_set_batching)."""
+        _check(lib().ccfr_server_set_batching(self.h, int(max_pool_verts), int(max_scene_verts)),
+               "ccfr_server_set_batching")
 
     def preload(self, fraction: float = 0.9) -> int:
         n = C.c_int()

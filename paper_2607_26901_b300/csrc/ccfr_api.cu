@@ -50,6 +50,7 @@ struct ccfr_ctx {
     unsigned long long* pair_count = nullptr;
     std::vector<void*> allocs;
     int n_scenes = 1;
+    unsigned char* active = nullptr;   // per-scene step mask of a batched context (all 1 between calls)
 };
 
 namespace {
@@ -378,10 +379,12 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     if (!vscene.empty()) {
         ok &= dalloc(c, &dscene, vscene.size()) == cudaSuccess;
         ok &= dalloc(c, &dsp, sparams.size()) == cudaSuccess;
+        ok &= dalloc(c, &c->active, sparams.size()) == cudaSuccess;
     }
     if (!ok) { cudaGetLastError(); free_ctx(c); return CCFR_ERR_OOM; }
     d.vscene = dscene;
     d.sparams = dsp;
+    d.active = c->active;
     c->n_scenes = vscene.empty() ? 1 : (int)sparams.size();
     d.edges = edges;
     d.edges_col = edges_col;
@@ -417,6 +420,7 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
         err = cudaMemcpyAsync(dscene, vscene.data(), vscene.size() * sizeof(unsigned short), cudaMemcpyHostToDevice, st);
         if (err == cudaSuccess)
             err = cudaMemcpyAsync(dsp, sparams.data(), sparams.size() * sizeof(float4), cudaMemcpyHostToDevice, st);
+        if (err == cudaSuccess) err = cudaMemsetAsync(c->active, 1, sparams.size(), st);
     }
     if (err == cudaSuccess) err = cudaMemsetAsync(d.flags, 0, 2 * sizeof(int), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(d.stats, 0, sizeof(DevStats), st);
@@ -657,6 +661,20 @@ ccfr_status ccfr_step(ccfr_ctx* c, float* x, float* v, void* stream) {
     }
     cudaError_t err = cudaGraphLaunch(exec, st);
     c->regions_valid = true;
+    return from_cuda(err);
+}
+
+ccfr_status ccfr_step_active(ccfr_ctx* c, float* x, float* v, const unsigned char* active, void* stream) {
+    if (!c || !active) return CCFR_ERR_INVALID_ARG;
+    if (!c->active) return CCFR_ERR_INVALID_ARG;           // not a batched context
+    DeviceGuard g(c->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t err = cudaMemcpyAsync(c->active, active, (size_t)c->n_scenes, cudaMemcpyDeviceToDevice, st);
+    if (err != cudaSuccess) return CCFR_ERR_CUDA;
+    ccfr_status s = ccfr_step(c, x, v, stream);
+    // back to "every scene" for the next ccfr_step
+    err = cudaMemsetAsync(c->active, 1, (size_t)c->n_scenes, st);
+    if (s != CCFR_OK) return s;
     return from_cuda(err);
 }
 

@@ -139,6 +139,9 @@ struct DevCtx {
     // every vertex and each scene's (r, 2r, xi, pad); null for a single scene
     const unsigned short* vscene;
     const float4* sparams;
+    // per-scene step mask (ccfr_step_active): a scene whose byte is 0 is left
+    // unchanged by the substep (positions and velocities); null: all scenes
+    const unsigned char* active;
     int4* work;                 // [n_verts] vertices queued for the second projection kernels:
                                 //   long plane lists from the front, short ones from the back
     unsigned* work_count;       // [2] queue lengths: long lists, short lists
@@ -214,6 +217,9 @@ __device__ __forceinline__ unsigned pack_scene(unsigned packed) { return packed 
 // Per-scene parameters of the narrow phase and the clamp.
 struct SceneParams { float r, two_r, xi, pad; };
 __device__ __forceinline__ unsigned scene_of(const DevCtx& c, int v) { return c.vscene ? c.vscene[v] : 0u; }
+__device__ __forceinline__ bool vertex_active(const DevCtx& c, int v) {
+    return !c.active || c.active[scene_of(c, v)] != 0;
+}
 __device__ __forceinline__ SceneParams scene_params(const DevCtx& c, unsigned s) {
     SceneParams q;
     if (c.sparams) {

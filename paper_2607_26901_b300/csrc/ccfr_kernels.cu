@@ -91,8 +91,9 @@ __global__ void k_extent(DevCtx c, const float4* __restrict__ x) {
         unsigned sc;
         int kind = item_box(c, x, i, lo, hi, id, sc);
         float m = fmaxf(fmaxf(hi[0] - lo[0], hi[1] - lo[1]), hi[2] - lo[2]);
+        if (c.active && !c.active[sc]) m = 0.f;   // paused scene (ccfr_step_active): not in the grid
         // positive floats order as integers; the sum is fixed-point (nm) so it is order-independent
-        if (m == m && m < 1e6f && kind < 3) {
+        if (m == m && m > 0.f && m < 1e6f && kind < 3) {
             e[kind] = __float_as_uint(m);
             sum[kind] = (u64)(m * 1e9f + 0.5f);
         }
@@ -135,6 +136,7 @@ __global__ void k_bucket_count(DevCtx c, const float4* __restrict__ x) {
     unsigned sc;
     bool immobile;
     int kind = item_box(c, x, i, lo, hi, id, sc, &immobile);
+    if (c.active && !c.active[sc]) return;   // paused scene (ccfr_step_active): not in the grid
     if (kind <= KIND_EDGE && !fits_cell(lo, hi, cell_size_of(c, kind))) {
         unsigned s = atomicAdd(&c.big_count[kind], 1u);
         unsigned o = c.big_base[kind] + s;
@@ -159,6 +161,7 @@ __global__ void k_bucket_scatter(DevCtx c, const float4* __restrict__ x) {
     unsigned sc;
     bool immobile;
     int kind = item_box(c, x, i, lo, hi, id, sc, &immobile);
+    if (c.active && !c.active[sc]) return;
     if (kind == KIND_TRI && !fits_cell(lo, hi, cell_size_of(c, kind))) return;
     kind = table_of(c, kind, lo, hi, immobile);
     unsigned packed;
@@ -1690,7 +1693,7 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
     if (v < c.n_verts) {
         const float4 X = x_b[v];
         const float4 XP = x_in[v];
-        if (X.w > 0.f) {
+        if (X.w > 0.f && (!STEP || vertex_active(c, v))) {
             const unsigned cnt = c.count[v];
             const int np = (int)min(cnt, (unsigned)c.p.K);
             if (cnt > (unsigned)c.p.K || np > SHORT_LIST) {
@@ -2049,7 +2052,7 @@ __global__ void __launch_bounds__(RESP_WARPS * 32) k_response(DevCtx c, const fl
     if (v < c.n_verts) {
         const float4 X = x_b[v];
         const unsigned cnt = c.count[v];
-        if (X.w > 0.f && cnt > 0u && cnt <= (unsigned)c.p.K) {
+        if (X.w > 0.f && cnt > 0u && cnt <= (unsigned)c.p.K && vertex_active(c, v)) {
             const int np = (int)cnt;
             if (np > SHORT_LIST) {
                 warp_job = true;
@@ -2285,7 +2288,7 @@ __global__ void k_predict(DevCtx c, const float4* __restrict__ x, const float4* 
     if (!fin) atomicOr(&c.stats->error_flags, ERR_NONFINITE);
     c.x_n[i] = X;
     float dt = c.p.dt;
-    if (X.w > 0.f) {
+    if (X.w > 0.f && vertex_active(c, i)) {
         X.x = X.x + dt * V.x + dt * dt * c.p.gx;
         X.y = X.y + dt * V.y + dt * dt * c.p.gy;
         X.z = X.z + dt * V.z + dt * dt * c.p.gz;
@@ -2312,6 +2315,7 @@ __global__ void k_xpbd_color(DevCtx c, int e0, int e1) {
     int i = e0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= e1) return;
     int2 e = c.edges_col[i];
+    if (!vertex_active(c, e.x)) return;
     float4 A = c.x_s[e.x], B = c.x_s[e.y];
     float at = c.alpha_col[i];
     float wsum = A.w + B.w + at;
@@ -2336,6 +2340,7 @@ __global__ void k_xpbd_tet_color(DevCtx c, int q0, int q1) {
     int i = q0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= q1) return;
     const int4 T = c.tets_col[i];
+    if (!vertex_active(c, T.x)) return;
     const float4 X0 = c.x_s[T.x], X1 = c.x_s[T.y], X2 = c.x_s[T.z], X3 = c.x_s[T.w];
     const f3 e1 = sub(xyz(X1), xyz(X0)), e2 = sub(xyz(X2), xyz(X0)), e3 = sub(xyz(X3), xyz(X0));
     const f3 g1 = cross(e2, e3), g2 = cross(e3, e1), g3 = cross(e1, e2);
@@ -2364,7 +2369,7 @@ __global__ void k_iter_end(DevCtx c, int early_exit) {
 __global__ void k_update(DevCtx c, const float4* __restrict__ x, float4* vel) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) { c.flags[1] = 0; c.stats->steps += 1ull; }
-    if (i >= c.n_verts) return;
+    if (i >= c.n_verts || !vertex_active(c, i)) return;
     float4 X = x[i], N = c.x_n[i];
     float inv = 1.f / c.p.dt;
     vel[i] = make_float4((X.x - N.x) * inv, (X.y - N.y) * inv, (X.z - N.z) * inv, vel[i].w);

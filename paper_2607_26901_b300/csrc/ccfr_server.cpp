@@ -4,11 +4,18 @@
 // thread admits a scene to the device (context + state) when a request for it
 // is due and the HBM budget allows, evicting idle resident scenes (least
 // recently used, state copied back to the host) when it does not.  Up to
-// n_slots steps of different scenes run at once, each on its own stream, so
-// requests that arrive while others are on the GPU start as soon as a slot
-// and memory are free and their work overlaps on the device.  Requests of
-// one scene run in arrival order, one at a time.  Every wait is bounded: a
-// step that does not finish within the timeout is reported as timed out.
+// n_slots steps run at once, each on its own stream, so requests that arrive
+// while others are on the GPU start as soon as a slot and memory are free and
+// their work overlaps on the device.  Requests of one scene run in arrival
+// order, one at a time.  Every wait is bounded: a step that does not finish
+// within the timeout is reported as timed out.
+//
+// Batching (ccfr_server_set_batching): small scenes with the same settings
+// are grouped into pools, each resident as one batched context.  A pool's
+// launch steps, in one graph-captured substep, every member scene that has a
+// request due when the launch starts (ccfr_step_active masks the others);
+// requests that arrive meanwhile join the pool's next launch.  Pools are
+// admitted and evicted as units.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,6 +51,22 @@ struct SceneRec {
     bool stall = false;                // test hook: pretend the step never finishes
     double last_used = 0.0;
     long steps_done = 0;
+    int pool = -1;                     // pool of the scene (batching), or -1
+    int member = -1;                   // its index in the pool
+};
+
+// Scenes stepped together in one batched context.
+struct Pool {
+    std::vector<int> members;          // scene ids, in pool order
+    std::vector<long> voff;            // first vertex of each member in the merged arrays (+ total)
+    ccfr_ctx* ctx = nullptr;
+    float* dx = nullptr;               // merged state (device) while resident
+    float* dv = nullptr;
+    unsigned char* dmask = nullptr;    // per-member step mask (device)
+    std::vector<unsigned char> hmask;
+    size_t bytes = 0;
+    bool busy = false;
+    double last_used = 0.0;
 };
 
 struct Req {
@@ -55,9 +78,12 @@ struct Req {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
-    long req = -1;
+    long req = -1;                     // request of a scene stepped alone
+    int pool = -1;                     // or: the pool launched here and its requests
+    std::vector<long> preqs;
     double t_launch = 0.0;
     bool stalled = false;
+    bool busy() const { return req >= 0 || pool >= 0; }
 };
 
 }  // namespace
@@ -77,6 +103,11 @@ struct ccfr_server {
     double t0 = 0.0;
     long n_done = 0, admissions = 0, evictions = 0, failed = 0;
     long scan_from = 0;
+    // batching
+    int pool_max_verts = 0, pool_scene_max = 0;
+    bool pools_formed = false;
+    long pool_launches = 0;
+    std::vector<Pool> pools;
 };
 
 namespace {
@@ -98,31 +129,200 @@ size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false) {
     return b + (1 << 20);
 }
 
-// Make scene s resident; evict idle scenes if needed.  Called by the worker.
+// Copy a resident pool's state back to its members and release its memory.
+ccfr_status release_pool(ccfr_server* sv, Pool& P) {
+    for (size_t m = 0; m < P.members.size(); ++m) {
+        SceneRec& sc = sv->scenes[P.members[m]];
+        size_t nb = (size_t)sc.n_verts * 4 * sizeof(float);
+        if (cudaMemcpy(sc.x.data(), P.dx + 4 * P.voff[m], nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(sc.v.data(), P.dv + 4 * P.voff[m], nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return CCFR_ERR_CUDA;
+    }
+    ccfr_destroy(P.ctx);
+    cudaFree(P.dx);
+    cudaFree(P.dv);
+    cudaFree(P.dmask);
+    P.ctx = nullptr;
+    P.dx = P.dv = nullptr;
+    P.dmask = nullptr;
+    sv->resident -= P.bytes;
+    sv->evictions++;
+    return CCFR_OK;
+}
+
+// Evict the least recently used idle resident unit (a scene served alone, or
+// a pool), its state copied back to the host.  False when every resident unit
+// is busy (the caller waits).
+bool evict_one(ccfr_server* sv, ccfr_status* err) {
+    *err = CCFR_OK;
+    int vs = -1, vp = -1;
+    double oldest = 1e300;
+    for (int k = 0; k < (int)sv->scenes.size(); ++k) {
+        SceneRec& o = sv->scenes[k];
+        if (o.ctx && !o.busy && o.last_used < oldest) { oldest = o.last_used; vs = k; vp = -1; }
+    }
+    for (int p = 0; p < (int)sv->pools.size(); ++p) {
+        Pool& P = sv->pools[p];
+        if (P.ctx && !P.busy && P.last_used < oldest) { oldest = P.last_used; vp = p; vs = -1; }
+    }
+    if (vp >= 0) {
+        *err = release_pool(sv, sv->pools[vp]);
+        return true;
+    }
+    if (vs < 0) return false;
+    SceneRec& o = sv->scenes[vs];
+    size_t nb = (size_t)o.n_verts * 4 * sizeof(float);
+    if (cudaMemcpy(o.x.data(), o.dx, nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(o.v.data(), o.dv, nb, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        *err = CCFR_ERR_CUDA;
+        return true;
+    }
+    ccfr_destroy(o.ctx);
+    cudaFree(o.dx);
+    cudaFree(o.dv);
+    o.ctx = nullptr;
+    o.dx = o.dv = nullptr;
+    sv->resident -= o.bytes;
+    sv->evictions++;
+    return true;
+}
+
+// Make room for `bytes` more resident bytes.
+ccfr_status make_room(ccfr_server* sv, size_t bytes) {
+    while (sv->resident + bytes > sv->budget) {
+        ccfr_status e;
+        if (!evict_one(sv, &e)) return CCFR_ERR_OOM;   // everything resident is busy: wait
+        if (e != CCFR_OK) return e;
+    }
+    return CCFR_OK;
+}
+
+// Make pool p resident: one batched context over its members (scene-local
+// topology, rest shapes at registration), their current states merged.
+ccfr_status admit_pool(ccfr_server* sv, int p) {
+    Pool& P = sv->pools[p];
+    if (P.ctx) return CCFR_OK;
+    ccfr_status rs = make_room(sv, P.bytes);
+    if (rs != CCFR_OK) return rs;
+    const int M = (int)P.members.size();
+    const long nv = P.voff[M];
+    size_t ne = 0, nt = 0;
+    for (int m = 0; m < M; ++m) {
+        ne += sv->scenes[P.members[m]].edges.size();
+        nt += sv->scenes[P.members[m]].tris.size();
+    }
+    int *de = nullptr, *dt = nullptr;
+    float* dr = nullptr;
+    const size_t nb = (size_t)nv * 4 * sizeof(float);
+    cudaError_t err = cudaMalloc((void**)&dr, nb ? nb : 16);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&de, (ne ? ne : 1) * sizeof(int));
+    if (err == cudaSuccess) err = cudaMalloc((void**)&dt, (nt ? nt : 1) * sizeof(int));
+    if (err == cudaSuccess) err = cudaMalloc((void**)&P.dx, nb ? nb : 16);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&P.dv, nb ? nb : 16);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&P.dmask, (size_t)M);
+    std::vector<ccfr_mesh> meshes((size_t)M);
+    std::vector<ccfr_params> prm((size_t)M);
+    size_t eo = 0, to = 0;
+    for (int m = 0; m < M && err == cudaSuccess; ++m) {
+        const SceneRec& sc = sv->scenes[P.members[m]];
+        const size_t vb = (size_t)sc.n_verts * 4 * sizeof(float), vo = (size_t)P.voff[m] * 4;
+        err = cudaMemcpy(dr + vo, sc.rest.data(), vb, cudaMemcpyHostToDevice);
+        if (err == cudaSuccess) err = cudaMemcpy(P.dx + vo, sc.x.data(), vb, cudaMemcpyHostToDevice);
+        if (err == cudaSuccess) err = cudaMemcpy(P.dv + vo, sc.v.data(), vb, cudaMemcpyHostToDevice);
+        if (err == cudaSuccess && !sc.edges.empty())
+            err = cudaMemcpy(de + eo, sc.edges.data(), sc.edges.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (err == cudaSuccess && !sc.tris.empty())
+            err = cudaMemcpy(dt + to, sc.tris.data(), sc.tris.size() * sizeof(int), cudaMemcpyHostToDevice);
+        meshes[m] = ccfr_mesh{sc.n_verts, sc.n_edges, sc.n_tris, de + eo, dt + to, dr + vo};
+        prm[m] = sc.params;
+        eo += sc.edges.size();
+        to += sc.tris.size();
+    }
+    ccfr_status st = CCFR_OK;
+    if (err == cudaSuccess) st = ccfr_create_batch(meshes.data(), prm.data(), M, nullptr, &P.ctx);
+    cudaFree(de);
+    cudaFree(dt);
+    cudaFree(dr);
+    if (err != cudaSuccess || st != CCFR_OK) {
+        cudaGetLastError();
+        cudaFree(P.dx);
+        cudaFree(P.dv);
+        cudaFree(P.dmask);
+        P.dx = P.dv = nullptr;
+        P.dmask = nullptr;
+        P.ctx = nullptr;
+        return st != CCFR_OK ? st : CCFR_ERR_OOM;
+    }
+    sv->resident += P.bytes;
+    sv->peak_resident = std::max(sv->peak_resident, sv->resident);
+    sv->admissions++;
+    return CCFR_OK;
+}
+
+// Group the scenes into pools (once, before serving): scenes of at most
+// pool_scene_max vertices whose settings agree except for r, xi, delta and
+// pad (what a batched context allows to differ), in registration order, up to
+// pool_max_verts vertices and 2048 scenes per pool.
+void form_pools(ccfr_server* sv) {
+    if (sv->pools_formed || sv->pool_max_verts <= 0) return;
+    sv->pools_formed = true;
+    auto signature = [](ccfr_params q) {
+        q.r = q.xi = q.delta = q.pad = 0.f;
+        return q;
+    };
+    std::vector<int> open_pool;             // the pool taking members, per signature
+    std::vector<ccfr_params> open_sig;
+    for (int k = 0; k < (int)sv->scenes.size(); ++k) {
+        SceneRec& sc = sv->scenes[k];
+        if (sc.n_verts > sv->pool_scene_max || sc.n_verts > sv->pool_max_verts) continue;
+        const ccfr_params sig = signature(sc.params);
+        int i = 0;
+        while (i < (int)open_sig.size() && std::memcmp(&open_sig[i], &sig, sizeof(sig)) != 0) ++i;
+        if (i < (int)open_sig.size()) {
+            const Pool& P = sv->pools[open_pool[i]];
+            if (P.voff.back() + sc.n_verts > sv->pool_max_verts || P.members.size() >= 2048) {
+                open_pool.erase(open_pool.begin() + i);
+                open_sig.erase(open_sig.begin() + i);
+                i = (int)open_sig.size();
+            }
+        }
+        if (i == (int)open_sig.size()) {
+            sv->pools.emplace_back();
+            sv->pools.back().voff.push_back(0);
+            open_pool.push_back((int)sv->pools.size() - 1);
+            open_sig.push_back(sig);
+        }
+        const int p = open_pool[i];
+        Pool& P = sv->pools[p];
+        sc.pool = p;
+        sc.member = (int)P.members.size();
+        P.members.push_back(k);
+        P.voff.push_back(P.voff.back() + sc.n_verts);
+    }
+    for (Pool& P : sv->pools) {
+        long ne = 0, nt = 0;
+        int K = 0;
+        bool phi = false;
+        for (int k : P.members) {
+            const SceneRec& sc = sv->scenes[k];
+            ne += sc.n_edges;
+            nt += sc.n_tris;
+            K = sc.params.plane_capacity;
+            phi = sc.params.delta > 0.f;
+        }
+        const long nv = P.voff.back();
+        P.bytes = ctx_bytes(nv, ne, nt, K, false, phi) + (size_t)nv * 2 + P.members.size() * 20;
+        P.hmask.assign(P.members.size(), 0);
+    }
+}
+
+// Make scene s resident (served alone); evict idle units if needed.  Called
+// by the worker.
 ccfr_status admit(ccfr_server* sv, int s) {
     SceneRec& sc = sv->scenes[s];
     if (sc.ctx) return CCFR_OK;
-    while (sv->resident + sc.bytes > sv->budget) {
-        int victim = -1;
-        double oldest = 1e300;
-        for (int k = 0; k < (int)sv->scenes.size(); ++k) {
-            SceneRec& o = sv->scenes[k];
-            if (o.ctx && !o.busy && o.last_used < oldest) { oldest = o.last_used; victim = k; }
-        }
-        if (victim < 0) return CCFR_ERR_OOM;       // everything resident is busy: wait
-        SceneRec& o = sv->scenes[victim];
-        size_t nb = (size_t)o.n_verts * 4 * sizeof(float);
-        if (cudaMemcpy(o.x.data(), o.dx, nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
-            cudaMemcpy(o.v.data(), o.dv, nb, cudaMemcpyDeviceToHost) != cudaSuccess)
-            return CCFR_ERR_CUDA;
-        ccfr_destroy(o.ctx);
-        cudaFree(o.dx);
-        cudaFree(o.dv);
-        o.ctx = nullptr;
-        o.dx = o.dv = nullptr;
-        sv->resident -= o.bytes;
-        sv->evictions++;
-    }
+    ccfr_status rs = make_room(sv, sc.bytes);
+    if (rs != CCFR_OK) return rs;
     int *de = nullptr, *dt = nullptr;
     float* dr = nullptr;
     size_t nb = (size_t)sc.n_verts * 4 * sizeof(float);
@@ -174,6 +374,54 @@ void finish(ccfr_server* sv, Slot& sl, double t, int status) {
     sl.stalled = false;
 }
 
+// All requests of a pool launch are done (or failed together).
+void finish_pool(ccfr_server* sv, Slot& sl, double t, int status) {
+    Pool& P = sv->pools[sl.pool];
+    for (long i : sl.preqs) {
+        Req& r = sv->reqs[i];
+        r.t_done = t - sv->t0;
+        const int st = (r.status == CCFR_ERR_TIMEOUT) ? CCFR_ERR_TIMEOUT : status;
+        r.status = st;
+        SceneRec& sc = sv->scenes[r.scene];
+        sc.last_used = t;
+        if (st == CCFR_OK) sc.steps_done++;
+        else sv->failed++;
+        sv->n_done++;
+    }
+    P.busy = false;
+    P.last_used = t;
+    sl.pool = -1;
+    sl.preqs.clear();
+    sl.stalled = false;
+}
+
+// Launch pool p on slot sl: every member with a request due now takes its
+// oldest one (one step per scene and launch, in arrival order per scene).
+void launch_pool(ccfr_server* sv, Slot& sl, int p, double rel, double t) {
+    Pool& P = sv->pools[p];
+    std::fill(P.hmask.begin(), P.hmask.end(), (unsigned char)0);
+    sl.preqs.clear();
+    for (long i = sv->scan_from; i < (long)sv->reqs.size(); ++i) {
+        Req& q = sv->reqs[i];
+        if (q.t_arrival > rel) break;
+        if (q.t_start >= 0.0) continue;
+        const SceneRec& sc = sv->scenes[q.scene];
+        if (sc.pool != p || P.hmask[sc.member]) continue;
+        P.hmask[sc.member] = 1;
+        q.t_start = rel;
+        sl.preqs.push_back(i);
+    }
+    P.busy = true;
+    sl.pool = p;
+    sl.t_launch = t;
+    sv->pool_launches++;
+    // (a copy from pageable memory returns once the bytes are staged)
+    cudaError_t e = cudaMemcpyAsync(P.dmask, P.hmask.data(), P.hmask.size(), cudaMemcpyHostToDevice, sl.stream);
+    ccfr_status st = (e == cudaSuccess) ? ccfr_step_active(P.ctx, P.dx, P.dv, P.dmask, sl.stream) : CCFR_ERR_CUDA;
+    if (st != CCFR_OK || cudaEventRecord(sl.done, sl.stream) != cudaSuccess)
+        finish_pool(sv, sl, now_s(), st ? st : CCFR_ERR_CUDA);
+}
+
 void worker_loop(ccfr_server* sv) {
     cudaSetDevice(sv->device);
     while (!sv->stop.load()) {
@@ -182,25 +430,35 @@ void worker_loop(ccfr_server* sv) {
             std::lock_guard<std::mutex> lk(sv->mu);
             const double t = now_s();
             for (Slot& sl : sv->slots) {
-                if (sl.req < 0) continue;
+                if (!sl.busy()) continue;
                 active = true;
                 if (sl.stalled) {
                     if (t - sl.t_launch > sv->timeout) finish(sv, sl, t, CCFR_ERR_TIMEOUT);
                     continue;
                 }
                 cudaError_t q = cudaEventQuery(sl.done);
-                if (q == cudaSuccess) finish(sv, sl, t, CCFR_OK);
-                else if (q != cudaErrorNotReady) { cudaGetLastError(); finish(sv, sl, t, CCFR_ERR_CUDA); }
-                else if (t - sl.t_launch > sv->timeout) {
-                    // bounded wait: report the request; the slot stays closed until its
+                const bool pool = sl.pool >= 0;
+                if (q == cudaSuccess) {
+                    if (pool) finish_pool(sv, sl, t, CCFR_OK);
+                    else finish(sv, sl, t, CCFR_OK);
+                } else if (q != cudaErrorNotReady) {
+                    cudaGetLastError();
+                    if (pool) finish_pool(sv, sl, t, CCFR_ERR_CUDA);
+                    else finish(sv, sl, t, CCFR_ERR_CUDA);
+                } else if (t - sl.t_launch > sv->timeout) {
+                    // bounded wait: report the request(s); the slot stays closed until its
                     // work drains, so no later work is queued behind it
-                    sv->reqs[sl.req].status = CCFR_ERR_TIMEOUT;
+                    if (pool) {
+                        for (long i : sl.preqs) sv->reqs[i].status = CCFR_ERR_TIMEOUT;
+                    } else {
+                        sv->reqs[sl.req].status = CCFR_ERR_TIMEOUT;
+                    }
                 }
             }
             const double rel = t - sv->t0;
             for (Slot& sl : sv->slots) {
-                if (sl.req >= 0) continue;
-                // earliest due request whose scene is idle (first hit per scene = its oldest)
+                if (sl.busy()) continue;
+                // earliest due request whose scene (or pool) is idle (first hit per scene = its oldest)
                 long pick = -1;
                 while (sv->scan_from < (long)sv->reqs.size() && sv->reqs[sv->scan_from].t_start >= 0.0) sv->scan_from++;
                 for (long i = sv->scan_from; i < (long)sv->reqs.size(); ++i) {
@@ -208,6 +466,12 @@ void worker_loop(ccfr_server* sv) {
                     if (r.t_arrival > rel) break;
                     if (r.t_start >= 0.0) continue;
                     SceneRec& sc = sv->scenes[r.scene];
+                    if (sc.pool >= 0) {
+                        if (sv->pools[sc.pool].busy) continue;
+                        if (admit_pool(sv, sc.pool) != CCFR_OK) continue;
+                        pick = i;
+                        break;
+                    }
                     if (sc.busy) continue;
                     if (admit(sv, r.scene) != CCFR_OK) continue;
                     pick = i;
@@ -216,6 +480,11 @@ void worker_loop(ccfr_server* sv) {
                 if (pick < 0) break;
                 Req& r = sv->reqs[pick];
                 SceneRec& sc = sv->scenes[r.scene];
+                if (sc.pool >= 0) {
+                    launch_pool(sv, sl, sc.pool, rel, t);
+                    active = true;
+                    continue;
+                }
                 sc.busy = true;
                 r.t_start = rel;
                 sl.req = pick;
@@ -300,9 +569,18 @@ ccfr_status ccfr_server_preload(ccfr_server* sv, double fraction, int* n_admitte
     if (!sv || !(fraction > 0.0) || fraction > 1.0) return CCFR_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(sv->mu);
     if (sv->running.load()) return CCFR_ERR_STATE;
+    form_pools(sv);
     int n = 0;
     for (int k = 0; k < (int)sv->scenes.size(); ++k) {
         SceneRec& sc = sv->scenes[k];
+        if (sc.pool >= 0) {
+            Pool& P = sv->pools[sc.pool];
+            if (P.ctx || (double)(sv->resident + P.bytes) > fraction * (double)sv->budget) continue;
+            ccfr_status st = admit_pool(sv, sc.pool);
+            if (st != CCFR_OK) return st;
+            n += (int)P.members.size();
+            continue;
+        }
         if (sc.ctx) continue;
         if ((double)(sv->resident + sc.bytes) > fraction * (double)sv->budget) continue;
         ccfr_status st = admit(sv, k);
@@ -313,8 +591,21 @@ ccfr_status ccfr_server_preload(ccfr_server* sv, double fraction, int* n_admitte
     return CCFR_OK;
 }
 
+ccfr_status ccfr_server_set_batching(ccfr_server* sv, int max_pool_verts, int max_scene_verts) {
+    if (!sv || max_pool_verts < 0 || max_scene_verts < 0) return CCFR_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (sv->running.load() || sv->pools_formed) return CCFR_ERR_STATE;
+    sv->pool_max_verts = max_pool_verts;
+    sv->pool_scene_max = max_scene_verts;
+    return CCFR_OK;
+}
+
 ccfr_status ccfr_server_start(ccfr_server* sv) {
     if (!sv) return CCFR_ERR_INVALID_ARG;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        form_pools(sv);
+    }
     if (sv->running.exchange(true)) return CCFR_ERR_STATE;
     sv->t0 = now_s();
     sv->stop = false;
@@ -371,6 +662,17 @@ ccfr_status ccfr_server_get_state(ccfr_server* sv, int scene_id, float* x, float
     SceneRec& sc = sv->scenes[scene_id];
     if (sc.busy) return CCFR_ERR_STATE;
     size_t nb = (size_t)sc.n_verts * 4 * sizeof(float);
+    if (sc.pool >= 0) {
+        const Pool& P = sv->pools[sc.pool];
+        if (P.busy) return CCFR_ERR_STATE;
+        if (P.ctx) {
+            const size_t vo = (size_t)P.voff[sc.member] * 4;
+            if (cudaMemcpy(x, P.dx + vo, nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(v, P.dv + vo, nb, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return CCFR_ERR_CUDA;
+            return CCFR_OK;
+        }
+    }
     if (sc.ctx) {
         if (cudaMemcpy(x, sc.dx, nb, cudaMemcpyDeviceToHost) != cudaSuccess ||
             cudaMemcpy(v, sc.dv, nb, cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -394,6 +696,8 @@ ccfr_status ccfr_server_get_info(ccfr_server* sv, ccfr_server_info* out) {
     out->resident_bytes = sv->resident;
     out->peak_resident_bytes = sv->peak_resident;
     out->budget_bytes = sv->budget;
+    out->pools = (long)sv->pools.size();
+    out->pool_launches = sv->pool_launches;
     return CCFR_OK;
 }
 
@@ -421,6 +725,12 @@ ccfr_status ccfr_server_destroy(ccfr_server* sv) {
         if (sc.ctx) ccfr_destroy(sc.ctx);
         cudaFree(sc.dx);
         cudaFree(sc.dv);
+    }
+    for (Pool& P : sv->pools) {
+        if (P.ctx) ccfr_destroy(P.ctx);
+        cudaFree(P.dx);
+        cudaFree(P.dv);
+        cudaFree(P.dmask);
     }
     for (Slot& sl : sv->slots) {
         if (sl.done) cudaEventDestroy(sl.done);

@@ -96,3 +96,35 @@ def test_tuning_does_not_change_results():
         ctx.close()
     for o in outs[1:]:
         np.testing.assert_array_equal(o, outs[0])
+
+
+def test_step_active_mask():
+    """ccfr_step_active: scenes whose mask byte is 0 keep x and v bitwise; the
+    others advance exactly as when stepped alone; a later full step moves the
+    paused scenes from where they were."""
+    scenes = small_batch()
+    x, v = merged(scenes)
+    ctx = ccfr.Context.from_scenes(scenes)
+    mask = np.array([1, 0, 1, 1, 0, 1, 0][:len(scenes)], np.uint8)
+    active = torch.as_tensor(mask).cuda()
+    x0, v0 = x.cpu().numpy().copy(), v.cpu().numpy().copy()
+    ctx.step_active(x, v, active)
+    ctx.step_active(x, v, active)
+    ctx.step(x, v)                              # every scene: paused ones take their first step
+    xb, vb = x.cpu().numpy(), v.cpu().numpy()
+    for k, sc in enumerate(scenes):
+        xs = torch.as_tensor(sc.x).cuda().contiguous()
+        vs = torch.as_tensor(sc.v).cuda().contiguous()
+        c1 = ccfr.Context.from_scene(sc)
+        for _ in range(3 if mask[k] else 1):
+            c1.step(xs, vs)
+        o0, o1 = ctx.offsets[k], ctx.offsets[k + 1]
+        np.testing.assert_array_equal(xb[o0:o1], xs.cpu().numpy(), err_msg=sc.name)
+        np.testing.assert_array_equal(vb[o0:o1], vs.cpu().numpy(), err_msg=sc.name)
+        c1.close()
+    # a mask of zeros leaves everything as it is
+    x1, v1 = x.clone(), v.clone()
+    ctx.step_active(x, v, torch.zeros(len(scenes), dtype=torch.uint8, device="cuda"))
+    assert torch.equal(x, x1) and torch.equal(v, v1)
+    ctx.close()
+    assert not np.array_equal(x0, xb)

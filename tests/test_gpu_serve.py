@@ -97,3 +97,65 @@ def test_stalled_step_times_out():
     assert res["status"][1] == 5 and res["status"][0] == 0 and res["status"][2] == 0
     assert res["t_done"][1] - res["t_start"][1] >= 0.5
     sv.close()
+
+
+def serve_batched(scenes, steps, budget, max_pool_verts, max_scene_verts, slots=3):
+    sv = ccfr.Server(budget, n_slots=slots, timeout_s=30.0)
+    ids = [sv.add_scene(sc) for sc in scenes]
+    sv.set_batching(max_pool_verts, max_scene_verts)
+    t = 0.0
+    order = []
+    for k in range(steps):
+        for i in ids:
+            order.append(i)
+            sv.submit(i, t)
+            t += 1e-4
+    sv.start()
+    n = sv.wait(120.0)
+    return sv, ids, order, n
+
+
+def test_batched_serving_equals_alone():
+    """Continuous batching: the scenes are served by pooled batched launches
+    (several requests per launch) and every scene ends bitwise where it ends
+    stepped alone; requests of one scene still run in order."""
+    scenes = pool()
+    steps = 3
+    sv, ids, order, n = serve_batched(scenes, steps, 40 << 30, max_pool_verts=1 << 20, max_scene_verts=1 << 20)
+    assert n == len(order)
+    res = sv.results(len(order))
+    assert np.all(res["status"] == 0)
+    info = sv.info()
+    assert info["pools"] >= 1 and 0 < info["pool_launches"] < len(order)
+    for i in ids:
+        own = np.nonzero(np.array(order) == i)[0]
+        assert np.all(np.diff(res["t_start"][own]) > 0)
+    for sc, i in zip(scenes, ids):
+        xs, vs = sv.state(i)
+        xa, va = alone(sc, steps)
+        np.testing.assert_array_equal(xs, xa, err_msg=sc.name)
+        np.testing.assert_array_equal(vs, va, err_msg=sc.name)
+    sv.close()
+
+
+def test_batched_pools_and_single_scenes_with_eviction():
+    """Small pools (a few scenes each) beside scenes served alone (the largest
+    ones), with a budget that holds only part of them: pools are evicted and
+    re-admitted as units and every result still equals the scene alone."""
+    scenes = pool()
+    steps = 2
+    sizes = sorted(sc.n_verts for sc in scenes)
+    big = max(ccfr.estimate_bytes(sc) for sc in scenes)
+    sv, ids, order, n = serve_batched(scenes, steps, budget=3 * big, max_pool_verts=2 * sizes[len(sizes) // 2],
+                                      max_scene_verts=sizes[-2], slots=2)
+    info = sv.info()
+    assert info["pools"] >= 2 and info["evictions"] > 0
+    assert info["peak_resident_bytes"] <= info["budget_bytes"]
+    res = sv.results(len(order))
+    assert np.all(res["status"] == 0)
+    for sc, i in zip(scenes, ids):
+        xs, vs = sv.state(i)
+        xa, va = alone(sc, steps)
+        np.testing.assert_array_equal(xs, xa, err_msg=sc.name)
+        np.testing.assert_array_equal(vs, va, err_msg=sc.name)
+    sv.close()
