@@ -714,6 +714,18 @@ orc_regions *orc_build(const double *x3, const float *x4w, int n, const int *edg
 
 long orc_regions_total(const orc_regions *R) { return R->total; }
 
+/* Planes per vertex and the band flags of a region build, without exporting
+ * the planes (for scenes whose plane lists are large). */
+void orc_region_counts(const double *x3, const float *x4w, int n, const int *edges, int ne, const int *tris,
+                       int nt, const orc_params *P, long *count, unsigned char *vflag) {
+    orc_regions *R = orc_build_ext(x3, x4w, n, edges, ne, tris, nt, NULL, P);
+    for (int i = 0; i < n; ++i) {
+        count[i] = R->offs[i + 1] - R->offs[i];
+        vflag[i] = R->vflag[i];
+    }
+    orc_regions_free(R);
+}
+
 void orc_regions_export(const orc_regions *R, long *offs, double *planes4, double *phi, u64 *key,
                         double *dlimit, unsigned char *vflag, long *cand_acc) {
     for (int i = 0; i <= R->n; ++i) offs[i] = R->offs[i];

@@ -81,6 +81,7 @@ def lib():
         _lib.orc_build_ext.restype = C.c_void_p
         _lib.orc_build_ext.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcExtra),
                                        C.POINTER(OrcParams)]
+        _lib.orc_region_counts.argtypes = [P, P, C.c_int, P, C.c_int, P, C.c_int, C.POINTER(OrcParams), P, P]
         _lib.orc_regions_total.restype = C.c_long
         _lib.orc_regions_total.argtypes = [P]
         _lib.orc_regions_export.argtypes = [P, P, P, P, P, P, P, P]
@@ -224,6 +225,22 @@ def build_regions(x3: np.ndarray, x4w: np.ndarray, edges, tris, params: OrcParam
         L.orc_regions_free(h)
     return {"offs": offs, "planes": planes[:tot], "phi": phi[:tot], "key": key[:tot],
             "dlimit": dlimit, "vflag": vflag, "cand": ca[:4], "acc": ca[4:]}
+
+
+def region_counts(x3, x4w, edges, tris, params: OrcParams):
+    """Planes per vertex (Alg. 3 over all pairs) and the per-vertex flags
+    (bit 0 overflow, bit 1 a band pair, |phi - 2r| <= band), without
+    exporting the planes."""
+    L = lib()
+    x3 = _c(x3, np.float64)
+    x4w = _c(x4w, np.float32)
+    e = _c(edges, np.int32)
+    t = _c(tris, np.int32)
+    n = len(x3)
+    count = np.zeros(n, np.int64)
+    vflag = np.zeros(n, np.uint8)
+    L.orc_region_counts(_p(x3), _p(x4w), n, _p(e), len(e), _p(t), len(t), C.byref(params), _p(count), _p(vflag))
+    return count, vflag
 
 
 def project(x3, xp3, w, offs, planes4, keys, dlimit, params: OrcParams):

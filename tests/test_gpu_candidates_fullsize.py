@@ -8,7 +8,10 @@ positions: by the GPU's grid emission (ccfr_get_candidates) and by the
 oracle's sort-and-sweep (orc_candidates, OpenMP over the queries).  The
 vertex-face and edge-edge sets must be equal after sorting, bit for bit, at
 the initial state and again after one full substep on the GPU (the oracle
-then reads the GPU's positions)."""
+then reads the GPU's positions).  At both states the number of planes each
+vertex receives (accepted pairs, phi < 2r, Alg. 3) must equal the oracle's
+exactly, except at vertices of a pair within 1e-7 L of the acceptance
+threshold (counted; below 1% of the vertices)."""
 import numpy as np
 import pytest
 
@@ -50,6 +53,16 @@ def test_candidate_sets_bit_exact_at_bench_size(orc, cfg):
             assert g.shape == r.shape, (stage, k, g.shape, r.shape)
             assert np.array_equal(g, r), (stage, k)
         assert len(ref["ee"]) > 0
+        # planes per vertex
+        ctx.build_regions(x)
+        gcount = ctx.regions()["count"].cpu().numpy().astype(np.int64)
+        L = orc.scene_scale(xs)
+        P = orc.make_params(sc.params, band=1e-7 * L, capacity=0)
+        rcount, vflag = orc.region_counts(xs[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, P)
+        band = (vflag & 2) != 0
+        assert band.mean() < 0.01, (stage, int(band.sum()))
+        bad = np.nonzero(~band & (gcount != rcount))[0]
+        assert len(bad) == 0, (stage, [(int(b), int(gcount[b]), int(rcount[b])) for b in bad[:10]])
         if stage == "initial state":
             ctx.step(x, v)
             st = ctx.stats()

@@ -145,8 +145,13 @@ def test_batched_pools_and_single_scenes_with_eviction():
     scenes = pool()
     steps = 2
     sizes = sorted(sc.n_verts for sc in scenes)
-    big = max(ccfr.estimate_bytes(sc) for sc in scenes)
-    sv, ids, order, n = serve_batched(scenes, steps, budget=3 * big, max_pool_verts=2 * sizes[len(sizes) // 2],
+    est = [ccfr.estimate_bytes(sc) for sc in scenes]
+    big = max(est)
+    # pools of at most the largest scene's vertex count, the largest scene alone; a budget
+    # for about two such units while the scenes need more
+    budget = int(2.2 * big)
+    assert budget < 0.9 * sum(est)
+    sv, ids, order, n = serve_batched(scenes, steps, budget=budget, max_pool_verts=sizes[-1],
                                       max_scene_verts=sizes[-2], slots=2)
     info = sv.info()
     assert info["pools"] >= 2 and info["evictions"] > 0
