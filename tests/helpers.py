@@ -52,7 +52,7 @@ def csr_to_padded(offs, planes4, K):
     return out, cnt
 
 
-def band_vertices_valid(orc, sc, P, x_build, y, band_mask, L, tol_rel=1e-5, step_bound=None):
+def band_vertices_valid(orc, sc, P, x_build, y, band_mask, L, tol_rel=1e-5, step_bound=None, extra=None):
     """Validity of the GPU's result at vertices the oracle excludes from the
     position comparison (a decision inside a band, where either branch is a
     correct outcome of the method).  Each such movable vertex must either have
@@ -60,9 +60,10 @@ def band_vertices_valid(orc, sc, P, x_build, y, band_mask, L, tol_rel=1e-5, step
     its oracle region, except planes of band pairs, within the final-check
     tolerance tau plus tol_rel L (the plane parity bar), and move at most
     step_bound when given (plus the binary32 rounding of the positions).
+    extra: the links and tetrahedra of a mixed scene (oracle.Extra).
     Returns a list of (vertex, reason, amount) for the violations."""
     x_build = np.asarray(x_build, np.float64)
-    R = orc.build_regions(x_build, sc.x, sc.edges, sc.tris, P)
+    R = orc.build_regions(x_build, sc.x, sc.edges, sc.tris, P, extra=extra)
     r2 = 2.0 * P.r
     u32 = 2.0 ** -24
     bad = []

@@ -56,12 +56,22 @@ SCENES = {
     "cloth_on_sphere 32x32": lambda: S.config(1),
     "wires 6x6x32": lambda: S.wires(n_grid=6, n_seg=32, seed=3),
     "particles 512": lambda: S.particle_cloud(512, seed=6, sphere_radius=0.03),
+    # rods, soft volumes, cloth and particles (links, tetrahedra, point-edge pairs); with
+    # compliance 0 the multipliers do not affect positions, as for the other scenes
+    "codimensional 829 verts, compliance 0": lambda: S.codimensional(rod_seg=16, cube_n=3, cloth_bending=0.0,
+                                                                     rod_bending=0.0, volume_compliance=0.0),
 }
+
+
+def _extra(orc, sc):
+    if not (len(sc.links) or len(sc.tets)):
+        return None
+    return orc.Extra(sc.x[:, :3].astype(np.float64), sc.links, sc.link_compliance, sc.tets, sc.volume_compliance)
 
 
 def _capacity(orc, sc):
     R = orc.build_regions(sc.x[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris,
-                          orc.make_params(sc.params, capacity=0))
+                          orc.make_params(sc.params, capacity=0), extra=_extra(orc, sc))
     m = int(np.diff(R["offs"]).max()) if sc.n_verts else 0
     return max(64, int(np.ceil(m * 1.5 / 32.0)) * 32)
 
@@ -77,6 +87,8 @@ def report(line):
 @pytest.mark.parametrize("name", sorted(SCENES))
 def test_every_iteration_against_oracle(orc, name):
     sc = SCENES[name]()
+    assert not np.any(sc.link_compliance) and sc.volume_compliance == 0.0 and sc.params["compliance"] == 0.0
+    ex = _extra(orc, sc)
     iters = sc.params["iters"]
     L = orc.scene_scale(sc.x)
     K = _capacity(orc, sc)
@@ -112,7 +124,7 @@ def test_every_iteration_against_oracle(orc, name):
         outs = {}
         for f in DEP_BANDS_REPORTED:
             P = orc.make_params(sc.params, band=BAND_REL * L, iters=1, capacity=K, dep_band=f, cond_band=cb)
-            xo, _, info, vband = orc.step(xc, vel, sc.x, sc.edges, sc.tris, rest, P)
+            xo, _, info, vband = orc.step(xc, vel, sc.x, sc.edges, sc.tris, rest, P, extra=ex)
             outs[f] = (xo, vband, P)
         xo, vband, P = outs[10.0]
         for f in DEP_BANDS_REPORTED:
@@ -123,7 +135,8 @@ def test_every_iteration_against_oracle(orc, name):
         bad = np.nonzero(ok & (err > TOL_REL * L))[0]
         assert len(bad) == 0, (i, [(int(b), float(err[b] / L), float(np.linalg.norm(y[b] - xc[b])),
                                     float(np.linalg.norm(xo[b] - xc[b]))) for b in bad[:5]])
-        invalid = band_vertices_valid(orc, sc, P, xc, y, (vband != 0) & mov, L, step_bound=sc.params["r"])
+        invalid = band_vertices_valid(orc, sc, P, xc, y, (vband != 0) & mov, L, step_bound=sc.params["r"],
+                                      extra=ex)
         assert not invalid, (i, len(invalid), invalid[:10])
         worst = max(worst, float(err[ok].max()) / L if ok.any() else 0.0)
         n_cmp += int(ok.sum())

@@ -136,12 +136,16 @@ def test_rod_scenes_full_substep(orc, name):
 
 def test_mixed_scene_substeps(orc):
     """Two iterations: every vertex outside the bands within the bar.  Ten
-    iterations (the full substep): the self-colliding volume surfaces and the
-    cloth go through many halts, and a halt taken differently in binary32 and
-    FP64 moves that vertex by up to the step bound (as in the cloth stack's
-    full-substep case); the rods, particles and volume interiors, driven by the
-    links, the point-edge pairs and the volume constraints, stay within the bar
-    everywhere, and the median stays at the rounding level."""
+    iterations (the full substep) compared in one shot: the rods, particles
+    and volume interiors, driven by the links, the point-edge pairs and the
+    volume constraints, stay within the bar everywhere; on the self-colliding
+    volume surfaces and the cloth, a decision taken differently in binary32 and
+    FP64 inside a band moves that vertex by up to the step bound and spreads
+    over later iterations (as in the cloth stack's one-shot case), so there
+    only the median is asserted here.  The full substep of the same scene is
+    asserted iteration by iteration, every vertex outside the bands within the
+    bar and every band vertex valid, in tests/test_gpu_iterations.py (with
+    zero compliance, where the XPBD multipliers do not affect positions)."""
     sc = SCENES["codimensional"]()
     err, ok = substep_error(orc, sc, 2)
     assert err[ok].max() <= TOL_REL
@@ -150,7 +154,7 @@ def test_mixed_scene_substeps(orc):
     for name in ("rod", "particle", "interior"):
         m = parts[name] & ok
         assert m.sum() > 0 and err[m].max() <= TOL_REL, name
-    assert np.mean(err[ok] <= TOL_REL) >= 0.97 and np.median(err[ok]) <= 1e-7
+    assert np.median(err[ok]) <= 1e-7
 
 
 def test_mixed_scene_stays_free_of_intersections(orc):
@@ -214,6 +218,13 @@ def test_mixed_full_size_sampled_projection(orc):
     ok = band == 0
     assert ok.sum() >= 0.5 * len(sample) and (nviol[ok] > 0).sum() > 0
     err = np.abs(got - out).max(axis=1)[ok] / L
-    # the oracle breaks equal sort keys by slot here, the library by plane hash
-    # and bits; a vertex whose walk meets equal keys on distinct planes may differ
-    assert np.mean(err <= TOL_REL) >= 0.99, (float(np.mean(err <= TOL_REL)), float(err.max()))
+    # exact FP64 key ties are bitwise-identical planes (their order does not
+    # change the result); near-ties of distinct planes are band cases
+    assert err.max() <= TOL_REL, (float(np.mean(err <= TOL_REL)), float(err.max()))
+    # excluded (band) vertices: halted at the build position or inside every plane
+    for i in np.nonzero(~ok)[0]:
+        d = got[i] - xb[i]
+        if np.all(d == 0.0):
+            continue
+        p = flat[offs[i]:offs[i + 1]]
+        assert (p[:, :3] @ d + p[:, 3]).min() >= -(P.tau_feas + TOL_REL * L), int(sample[i])
