@@ -1393,7 +1393,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
 // src into buffer src ^ 1, on the 8-bit digit dig(slot), computed once per
 // entry (four planes in flight per lane) and kept in sb.dig for the scatter.
 // Equal digits keep their relative order: ranks within each 32-entry chunk
-// come from the intersection of the eight bit-slice ballots.
+// come from the lanes that hold the same digit (one match instruction).
 template <typename Dig>
 __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src, Dig dig) {
     const unsigned lt = (1u << lane) - 1u;
@@ -1436,14 +1436,8 @@ __device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src
         const bool valid = i < n;
         const unsigned short j = valid ? sb.idx[src][i] : 0;
         const unsigned dg = valid ? (unsigned)sb.dig[i] : 256u;
-        // lanes holding the same digit: intersect the eight bit-slice ballots
-        unsigned peers = __ballot_sync(FULL, valid);
-        if (!valid) peers = ~peers;
-        #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const unsigned bit = __ballot_sync(FULL, (dg >> b) & 1u);
-            peers &= ((dg >> b) & 1u) ? bit : ~bit;
-        }
+        // lanes holding the same digit (the idle lanes, digit 256, form a group of their own)
+        const unsigned peers = __match_any_sync(FULL, dg);
         const unsigned start = valid ? sb.hist[dg] : 0u;
         __syncwarp();
         if (valid) {
