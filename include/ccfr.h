@@ -153,7 +153,10 @@ typedef struct {
                                                          items they tested, [13] oversized-
                                                          edge items tested by oversized
                                                          edges, [14] candidates found by
-                                                         oversized primitives, [15] zero   */
+                                                         oversized primitives, [15] kinds
+                                                         whose oversized pairs overflowed
+                                                         the pair buffer (redone by the
+                                                         fused pass; time only)           */
     unsigned int max_planes;                          /* largest per-vertex plane count */
     unsigned int error_flags;                         /* bit 0 non-finite input         */
     unsigned long long cand_ve, pairs_ve, planes_ve;  /* point-edge pairs (ccfr_mesh_ext):

@@ -367,6 +367,9 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.work, (size_t)N) == cudaSuccess;
     ok &= dalloc(c, &d.work_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
+    d.bq_cap = BQ_PER_PRIM * ((long)T + E) + 4096;
+    ok &= dalloc(c, &d.bq, (size_t)d.bq_cap) == cudaSuccess;
+    ok &= dalloc(c, &d.bq_count, 1) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
     ok &= dalloc(c, &c->tile_sums, (size_t)n_tiles) == cudaSuccess;
     ok &= dalloc(c, &d.flags, 2) == cudaSuccess;

@@ -34,7 +34,9 @@ typedef unsigned long long u64;
 // immobile), and giant edges.
 enum { KIND_TRI = 0, KIND_EDGE = 1, KIND_PT = 2, KIND_VQ = 3, KIND_BIGE = 4, KIND_BIGS = 5, KIND_GIANT = 6,
        N_TABLES = 7 };
-enum { MODE_PLANES = 0, MODE_PAIRS = 1 };
+// MODE_BIGQ: the oversized pass's broad phase alone, its candidate pairs
+// written to DevCtx::bq for the narrow kernel (k_big_narrow)
+enum { MODE_PLANES = 0, MODE_PAIRS = 1, MODE_BIGQ = 2 };
 enum { ERR_NONFINITE = 1u };
 
 // Near-parallel edge pairs (a*e - b^2 <= NEAR_PARALLEL * a * e in binary32)
@@ -115,6 +117,12 @@ struct DevCtx {
     float4* big_box;            // [2 (n_tris + n_edges)] their padded boxes (lo + id, hi)
     int big_base[2];            // first slot of the triangles / edges
     unsigned* big_count;        // [2]
+    // candidate pairs of the oversized primitives between their broad and narrow
+    // kernels (oversized primitive first); bq_count[0] counts the pairs found
+    // (past bq_cap the buffer overflowed and the fused pass redoes the kind)
+    int2* bq;
+    unsigned* bq_count;         // [1]
+    long bq_cap;
     int2* units;                // [n_tris + n_edges + n_pts + 3] warp work units
     int unit_base[3];           // first unit slot of each query table
     unsigned* unit_count;       // [3]
@@ -171,6 +179,11 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // BIGE_FACTOR edge cells; the few larger than that ("giants") to a table whose
 // cell is the largest edge box.
 constexpr float BIGE_FACTOR = 2.0f;
+
+// Capacity of the oversized primitives' pair buffer, in pairs per triangle
+// and edge of the context (the cloth stack at 262,144 vertices finds about 7
+// per primitive in its most tangled substeps; an overflow only costs time).
+constexpr long BQ_PER_PRIM = 16;
 
 __device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
     const bool big = kind == KIND_BIGE || kind == KIND_BIGS;

@@ -794,13 +794,28 @@ __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __re
     return scene;
 }
 
+// Append the n (<= 32) pairs the lanes hold to the oversized primitives'
+// pair buffer (one reservation per warp; the count runs on past the capacity,
+// which tells the fused pass to redo the kind).
+__device__ __forceinline__ void bq_put(const DevCtx& c, int2 pr, int n, int lane) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(c.bq_count, (unsigned)n);
+    base = __shfl_sync(FULL, base, 0);
+    if (lane < n && (long)base + lane < c.bq_cap) c.bq[base + lane] = pr;
+}
+
 // VE (QK = KIND_EDGE): every free edge against the isolated points of the
 // point-table cells its box reaches (pairs (point, edge)); one warp per free
 // edge, as for the oversized primitives, so that no point scans the far more
 // numerous edges of triangles.
-template <int QK, int MODE, bool VE = false>
+// MODE_BIGQ: the scan alone; its pairs go to c.bq for k_big_narrow, so that
+// the scan runs at the occupancy of its own small register set.  FALLBACK:
+// the fused scan and narrow phase, run only when the pair buffer of this kind
+// overflowed (k_big_narrow then left the kind untouched).
+template <int QK, int MODE, bool VE = false, bool FALLBACK = false>
 __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po) {
     if (c.flags[1]) return;
+    if (FALLBACK && (long)*c.bq_count <= c.bq_cap) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int2* q = queue[wib];
@@ -818,7 +833,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         qn += __popc(hb);
         if (qn >= 32) {
             __syncwarp();
-            process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
+            if constexpr (MODE == MODE_BIGQ) bq_put(c, q[lane], 32, lane);
+            else process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
             int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
             __syncwarp();
             if (lane < qn - 32) q[lane] = rest;
@@ -985,17 +1001,45 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         }
     }
     __syncwarp();
-    if (lane < qn) process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
+    if constexpr (MODE == MODE_BIGQ) {
+        if (qn > 0) bq_put(c, q[lane], qn, lane);
+    } else {
+        if (lane < qn) process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
+    }
     constexpr int SK = VE ? PAIR_VE : QK;
-    warp_add_u64(&c.stats->cand[SK], k.cand);
-    warp_add_u64(&c.stats->pairs[SK], k.acc);
-    warp_add_u64(&c.stats->planes_kind[SK], k.planes);
+    if (MODE != MODE_BIGQ) {
+        warp_add_u64(&c.stats->cand[SK], k.cand);
+        warp_add_u64(&c.stats->pairs[SK], k.acc);
+        warp_add_u64(&c.stats->planes_kind[SK], k.planes);
+    }
     if (VE) return;
-    if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+    if (MODE != MODE_BIGQ && QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+    if (MODE != MODE_BIGQ) warp_add_u64(&c.stats->aux[14], k.cand);
+    if (FALLBACK) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c.stats->aux[15], 1ull);
+        return;                        // the scan diagnostics were counted by the MODE_BIGQ pass
+    }
     warp_add_u64(&c.stats->aux[10], big_cells);
     warp_add_u64(&c.stats->aux[11], big_scans);
     warp_add_u64(&c.stats->aux[12], big_items);
     warp_add_u64(&c.stats->aux[13], bige_items);
+}
+
+// Narrow phase of the oversized primitives' candidate pairs (MODE_BIGQ): one
+// thread per pair, grid-strided, three blocks per SM; nothing when the buffer
+// overflowed.
+template <int QK>
+__global__ void __launch_bounds__(256, 3) k_big_narrow(DevCtx c, const float4* __restrict__ x, PairOut po) {
+    if (c.flags[1]) return;
+    const unsigned n = *c.bq_count;
+    EmitCounters k{0, 0, 0, 0};
+    if ((long)n <= c.bq_cap)
+        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+            process_pair<QK, MODE_PLANES>(c, x, po, c.bq[i], k);
+    warp_add_u64(&c.stats->cand[QK], k.cand);
+    warp_add_u64(&c.stats->pairs[QK], k.acc);
+    warp_add_u64(&c.stats->planes_kind[QK], k.planes);
+    if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
     warp_add_u64(&c.stats->aux[14], k.cand);
 }
 
@@ -2405,6 +2449,16 @@ __global__ void k_dmin_export(DevCtx c, float* out) {
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
+// The oversized primitives of one kind: the scan into the pair buffer, the
+// narrow phase over it, and the fused pass that runs only if it overflowed.
+template <int QK>
+static void launch_big(const DevCtx& c, const float4* x, const PairOut& po, int G, cudaStream_t st) {
+    cudaMemsetAsync(c.bq_count, 0, sizeof(unsigned), st);
+    k_emit_big<QK, MODE_BIGQ><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+    k_big_narrow<QK><<<G, 256, 0, st>>>(c, x, po);
+    k_emit_big<QK, MODE_PLANES, false, true><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+}
+
 void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* poh,
                   unsigned* tile_sums, int n_buckets_total, StageTimer* tm, const SideStream* side) {
     PairOut po{};
@@ -2449,11 +2503,11 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
         }
         if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_VF, st);
-        if (c.n_tris > 0) k_emit_big<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_tris > 0) launch_big<KIND_TRI>(c, x, po, G, st);
         if (tm) tm->mark(ST_EMIT_VF_BIG, st);
         if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (tm) tm->mark(ST_EMIT_EE, st);
-        if (c.n_edges > 0) k_emit_big<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_edges > 0) launch_big<KIND_EDGE>(c, x, po, G, st);
         if (tm) tm->mark(ST_EMIT_EE_BIG, st);
         if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
         if (c.n_pts > 0 && c.n_free > 0) k_emit_big<KIND_EDGE, MODE_PLANES, true><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);

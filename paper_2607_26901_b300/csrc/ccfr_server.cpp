@@ -125,6 +125,7 @@ size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false) {
     b += (size_t)e * (8 + 8 + 4 + 4);
     b += (size_t)t * 12;
     b += (size_t)buckets * 8 + (size_t)items * (4 + 32) + (size_t)(t + e + n + 3) * 8 + (size_t)(t + e) * 36;
+    b += (size_t)(t + e) * 16 * 8 + 4096 * 8;   // oversized primitives' pair buffer
     b += 2 * (size_t)n * 16;               // resident x, v
     return b + (1 << 20);
 }
