@@ -430,7 +430,9 @@ def main():
         e2e = {"value": sc.n_movable * st3["iterations"] * ws / te, "unit": UNIT,
                "h2d_bytes_per_step": 2 * N * 16, "d2h_bytes_per_step": 2 * N * 16}
 
-    n_emit = (2 if T > 0 else 0) + (2 if E > 0 else 0) + (1 if n_pts > 1 else 0)
+    # vertex-face and edge-edge, fitting and oversized primitives: scan, narrow phase and the fused
+    # kernel that returns at once unless the pair buffer overflowed (three launches each)
+    n_emit = (6 if T > 0 else 0) + (6 if E > 0 else 0) + (1 if n_pts > 1 else 0)
     if n_pts > 0 and has_free_edges(sc):
         n_emit += 1                                   # point-edge pairs (one warp per free edge)
     # iter_begin, extent, count, 3 scan kernels, scatter, make_units, emission, colours of the
@@ -476,7 +478,8 @@ def main():
                                "proj_short_verts": n_s, "proj_short_planes": planes_s,
                                "big_cells": st["aux"][10] / per_iter, "big_table_scans": st["aux"][11] / per_iter,
                                "big_items": st["aux"][12] / per_iter, "bige_items": st["aux"][13] / per_iter,
-                               "big_cand": st["aux"][14] / per_iter},
+                               "big_cand": st["aux"][14] / per_iter,
+                               "pair_buffer_overflows": st["aux"][15] / per_iter},
             "kernel_sha": kernel_sha(),
         }
         print(json.dumps(line), flush=True)

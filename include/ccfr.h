@@ -79,6 +79,13 @@ typedef struct {
     float response_stiffness;  /* k (>= 0)                                                */
     float delta_v;        /* occlusion transition width (> 0 when delta > 0)             */
     float mu_s, mu_k;     /* static and kinetic friction coefficients (>= 0)             */
+    /* Candidate pairs buffered between the broad and the narrow kernels of
+     * the region build (Alg. 3): the vertex-face and oversized-primitive
+     * buffer holds pair_capacity x (triangles + edges) pairs, the edge-edge
+     * buffer 3 x pair_capacity x edges (plus 4096 each); 8 bytes a pair.
+     * 0 = 32.  A kind whose pairs overflow a buffer is redone by a fused
+     * kernel: the result is the same, only slower (stats aux[15]). */
+    int pair_capacity;
 } ccfr_params;
 
 /* Topology of one scene.  All arrays are device pointers, read at ccfr_create

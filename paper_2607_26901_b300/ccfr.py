@@ -35,7 +35,8 @@ class Params(C.Structure):
                 ("max_passes", C.c_int), ("solver_iters", C.c_int), ("plane_capacity", C.c_int),
                 ("cell_size", C.c_float), ("cell_factor", C.c_float), ("dt", C.c_float), ("gravity", C.c_float * 3),
                 ("compliance", C.c_float), ("flags", C.c_uint),
-                ("response_stiffness", C.c_float), ("delta_v", C.c_float), ("mu_s", C.c_float), ("mu_k", C.c_float)]
+                ("response_stiffness", C.c_float), ("delta_v", C.c_float), ("mu_s", C.c_float), ("mu_k", C.c_float),
+                ("pair_capacity", C.c_int)]
 
 
 class Mesh(C.Structure):
@@ -158,7 +159,8 @@ def _check(rc: int, what: str):
 
 
 def make_params(p: dict, flags: int = 0, plane_capacity: int | None = None,
-                iters: int | None = None, cell_size: float = 0.0, cell_factor: float = 0.0) -> Params:
+                iters: int | None = None, cell_size: float = 0.0, cell_factor: float = 0.0,
+                pair_capacity: int = 0) -> Params:
     o = Params()
     o.r, o.xi, o.delta, o.pad = p["r"], p["xi"], p.get("delta", 0.0), p["pad"]
     o.eps_retract, o.eps_dep, o.tau_feas = p["eps"], p["eps_dep"], p["tau_feas"]
@@ -175,6 +177,7 @@ def make_params(p: dict, flags: int = 0, plane_capacity: int | None = None,
     o.response_stiffness = p.get("k_resp", 0.0)
     o.delta_v = p.get("delta_v", 0.0)
     o.mu_s, o.mu_k = p.get("mu_s", 0.0), p.get("mu_k", 0.0)
+    o.pair_capacity = pair_capacity
     return o
 
 
@@ -240,8 +243,8 @@ class Context:
 
     @classmethod
     def from_scene(cls, scene, flags: int = 0, plane_capacity: int | None = None, iters: int | None = None,
-                   cell_size: float = 0.0, cell_factor: float = 0.0, stream=None):
-        p = make_params(scene.params, flags, plane_capacity, iters, cell_size, cell_factor)
+                   cell_size: float = 0.0, cell_factor: float = 0.0, pair_capacity: int = 0, stream=None):
+        p = make_params(scene.params, flags, plane_capacity, iters, cell_size, cell_factor, pair_capacity)
         ext = {}
         if len(getattr(scene, "links", ())) or len(getattr(scene, "tets", ())):
             ext = dict(links=scene.links, link_compliance=scene.link_compliance, tets=scene.tets,

@@ -102,6 +102,7 @@ ccfr_status check_params(const ccfr_params* p) {
     if (p->plane_capacity < 32 || p->plane_capacity % 32 != 0 || p->plane_capacity > 65536) return CCFR_ERR_INVALID_ARG;
     if (!(p->cell_size >= 0.f) || !(p->dt > 0.f) || !(p->compliance >= 0.f)) return CCFR_ERR_INVALID_ARG;
     if (!(p->cell_factor >= 0.f) || p->cell_factor > 64.f) return CCFR_ERR_INVALID_ARG;
+    if (p->pair_capacity < 0 || p->pair_capacity > 1024) return CCFR_ERR_INVALID_ARG;
     if (!(p->response_stiffness >= 0.f) || !(p->mu_s >= 0.f) || !(p->mu_k >= 0.f) || !(p->delta_v >= 0.f))
         return CCFR_ERR_INVALID_ARG;
     if (p->delta > 0.f && !(p->delta_v > 0.f)) return CCFR_ERR_INVALID_ARG;
@@ -367,9 +368,13 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.work, (size_t)N) == cudaSuccess;
     ok &= dalloc(c, &d.work_count, 2) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
-    d.bq_cap = BQ_PER_PRIM * ((long)T + E) + 4096;
+    const long pcap = params->pair_capacity > 0 ? params->pair_capacity : PAIR_CAP_DEFAULT;
+    d.bq_cap = pcap * ((long)T + E) + 4096;
     ok &= dalloc(c, &d.bq, (size_t)d.bq_cap) == cudaSuccess;
     ok &= dalloc(c, &d.bq_count, 1) == cudaSuccess;
+    d.eq_cap = 3 * pcap * (long)E + 4096;
+    ok &= dalloc(c, &d.eq, (size_t)d.eq_cap) == cudaSuccess;
+    ok &= dalloc(c, &d.eq_count, 1) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
     ok &= dalloc(c, &c->tile_sums, (size_t)n_tiles) == cudaSuccess;
     ok &= dalloc(c, &d.flags, 2) == cudaSuccess;

@@ -117,12 +117,15 @@ struct DevCtx {
     float4* big_box;            // [2 (n_tris + n_edges)] their padded boxes (lo + id, hi)
     int big_base[2];            // first slot of the triangles / edges
     unsigned* big_count;        // [2]
-    // candidate pairs of the oversized primitives between their broad and narrow
-    // kernels (oversized primitive first); bq_count[0] counts the pairs found
-    // (past bq_cap the buffer overflowed and the fused pass redoes the kind)
+    // candidate pairs between the broad and narrow kernels of the emission
+    // (MODE_BIGQ): bq for the kinds on the main stream (vertex-face, oversized
+    // primitives), eq for the edge-edge pairs of fitting edges (side stream)
     int2* bq;
-    unsigned* bq_count;         // [1]
+    u64* bq_count;              // [1]
     long bq_cap;
+    int2* eq;
+    u64* eq_count;              // [1]
+    long eq_cap;
     int2* units;                // [n_tris + n_edges + n_pts + 3] warp work units
     int unit_base[3];           // first unit slot of each query table
     unsigned* unit_count;       // [3]
@@ -180,10 +183,21 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // cell is the largest edge box.
 constexpr float BIGE_FACTOR = 2.0f;
 
-// Capacity of the oversized primitives' pair buffer, in pairs per triangle
-// and edge of the context (the cloth stack at 262,144 vertices finds about 7
-// per primitive in its most tangled substeps; an overflow only costs time).
-constexpr long BQ_PER_PRIM = 16;
+// Default capacity of the candidate-pair buffers (ccfr_params.pair_capacity):
+// the main-stream buffer holds 32 pairs per triangle and edge, the edge-edge
+// buffer 96 per edge.  The cloth stack at 262,144 vertices (520,200
+// triangles, 782,340 edges) finds about 42 vertex-face pairs per triangle
+// and 67 edge-edge pairs per edge in its initial layered state, and about 21
+// and 42 once tangled.  An overflow only costs time: the fused pass redoes
+// the kind.
+constexpr long PAIR_CAP_DEFAULT = 32;
+
+// One of the pair buffers, as a kernel argument.
+struct PairBuf {
+    int2* p;
+    u64* count;                 // pairs found (64-bit: it runs on past cap)
+    long cap;
+};
 
 __device__ __forceinline__ float cell_size_of(const DevCtx& c, int kind) {
     const bool big = kind == KIND_BIGE || kind == KIND_BIGS;

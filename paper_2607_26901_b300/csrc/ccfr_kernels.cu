@@ -568,6 +568,16 @@ __global__ void k_make_units(DevCtx c) {
 
 struct EmitCounters { u64 cand, acc, planes, fp64; };
 
+// Append the n (<= 32) pairs the lanes hold to a candidate-pair buffer (one
+// reservation per warp; the count runs on past the capacity, which tells the
+// fused pass to redo the kind).
+__device__ __forceinline__ void pb_put(const PairBuf& pb, int2 pr, int n, int lane) {
+    u64 base = 0;
+    if (lane == 0) base = atomicAdd(pb.count, (u64)n);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (lane < n && base + (u64)lane < (u64)pb.cap) pb.p[base + lane] = pr;
+}
+
 // Narrow phase of one queued pair (a = query id, b = item id).  VE: (isolated
 // point, free edge) pairs.
 template <int QK, int MODE, bool VE = false>
@@ -671,11 +681,16 @@ __device__ __forceinline__ void warp_cell_items(const DevCtx& c, int lane, bool 
 // all 27 cells of the vertex table.  The items of the scanned cells are
 // gathered 32 at a time (warp_cell_items), compacted into shared memory and
 // tested by every query lane against one broadcast item at a time.
-template <int QK, int MODE>
-// three blocks per SM: the edge-edge narrow phase would otherwise take enough
-// registers to leave room for two
-__global__ void __launch_bounds__(EMIT_WARPS * 32, 3) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po) {
+// MODE_BIGQ: the scan alone, its pairs written to pb for k_pair_narrow (the
+// scan then runs at the occupancy of its own small register set); FALLBACK:
+// the fused scan and narrow phase, run only when pb overflowed.
+template <int QK, int MODE, bool FALLBACK = false>
+// three blocks per SM with the narrow phase (the edge-edge one would otherwise
+// take enough registers to leave room for two), five for the scan alone
+__global__ void __launch_bounds__(EMIT_WARPS * 32, MODE == MODE_BIGQ ? 5 : 3) k_emit(DevCtx c, const float4* __restrict__ x, PairOut po,
+                                                             PairBuf pb) {
     if (c.flags[1]) return;
+    if (FALLBACK && *pb.count <= (u64)pb.cap) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
     __shared__ float4 items[EMIT_WARPS][64];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -744,7 +759,8 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32, 3) k_emit(DevCtx c, const flo
                     qn += __popc(hb);
                     if (qn >= 32) {
                         __syncwarp();
-                        process_pair<QK, MODE>(c, x, po, q[lane], k);
+                        if constexpr (MODE == MODE_BIGQ) pb_put(pb, q[lane], 32, lane);
+                        else process_pair<QK, MODE>(c, x, po, q[lane], k);
                         int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
                         __syncwarp();
                         if (lane < qn - 32) q[lane] = rest;
@@ -757,11 +773,17 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32, 3) k_emit(DevCtx c, const flo
         }
     }
     __syncwarp();
-    if (lane < qn) process_pair<QK, MODE>(c, x, po, q[lane], k);
+    if constexpr (MODE == MODE_BIGQ) {
+        if (qn > 0) pb_put(pb, q[lane], qn, lane);
+        return;                         // the narrow kernel counts the pairs
+    } else {
+        if (lane < qn) process_pair<QK, MODE>(c, x, po, q[lane], k);
+    }
     warp_add_u64(&c.stats->cand[QK], k.cand);
     warp_add_u64(&c.stats->pairs[QK], k.acc);
     warp_add_u64(&c.stats->planes_kind[QK], k.planes);
     if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
+    if (FALLBACK && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&c.stats->aux[15], 1ull);
 }
 
 // Oversized primitives (box larger than a cell): one warp per primitive scans
@@ -794,28 +816,20 @@ __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __re
     return scene;
 }
 
-// Append the n (<= 32) pairs the lanes hold to the oversized primitives'
-// pair buffer (one reservation per warp; the count runs on past the capacity,
-// which tells the fused pass to redo the kind).
-__device__ __forceinline__ void bq_put(const DevCtx& c, int2 pr, int n, int lane) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(c.bq_count, (unsigned)n);
-    base = __shfl_sync(FULL, base, 0);
-    if (lane < n && (long)base + lane < c.bq_cap) c.bq[base + lane] = pr;
-}
 
 // VE (QK = KIND_EDGE): every free edge against the isolated points of the
 // point-table cells its box reaches (pairs (point, edge)); one warp per free
 // edge, as for the oversized primitives, so that no point scans the far more
 // numerous edges of triangles.
-// MODE_BIGQ: the scan alone; its pairs go to c.bq for k_big_narrow, so that
+// MODE_BIGQ: the scan alone; its pairs go to pb for k_pair_narrow, so that
 // the scan runs at the occupancy of its own small register set.  FALLBACK:
 // the fused scan and narrow phase, run only when the pair buffer of this kind
-// overflowed (k_big_narrow then left the kind untouched).
+// overflowed (k_pair_narrow then left the kind untouched).
 template <int QK, int MODE, bool VE = false, bool FALLBACK = false>
-__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po) {
+__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po,
+                                                              PairBuf pb) {
     if (c.flags[1]) return;
-    if (FALLBACK && (long)*c.bq_count <= c.bq_cap) return;
+    if (FALLBACK && *pb.count <= (u64)pb.cap) return;
     __shared__ int2 queue[EMIT_WARPS][QCAP];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int2* q = queue[wib];
@@ -833,7 +847,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
         qn += __popc(hb);
         if (qn >= 32) {
             __syncwarp();
-            if constexpr (MODE == MODE_BIGQ) bq_put(c, q[lane], 32, lane);
+            if constexpr (MODE == MODE_BIGQ) pb_put(pb, q[lane], 32, lane);
             else process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
             int2 rest = (lane < qn - 32) ? q[32 + lane] : make_int2(0, 0);
             __syncwarp();
@@ -1002,7 +1016,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     }
     __syncwarp();
     if constexpr (MODE == MODE_BIGQ) {
-        if (qn > 0) bq_put(c, q[lane], qn, lane);
+        if (qn > 0) pb_put(pb, q[lane], qn, lane);
     } else {
         if (lane < qn) process_pair<VE ? KIND_PT : QK, MODE, VE>(c, x, po, q[lane], k);
     }
@@ -1025,22 +1039,23 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     warp_add_u64(&c.stats->aux[13], bige_items);
 }
 
-// Narrow phase of the oversized primitives' candidate pairs (MODE_BIGQ): one
+// Narrow phase of the candidate pairs a MODE_BIGQ scan wrote to pb: one
 // thread per pair, grid-strided, three blocks per SM; nothing when the buffer
-// overflowed.
-template <int QK>
-__global__ void __launch_bounds__(256, 3) k_big_narrow(DevCtx c, const float4* __restrict__ x, PairOut po) {
+// overflowed.  BIG: the pairs of the oversized primitives.
+template <int QK, bool BIG>
+__global__ void __launch_bounds__(256, 3) k_pair_narrow(DevCtx c, const float4* __restrict__ x, PairOut po,
+                                                        PairBuf pb) {
     if (c.flags[1]) return;
-    const unsigned n = *c.bq_count;
+    const u64 n = *pb.count;
     EmitCounters k{0, 0, 0, 0};
-    if ((long)n <= c.bq_cap)
-        for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-            process_pair<QK, MODE_PLANES>(c, x, po, c.bq[i], k);
+    if (n <= (u64)pb.cap)
+        for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+            process_pair<QK, MODE_PLANES>(c, x, po, pb.p[i], k);
     warp_add_u64(&c.stats->cand[QK], k.cand);
     warp_add_u64(&c.stats->pairs[QK], k.acc);
     warp_add_u64(&c.stats->planes_kind[QK], k.planes);
     if (QK == KIND_EDGE) warp_add_u64(&c.stats->ee_fp64, k.fp64);
-    warp_add_u64(&c.stats->aux[14], k.cand);
+    if (BIG) warp_add_u64(&c.stats->aux[14], k.cand);
 }
 
 // -------------------------------------------------------------- Alg. 1/2
@@ -2449,14 +2464,18 @@ __global__ void k_dmin_export(DevCtx c, float* out) {
 
 static inline int nblk(long n, int t) { return (int)((n + t - 1) / t); }
 
-// The oversized primitives of one kind: the scan into the pair buffer, the
-// narrow phase over it, and the fused pass that runs only if it overflowed.
-template <int QK>
-static void launch_big(const DevCtx& c, const float4* x, const PairOut& po, int G, cudaStream_t st) {
-    cudaMemsetAsync(c.bq_count, 0, sizeof(unsigned), st);
-    k_emit_big<QK, MODE_BIGQ><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
-    k_big_narrow<QK><<<G, 256, 0, st>>>(c, x, po);
-    k_emit_big<QK, MODE_PLANES, false, true><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+// The planes of one kind (BIG: of its oversized primitives): the scan into
+// the pair buffer pb, the narrow phase over it, and the fused pass that runs
+// only if pb overflowed.
+template <int QK, bool BIG>
+static void launch_emit(const DevCtx& c, const float4* x, const PairOut& po, const PairBuf& pb, int G,
+                        cudaStream_t st) {
+    cudaMemsetAsync(pb.count, 0, sizeof(u64), st);
+    if (BIG) k_emit_big<QK, MODE_BIGQ><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, pb);
+    else k_emit<QK, MODE_BIGQ><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, pb);
+    k_pair_narrow<QK, BIG><<<G, 256, 0, st>>>(c, x, po, pb);
+    if (BIG) k_emit_big<QK, MODE_PLANES, false, true><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, pb);
+    else k_emit<QK, MODE_PLANES, true><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, pb);
 }
 
 void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, const PairOutHost* poh,
@@ -2501,31 +2520,34 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
             cudaStreamWaitEvent(side->s, side->fork, 0);
             sb = side->s;
         }
-        if (c.n_tris > 0) k_emit<KIND_TRI, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        const PairBuf bq{c.bq, c.bq_count, c.bq_cap}, eq{c.eq, c.eq_count, c.eq_cap}, none{nullptr, nullptr, 0};
+        if (c.n_tris > 0) launch_emit<KIND_TRI, false>(c, x, po, bq, G, st);
         if (tm) tm->mark(ST_EMIT_VF, st);
-        if (c.n_tris > 0) launch_big<KIND_TRI>(c, x, po, G, st);
+        if (c.n_tris > 0) launch_emit<KIND_TRI, true>(c, x, po, bq, G, st);
         if (tm) tm->mark(ST_EMIT_VF_BIG, st);
-        if (c.n_edges > 0) k_emit<KIND_EDGE, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
+        if (c.n_edges > 0) launch_emit<KIND_EDGE, false>(c, x, po, eq, G, sb);
         if (tm) tm->mark(ST_EMIT_EE, st);
-        if (c.n_edges > 0) launch_big<KIND_EDGE>(c, x, po, G, st);
+        if (c.n_edges > 0) launch_emit<KIND_EDGE, true>(c, x, po, bq, G, st);
         if (tm) tm->mark(ST_EMIT_EE_BIG, st);
-        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
-        if (c.n_pts > 0 && c.n_free > 0) k_emit_big<KIND_EDGE, MODE_PLANES, true><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po);
+        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PLANES><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po, none);
+        if (c.n_pts > 0 && c.n_free > 0)
+            k_emit_big<KIND_EDGE, MODE_PLANES, true><<<G, EMIT_WARPS * 32, 0, sb>>>(c, x, po, none);
         if (tm) tm->mark(ST_EMIT_PP, st);
         if (fork) {
             cudaEventRecord(side->join, sb);
             cudaStreamWaitEvent(st, side->join, 0);
         }
     } else {
+        const PairBuf none{nullptr, nullptr, 0};
         if (c.n_tris > 0) {
-            k_emit<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
-            k_emit_big<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+            k_emit<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, none);
+            k_emit_big<KIND_TRI, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, none);
         }
         if (c.n_edges > 0) {
-            k_emit<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
-            k_emit_big<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+            k_emit<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, none);
+            k_emit_big<KIND_EDGE, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, none);
         }
-        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po);
+        if (c.n_pts > 1) k_emit<KIND_PT, MODE_PAIRS><<<G, EMIT_WARPS * 32, 0, st>>>(c, x, po, none);
     }
 }
 

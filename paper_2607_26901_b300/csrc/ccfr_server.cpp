@@ -115,7 +115,7 @@ namespace {
 // Device bytes of a context for n verts, e edges, t triangles and capacity k
 // (the allocations of ccfr_create, isolated points bounded by the vertices),
 // plus the resident state x, v.
-size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false) {
+size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false, int pair_cap = 0) {
     auto pow2 = [](long v) { long p = 64; while (p < v) p <<= 1; return p; };
     long buckets = pow2(t) + pow2(e) + pow2(n) + pow2(n) + 2 * pow2(e / 4) + pow2(e / 16) + 1;
     long items = t + e + 2 * n;
@@ -125,7 +125,8 @@ size_t ctx_bytes(long n, long e, long t, long k, bool keys, bool phi = false) {
     b += (size_t)e * (8 + 8 + 4 + 4);
     b += (size_t)t * 12;
     b += (size_t)buckets * 8 + (size_t)items * (4 + 32) + (size_t)(t + e + n + 3) * 8 + (size_t)(t + e) * 36;
-    b += (size_t)(t + e) * 16 * 8 + 4096 * 8;   // oversized primitives' pair buffer
+    const size_t pc = pair_cap > 0 ? (size_t)pair_cap : 32;
+    b += ((size_t)(t + e) * pc + (size_t)e * 3 * pc + 2 * 4096) * 8;   // candidate-pair buffers
     b += 2 * (size_t)n * 16;               // resident x, v
     return b + (1 << 20);
 }
@@ -302,17 +303,18 @@ void form_pools(ccfr_server* sv) {
     }
     for (Pool& P : sv->pools) {
         long ne = 0, nt = 0;
-        int K = 0;
+        int K = 0, pc = 0;
         bool phi = false;
         for (int k : P.members) {
             const SceneRec& sc = sv->scenes[k];
             ne += sc.n_edges;
             nt += sc.n_tris;
             K = sc.params.plane_capacity;
+            pc = sc.params.pair_capacity;
             phi = sc.params.delta > 0.f;
         }
         const long nv = P.voff.back();
-        P.bytes = ctx_bytes(nv, ne, nt, K, false, phi) + (size_t)nv * 2 + P.members.size() * 20;
+        P.bytes = ctx_bytes(nv, ne, nt, K, false, phi, pc) + (size_t)nv * 2 + P.members.size() * 20;
         P.hmask.assign(P.members.size(), 0);
     }
 }
@@ -546,7 +548,8 @@ ccfr_status ccfr_server_add_scene(ccfr_server* sv, int n_verts, int n_edges, int
     sc.rest = sc.x;
     sc.params = *params;
     sc.params.flags &= ~(unsigned)CCFR_FLAG_STORE_KEYS;
-    sc.bytes = ctx_bytes(n_verts, n_edges, n_tris, params->plane_capacity, false, params->delta > 0.f);
+    sc.bytes = ctx_bytes(n_verts, n_edges, n_tris, params->plane_capacity, false, params->delta > 0.f,
+                         params->pair_capacity);
     if (sc.bytes > sv->budget) return CCFR_ERR_OOM;
     sv->scenes.push_back(std::move(sc));
     *scene_id = (int)sv->scenes.size() - 1;

@@ -33,7 +33,7 @@ def test_status_strings_without_gpu():
 
 def test_struct_layouts():
     # ccfr_params: 7 floats, 3 ints, 3 floats, 3 floats, float, unsigned
-    assert C.sizeof(ccfr.Params) == 4 * 22
+    assert C.sizeof(ccfr.Params) == 4 * 23
     assert C.sizeof(ccfr.Mesh) == 3 * 4 + 4 + 3 * 8
     assert C.sizeof(ccfr.Stats) == 34 * 8 + 8 + 3 * 8
     assert C.sizeof(ccfr.MeshExt) == 40 + 4 + 4 + 8 + 8 + 4 + 4 + 8 + 4 + 4

@@ -1,16 +1,16 @@
-"""The oversized primitives' pass (Alg. 3's broad and narrow phase for the
-triangles and edges whose boxes span more than a grid cell): a scan kernel
-writes their candidate pairs to a pair buffer and a narrow kernel computes the
-planes; when the buffer overflows, the fused scan-and-narrow kernel redoes the
-kind instead.  The cell size decides only which primitives are oversized, not
-the candidate set, so both paths must give the oracle's regions.
+"""The region build's two-kernel emission (Alg. 3's broad and narrow phase):
+scan kernels write the candidate pairs of each kind (vertex-face, edge-edge,
+and those of the primitives whose boxes span more than a grid cell) to a
+pair buffer, narrow kernels compute the planes; a kind whose pairs overflow
+the buffer is redone by the fused scan-and-narrow kernel.  Neither the cell
+size nor the buffer capacity may change the candidate set or the regions.
 
 Scene: a 3 x 16 x 16 cloth stack moved by 0.3 of its predicted step (edges
-stretched to a few cells).  At the default cell factor some edges are
-oversized and the buffer holds their pairs; at cell factor 0.3 nearly every
-primitive is oversized, the edge-edge pairs (about 125k) exceed the buffer
-(16 per triangle and edge plus 4096, 59,536 here) while the vertex-face pairs
-(about 47k) fit, so one kind takes each path."""
+stretched to a few cells; about 47k vertex-face and 125k edge-edge candidate
+pairs).  Cases: the defaults (no kind overflows; some edges oversized), a
+capacity of one pair per primitive (the vertex-face and edge-edge buffers
+overflow and the fused kernels redo those kinds), and cell factor 0.3 (nearly
+every primitive oversized)."""
 import numpy as np
 import pytest
 
@@ -36,18 +36,23 @@ def tangled_stack():
     return sc
 
 
-@pytest.mark.parametrize("cell_factor, overflow", [(0.0, False), (0.3, True)])
-def test_oversized_pass_parity(orc, cell_factor, overflow):
+@pytest.mark.parametrize("cell_factor, pair_capacity", [(0.0, 0), (0.0, 1), (0.3, 0)])
+def test_emission_paths_parity(orc, cell_factor, pair_capacity):
     sc = tangled_stack()
     x = torch.as_tensor(sc.x).cuda().contiguous()
-    ctx = ccfr.Context.from_scene(sc, flags=ccfr.FLAG_STORE_KEYS, plane_capacity=K, cell_factor=cell_factor)
+    ctx = ccfr.Context.from_scene(sc, flags=ccfr.FLAG_STORE_KEYS, plane_capacity=K, cell_factor=cell_factor,
+                                  pair_capacity=pair_capacity)
     ctx.reset_stats()
     ctx.build_regions(x)
     torch.cuda.synchronize()
     st = ctx.stats()
     assert st["aux"][4] > 0                               # oversized edges
-    assert st["aux"][3] > 0 or not overflow               # and triangles, at the small cell factor
-    assert (st["aux"][15] > 0) == overflow, st["aux"][15]  # fused fallback launches
+    if cell_factor > 0:
+        assert st["aux"][3] > 0                           # and triangles, at the small cell factor
+    if pair_capacity == 1:
+        assert st["aux"][15] >= 2, st["aux"][15]          # vertex-face and edge-edge redone fused
+    elif cell_factor == 0:
+        assert st["aux"][15] == 0, st["aux"][15]
 
     # candidate sets (the pair-listing mode) stay bit-exact
     got = ctx.candidates(x)
