@@ -1182,14 +1182,15 @@ __device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float e
 
 __device__ __forceinline__ float rho_at(f3 y, float4 P) { return fmaf(y.x, P.x, fmaf(y.y, P.y, fmaf(y.z, P.z, P.w))); }
 
-// Bitwise-identical planes (one contact reached through several pairs).  In
-// the pass order they are adjacent (equal key, hash and bits), and a copy of
-// the plane just visited is a no-op for Alg. 1 (beta = 0: the iterate is
-// already on it) and for the pass result (its violation was counted with the
-// first copy), so the walks skip it.
-__device__ __forceinline__ bool same_bits(float4 a, float4 b) {
-    return __float_as_uint(a.x) == __float_as_uint(b.x) && __float_as_uint(a.y) == __float_as_uint(b.y) &&
-           __float_as_uint(a.z) == __float_as_uint(b.z) && __float_as_uint(a.w) == __float_as_uint(b.w);
+// Copies of one plane (one contact reached through several pairs): equal in
+// value, bitwise or up to the sign of a zero component.  A copy of the plane
+// just visited is a no-op for Alg. 1 (beta = 0: the iterate is already on it)
+// and for the pass result (its violation was counted with the first copy), so
+// the walks skip it.  Comparing values rather than bits also makes the visit
+// count independent of the arrival order of copies that differ only in the
+// sign of a zero (those can tie in the pass order up to their slots).
+__device__ __forceinline__ bool same_plane(float4 a, float4 b) {
+    return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w;
 }
 
 // One pass of Alg. 2 in progress: the pass input, the binary32 iterate y
@@ -1430,7 +1431,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
             float key;
             int j;
             get(e, P, key, j);
-            if (rho_at(W.y, P) < 0.f && (first || !same_bits(P, tup_plane(cur)))) {
+            if (rho_at(W.y, P) < 0.f && (first || !same_plane(P, tup_plane(cur)))) {
                 Tup t = make_tup(key, P, j);
                 if ((first || tless(cur, t)) && tless(t, best)) best = t;
             }
@@ -1561,7 +1562,7 @@ __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, 
         const float4 P = (e < m) ? pl[sb.idx[0][e]] : make_float4(0.f, 0.f, 0.f, 0.f);
         int lo = 0;   // lanes below lo are already behind the walk
         for (;;) {
-            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f && !same_bits(P, Plast);
+            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f && !same_plane(P, Plast);
             const unsigned bal = __ballot_sync(FULL, viol);
             if (!bal) break;
             const int f = __ffs(bal) - 1;
@@ -2000,7 +2001,7 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
                 const float4 Pcur = tup_plane(cur);
                 for (int j = 0; j < np; ++j) {
                     const float4 P = pl[j];
-                    if (rho_at(W.y, P) < 0.f && (first || !same_bits(P, Pcur))) {
+                    if (rho_at(W.y, P) < 0.f && (first || !same_plane(P, Pcur))) {
                         const Tup t = make_tup(rho_at(y0, P), P, j);
                         if ((first || tless(cur, t)) && tless(t, best)) best = t;
                     }
