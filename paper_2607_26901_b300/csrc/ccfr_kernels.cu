@@ -1156,6 +1156,7 @@ template <typename R> struct Ero {
     V3<R> V[3];
     f3 A[3];
     R B[3];
+    V3<R> D[3];   // A[j] - A[0] in R (exact: a difference of two binary32 values), j >= 1
 };
 
 // One Alg. 1 step with |V| >= 1 stored lines: project zt onto the
@@ -1169,7 +1170,8 @@ __device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float e
     const f3 n0 = S.A[0];
     const R b0 = S.B[0];
     const V3<R> vm = S.V[m - 1];
-    const R beta_u = v3_dot(v3_diff<R>(n, n0), vm);
+    const V3<R> dn = v3_diff<R>(n, n0);
+    const R beta_u = v3_dot(dn, vm);
     if (X::abs_lt(beta_u, eps)) return;
     const V3<R> nd = v3_of<R>(n);
     const V3<R> u = v3_axpy(X::div(X::sub(b, v3_dot(nd, zt)), beta_u), vm, zt);
@@ -1177,22 +1179,22 @@ __device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float e
     #pragma unroll
     for (int j = 1; j <= 2; ++j) {
         if (j > m) break;
-        const f3 nj = (j < m) ? S.A[j] : n;
         const R bj = (j < m) ? S.B[j] : b;
-        const V3<R> dnj = v3_diff<R>(nj, n0);
+        const V3<R> dnj = (j < m) ? S.D[j] : dn;
         const R beta_w = v3_dot(dnj, S.V[j - 1]);
         if (X::abs_gt(beta_w, eps))
             w = v3_axpy(X::div(X::sub(X::sub(bj, b0), v3_dot(dnj, w)), beta_w), S.V[j - 1], w);
     }
     const V3<R> vn = v3_sub(w, u);
     if (X::gt(v3_dot(vn, vn), eps * eps)) {
-        const V3<R> n0d = v3_of<R>(n0);
+        const V3<R> n0d = S.V[0];   // the first line's vector is its normal, in R
         const R beta_new = v3_dot(n0d, vn);
         zt = X::abs_lt(beta_new, eps) ? u : v3_axpy(X::div(X::sub(b0, v3_dot(n0d, u)), beta_new), vn, u);
         if (S.m < 3) {
             S.V[S.m] = vn;
             S.A[S.m] = n;
             S.B[S.m] = b;
+            S.D[S.m] = dn;
             S.m++;
         }
     }
@@ -1228,6 +1230,7 @@ template <typename R> struct Walk {
     int nv;
     bool lazy0;
     float4 P0;
+    V3<R> yp;     // the pass input in R, formed with the first step in R
     V3<R> z;
     Ero<R> S;
 };
@@ -1276,13 +1279,13 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
     } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
         // (a normal equal to the first line's gives beta_u = (n - n0) . v = 0
         // exactly, and Alg. 1 leaves the iterate unchanged: skipped)
-        const V3<R> yp = v3_of<R>(W.ypass);
         if (W.lazy0) {
-            walk_lazy0(W, yp);
+            W.yp = v3_of<R>(W.ypass);
+            walk_lazy0(W, W.yp);
             W.lazy0 = false;
         }
-        ortho_step<R>(W.z, xyz(P), plane_b<R>(P, yp), W.S, eps_dep);
-        const V3<R> yn = v3_add(yp, W.z);
+        ortho_step<R>(W.z, xyz(P), plane_b<R>(P, W.yp), W.S, eps_dep);
+        const V3<R> yn = v3_add(W.yp, W.z);
         W.y = mk(XP<R>::to_float(yn.x), XP<R>::to_float(yn.y), XP<R>::to_float(yn.z));
     }
     const f3 dz = sub(W.y, W.ypass);
@@ -1307,10 +1310,12 @@ __device__ __forceinline__ void walk_visit_warp(Walk<double>& W, float4 P, float
         }
     } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
         if (lane == 0) {
-            const V3<double> yp = v3_of<double>(W.ypass);
-            if (W.lazy0) walk_lazy0(W, yp);
-            ortho_step<double>(W.z, xyz(P), plane_b<double>(P, yp), W.S, eps_dep);
-            const V3<double> yn = v3_add(yp, W.z);
+            if (W.lazy0) {
+                W.yp = v3_of<double>(W.ypass);
+                walk_lazy0(W, W.yp);
+            }
+            ortho_step<double>(W.z, xyz(P), plane_b<double>(P, W.yp), W.S, eps_dep);
+            const V3<double> yn = v3_add(W.yp, W.z);
             W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
         }
         W.lazy0 = false;
