@@ -1112,6 +1112,8 @@ template <> struct XP<double> {
     static __device__ __forceinline__ bool abs_gt(double a, float e) { return fabs(a) > (double)e; }
     static __device__ __forceinline__ bool gt(double a, float e) { return a > (double)e; }
     static __device__ __forceinline__ float to_float(double a) { return (float)a; }
+    // a - b from the binary32 values and their R conversions: exact, as diff
+    static __device__ __forceinline__ double diff2(float, double ad, float, double bd) { return ad - bd; }
 };
 template <> struct XP<dfl> {
     static __device__ __forceinline__ dfl make(float a) { return df_make(a); }
@@ -1126,6 +1128,7 @@ template <> struct XP<dfl> {
     static __device__ __forceinline__ bool abs_gt(dfl a, float e) { return fabsf(a.hi) > e; }
     static __device__ __forceinline__ bool gt(dfl a, float e) { return a.hi > e; }
     static __device__ __forceinline__ float to_float(dfl a) { return df_to_float(a); }
+    static __device__ __forceinline__ dfl diff2(float a, dfl, float b, dfl) { return two_sum(a, -b); }
 };
 
 template <typename R> struct V3 { R x, y, z; };
@@ -1164,16 +1167,17 @@ template <typename R> struct Ero {
 // a single plane, is taken in binary32 by the caller.)  The |v| > eps_dep
 // test compares squares (no square root).
 template <typename R>
-__device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, R b, Ero<R>& S, float eps) {
+__device__ __noinline__ void ortho_step(V3<R>& zt, f3 n, const V3<R>& nd, R b, Ero<R>& S, float eps) {
     using X = XP<R>;
     const int m = S.m;
     const f3 n0 = S.A[0];
     const R b0 = S.B[0];
     const V3<R> vm = S.V[m - 1];
-    const V3<R> dn = v3_diff<R>(n, n0);
+    // (S.V[0] is the first line's normal n0 in R)
+    const V3<R> dn = v3<R>(X::diff2(n.x, nd.x, n0.x, S.V[0].x), X::diff2(n.y, nd.y, n0.y, S.V[0].y),
+                           X::diff2(n.z, nd.z, n0.z, S.V[0].z));
     const R beta_u = v3_dot(dn, vm);
     if (X::abs_lt(beta_u, eps)) return;
-    const V3<R> nd = v3_of<R>(n);
     const V3<R> u = v3_axpy(X::div(X::sub(b, v3_dot(nd, zt)), beta_u), vm, zt);
     V3<R> w = nd;
     #pragma unroll
@@ -1244,9 +1248,10 @@ template <typename R> __device__ __forceinline__ void walk_begin(Walk<R>& W, f3 
     W.S.m = 0;
 }
 
-// b = -d - n . ypass of the plane n . z = b in coordinates centred at ypass
-template <typename R> __device__ __forceinline__ R plane_b(float4 P, const V3<R>& yp) {
-    return XP<R>::neg(XP<R>::add(XP<R>::make(P.w), v3_dot(v3_of<R>(xyz(P)), yp)));
+// b = -d - n . ypass of the plane (n, d) as n . z = b in coordinates centred
+// at ypass, from the normal already converted to R (nd)
+template <typename R> __device__ __forceinline__ R plane_b_nd(float w, const V3<R>& nd, const V3<R>& yp) {
+    return XP<R>::neg(XP<R>::add(XP<R>::make(w), v3_dot(nd, yp)));
 }
 
 // The first step's ERO entry and its iterate in R (z = (b0 / |n0|^2) n0 in
@@ -1254,7 +1259,7 @@ template <typename R> __device__ __forceinline__ R plane_b(float4 P, const V3<R>
 template <typename R> __device__ __forceinline__ void walk_lazy0(Walk<R>& W, const V3<R>& yp) {
     W.S.A[0] = xyz(W.P0);
     W.S.V[0] = v3_of<R>(xyz(W.P0));
-    W.S.B[0] = plane_b<R>(W.P0, yp);
+    W.S.B[0] = plane_b_nd<R>(W.P0.w, W.S.V[0], yp);
     const R beta0 = v3_dot(W.S.V[0], W.S.V[0]);
     const R s0 = XP<R>::div(W.S.B[0], beta0);
     W.z = v3<R>(XP<R>::mul(s0, W.S.V[0].x), XP<R>::mul(s0, W.S.V[0].y), XP<R>::mul(s0, W.S.V[0].z));
@@ -1284,7 +1289,8 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
             walk_lazy0(W, W.yp);
             W.lazy0 = false;
         }
-        ortho_step<R>(W.z, xyz(P), plane_b<R>(P, W.yp), W.S, eps_dep);
+        const V3<R> nd = v3_of<R>(xyz(P));
+        ortho_step<R>(W.z, xyz(P), nd, plane_b_nd<R>(P.w, nd, W.yp), W.S, eps_dep);
         const V3<R> yn = v3_add(W.yp, W.z);
         W.y = mk(XP<R>::to_float(yn.x), XP<R>::to_float(yn.y), XP<R>::to_float(yn.z));
     }
@@ -1314,7 +1320,8 @@ __device__ __forceinline__ void walk_visit_warp(Walk<double>& W, float4 P, float
                 W.yp = v3_of<double>(W.ypass);
                 walk_lazy0(W, W.yp);
             }
-            ortho_step<double>(W.z, xyz(P), plane_b<double>(P, W.yp), W.S, eps_dep);
+            const V3<double> nd = v3_of<double>(xyz(P));
+            ortho_step<double>(W.z, xyz(P), nd, plane_b_nd<double>(P.w, nd, W.yp), W.S, eps_dep);
             const V3<double> yn = v3_add(W.yp, W.z);
             W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
         }
