@@ -393,8 +393,9 @@ ccfr_status ccfr_server_results(ccfr_server* sv, long n, double* t_arrival, doub
 /* Current state of a scene (host arrays, n_verts x 4 floats each). */
 ccfr_status ccfr_server_get_state(ccfr_server* sv, int scene_id, float* x, float* v);
 ccfr_status ccfr_server_get_info(ccfr_server* sv, ccfr_server_info* out);
-/* Device bytes a resident scene takes (context, plane lists, state), the
- * amount the server charges against its budget. */
+/* Device bytes a resident scene takes (context, plane lists, candidate-pair
+ * buffers at the default pair_capacity, state), the amount the server charges
+ * against its budget for a scene with that capacity. */
 ccfr_status ccfr_estimate_bytes(int n_verts, int n_edges, int n_tris, int plane_capacity, size_t* bytes);
 /* Test hook: steps of the scene are treated as never finishing (no GPU work
  * is issued), to exercise the bounded wait. */
