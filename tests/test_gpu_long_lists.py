@@ -1,0 +1,99 @@
+"""Alg. 2 on plane lists longer than the projection's shared-memory sort
+buffer (1,024 gathered planes): the heavy kernel then walks the full list in
+global memory, selecting each next plane in the pass order (the same order as
+the sorted walk).  GPU against the oracle on identical binary32 planes and
+inputs, next to the same construction at 900 planes (sorted in shared memory).
+
+Input: 48 vertices, each with its own synthetic plane list: normals in a
+cone around the direction opposite to the vertex's displacement (many
+near-duplicate contacts, as in the cloth stack), offsets that put rho at the
+candidate uniformly in [-0.2 r, 0.2 r] (about half violated) and keep the
+build position inside every plane.  Every plane is within the gather bound
+2 |rho_min|, so the 1,400-plane lists exceed the sort buffer."""
+import numpy as np
+import pytest
+
+from paper_2607_26901_b300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2607_26901_b300 import ccfr  # noqa: E402
+
+TOL_REL = 1e-5
+BAND_REL = 1e-7
+K = 2048
+
+
+def long_list_case(n_planes, cone, seed=5, n=48):
+    rng = np.random.default_rng(seed)
+    g = np.stack(np.meshgrid(np.arange(4), np.arange(4), np.arange(3), indexing="ij"), -1).reshape(-1, 3)[:n]
+    x4 = np.zeros((n, 4), np.float32)
+    x4[:, :3] = g * 0.01
+    x4[:, 3] = 1.0 / 5e-4
+    sc = S.Scene("long_lists", x4, np.zeros((n, 4), np.float32), np.zeros((0, 3), np.int32),
+                 np.zeros((0, 2), np.int32), S.default_params(2e-3, 1e-3, plane_capacity=K))
+    r = sc.params["r"]
+    x = x4[:, :3].astype(np.float64)
+    d = rng.normal(size=(n, 3))
+    d *= (0.5 * r / np.linalg.norm(d, axis=1))[:, None]
+    xp = (x + d).astype(np.float32).astype(np.float64)
+    planes = np.zeros((n, K, 4), np.float32)
+    cnt = np.full(n, n_planes, np.int32)
+    for v in range(n):
+        u = -d[v] / np.linalg.norm(d[v])
+        nn = u[None, :] + cone * rng.normal(size=(n_planes, 3))
+        nn = (nn / np.linalg.norm(nn, axis=1)[:, None]).astype(np.float32)
+        dn = (xp[v] - x[v]) @ nn.astype(np.float64).T
+        s = rng.uniform(-0.2 * r, 0.2 * r, n_planes)
+        planes[v, :n_planes, :3] = nn
+        planes[v, :n_planes, 3] = np.maximum(-dn + s, 0.0).astype(np.float32)
+    return sc, x, xp, planes, cnt
+
+
+@pytest.mark.parametrize("n_planes", [900, 1400])
+@pytest.mark.parametrize("cone", [0.01, 0.05])
+def test_long_list_projection_parity(orc, n_planes, cone):
+    sc, x, xp, planes, cnt = long_list_case(n_planes, cone)
+    n = sc.n_verts
+    L = orc.scene_scale(sc.x)
+    P = orc.make_params(sc.params, band=BAND_REL * L, capacity=K)
+    offs = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int64)
+    flat = np.concatenate([planes[v, :cnt[v]].astype(np.float64) for v in range(n)])
+    keys = np.arange(len(flat), dtype=np.uint64)
+    out, halt, band, nviol = orc.project(x, xp, sc.x[:, 3], offs, flat, keys, None, P)
+
+    xd = torch.as_tensor(sc.x).cuda().contiguous()
+    xio = torch.as_tensor(np.concatenate([xp, sc.x[:, 3:4]], axis=1).astype(np.float32)).cuda().contiguous()
+    ctx = ccfr.Context.from_scene(sc, plane_capacity=K)
+    ctx.load_regions(torch.as_tensor(planes).cuda(), torch.as_tensor(cnt).cuda())
+    ctx.reset_stats()
+    h = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    ctx.project(xd, xio, h)
+    torch.cuda.synchronize()
+    st = ctx.stats()
+    full_passes = st["aux"][1]
+    if n_planes > 1024:
+        assert full_passes > 0, st["aux"][:3]          # the global-memory walk ran
+    else:
+        assert full_passes == 0, st["aux"][:3]         # every list sorted in shared memory
+    got = xio.cpu().numpy()[:, :3].astype(np.float64)
+    ok = band == 0
+    assert (nviol > 0).all()
+    assert ok.sum() >= 0.75 * n, int(ok.sum())
+    err = np.abs(got - out).max(axis=1)
+    bad = np.nonzero(ok & (err > TOL_REL * L))[0]
+    assert len(bad) == 0, [(int(b), float(err[b]), int(nviol[b]), int(halt[b])) for b in bad[:5]]
+    np.testing.assert_array_equal(h.cpu().numpy()[ok], halt[ok])
+    # band-excluded vertices: a valid outcome on their own planes (halted at the build position,
+    # or inside every plane within tau plus the bar)
+    for v in np.nonzero(~ok)[0]:
+        dv = got[v] - x[v]
+        if np.all(got[v] == sc.x[v, :3].astype(np.float64)):
+            continue
+        p = planes[v, :cnt[v]].astype(np.float64)
+        assert (p[:, :3] @ dv + p[:, 3]).min() >= -(P.tau_feas + TOL_REL * L), int(v)
+    ctx.close()
