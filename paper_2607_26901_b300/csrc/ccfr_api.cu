@@ -366,7 +366,7 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.big, (size_t)T + E) == cudaSuccess;
     ok &= dalloc(c, &d.big_box, 2 * ((size_t)T + E)) == cudaSuccess;
     ok &= dalloc(c, &d.work, (size_t)N) == cudaSuccess;
-    ok &= dalloc(c, &d.work_count, 2) == cudaSuccess;
+    ok &= dalloc(c, &d.work_count, 4) == cudaSuccess;
     ok &= dalloc(c, &d.big_count, 2) == cudaSuccess;
     const long pcap = params->pair_capacity > 0 ? params->pair_capacity : PAIR_CAP_DEFAULT;
     d.bq_cap = pcap * ((long)T + E) + 4096;

@@ -155,7 +155,8 @@ struct DevCtx {
     const unsigned char* active;
     int4* work;                 // [n_verts] vertices queued for the second projection kernels:
                                 //   long plane lists from the front, short ones from the back
-    unsigned* work_count;       // [2] queue lengths: long lists, short lists
+    unsigned* work_count;       // [4] queue lengths (long lists, short lists), the long-list
+                                //   kernel's next queue entry, spare
     DevStats* stats;
 };
 

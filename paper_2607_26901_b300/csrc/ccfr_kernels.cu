@@ -1859,8 +1859,14 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, 
     SortBuf& sb = reinterpret_cast<SortBuf*>(proj_smem)[threadIdx.x >> 5];
     const float U = 5.9604645e-8f;   // unit roundoff of binary32
     const unsigned nwork = c.work_count[0];
-    const unsigned stride = gridDim.x * PROJ_WARPS;
-    for (unsigned wi = blockIdx.x * PROJ_WARPS + (threadIdx.x >> 5); wi < nwork; wi += stride) {
+    // the queued vertices are taken one at a time from a shared counter (their costs vary
+    // with the list length and the number of visits; a fixed stride left long tails)
+    auto next = [&]() {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(&c.work_count[2], 1u);
+        return __shfl_sync(FULL, w, 0);
+    };
+    for (unsigned wi = next(); wi < nwork; wi = next()) {
         const int4 wk = c.work[wi];
         const int v = wk.x;
         const float mn = __int_as_float(wk.y), dabs = __int_as_float(wk.z);
@@ -2615,7 +2621,7 @@ void launch_clear_regions(const DevCtx& c, cudaStream_t st) {
 
 void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned char* halt, cudaStream_t st) {
     long threads = (long)c.n_verts * 32;
-    cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
+    cudaMemsetAsync(c.work_count, 0, 4 * sizeof(unsigned), st);
     if (threads > 0) {
         k_project<false><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
         k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
@@ -2648,7 +2654,7 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
         k_response<<<nblk(c.n_verts, RESP_WARPS * 32), RESP_WARPS * 32, 0, st>>>(c, x);
     if (tm) tm->mark(ST_RESPONSE, st);
     long threads = (long)c.n_verts * 32;
-    cudaMemsetAsync(c.work_count, 0, 2 * sizeof(unsigned), st);
+    cudaMemsetAsync(c.work_count, 0, 4 * sizeof(unsigned), st);
     if (threads > 0) k_project<true><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
     if (threads > 0) k_project_heavy<true><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
@@ -2699,8 +2705,8 @@ constexpr int STATIC_MAX_VERTS = 1 << 18;   // 262,144 vertices
 struct StaticScratch {
     DevStats stats;
     int flags[2];
-    unsigned work_count[2];
-    unsigned pad_[12];
+    unsigned work_count[4];
+    unsigned pad_[10];
     int4 work[STATIC_MAX_VERTS];
     unsigned dmin[STATIC_MAX_VERTS];
 };
