@@ -376,6 +376,7 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     ok &= dalloc(c, &d.eq, (size_t)d.eq_cap) == cudaSuccess;
     ok &= dalloc(c, &d.eq_count, 1) == cudaSuccess;
     ok &= dalloc(c, &d.unit_count, 3) == cudaSuccess;
+    ok &= dalloc(c, &d.sched, N_SCHED) == cudaSuccess;
     ok &= dalloc(c, &c->tile_sums, (size_t)n_tiles) == cudaSuccess;
     ok &= dalloc(c, &d.flags, 2) == cudaSuccess;
     ok &= dalloc(c, &d.stats, 1) == cudaSuccess;

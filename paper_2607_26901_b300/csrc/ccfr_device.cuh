@@ -129,6 +129,8 @@ struct DevCtx {
     int2* units;                // [n_tris + n_edges + n_pts + 3] warp work units
     int unit_base[3];           // first unit slot of each query table
     unsigned* unit_count;       // [3]
+    unsigned* sched;            // [N_SCHED] next-work counters of the emission launches of one
+                                //   build (zeroed at its start), one per kernel instance
     unsigned* bucket_count;     // [Mtot + 1] counts, then exclusive scan (start)
     unsigned* bucket_fill;      // [Mtot]
     unsigned* item_bucket;      // [n_items]
@@ -183,6 +185,7 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // BIGE_FACTOR edge cells; the few larger than that ("giants") to a table whose
 // cell is the largest edge box.
 constexpr float BIGE_FACTOR = 2.0f;
+constexpr int N_SCHED = 24;
 
 // Default capacity of the candidate-pair buffers (ccfr_params.pair_capacity):
 // the main-stream buffer holds 32 pairs per triangle and edge, the edge-edge

@@ -704,11 +704,18 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32, MODE == MODE_BIGQ ? 5 : 3) k_
     const float inv = 1.0f / cell_size_of(c, QK);
     const unsigned ibase = (unsigned)c.bucket_base[IK], imask = (unsigned)c.bucket_mask[IK];
     const unsigned nunits = c.unit_count[QK];
-    const unsigned stride = gridDim.x * EMIT_WARPS;
+    // work units are taken one at a time from this launch's counter (their cells hold
+    // very different numbers of items)
+    unsigned* const ctr = c.sched + QK * 3 + (MODE == MODE_BIGQ ? 0 : MODE == MODE_PAIRS ? 1 : 2);
+    auto next = [&]() {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(ctr, 1u);
+        return __shfl_sync(FULL, w, 0);
+    };
     // this lane's neighbour offset (cell order (z, y, x); index 13 is the cell itself)
     const int oi = HALF ? 13 + lane : lane;
     const int ox = oi % 3 - 1, oy = (oi / 3) % 3 - 1, oz = oi / 9 - 1;
-    for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nunits; u += stride) {
+    for (unsigned u = next(); u < nunits; u = next()) {
         int2 U = c.units[c.unit_base[QK] + u];
         unsigned s0 = c.bucket_count[U.x] + (unsigned)U.y, s1 = c.bucket_count[U.x + 1];
         unsigned n = min(32u, s1 - s0);
@@ -855,7 +862,14 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
     const int IK = (QK == KIND_TRI) ? KIND_VQ : KIND_EDGE;
     const unsigned nbig = VE ? (unsigned)c.n_free : c.big_count[QK];
     u64 big_cells = 0, big_scans = 0, big_items = 0, bige_items = 0;   // diagnostics
-    const unsigned stride = gridDim.x * EMIT_WARPS;
+    // oversized primitives are taken one at a time from this launch's counter (the cells
+    // their boxes reach vary by orders of magnitude)
+    unsigned* const ctr = c.sched + 9 + (VE ? 6 : QK * 3) + (MODE == MODE_BIGQ ? 0 : MODE == MODE_PAIRS ? 1 : 2);
+    auto next = [&]() {
+        unsigned w = 0;
+        if (lane == 0) w = atomicAdd(ctr, 1u);
+        return __shfl_sync(FULL, w, 0);
+    };
     // append a hit to the warp queue; process 32 queued pairs at a time
     auto push = [&](bool hit, int2 pr) {
         const unsigned hb = __ballot_sync(FULL, hit);
@@ -873,7 +887,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
             __syncwarp();
         }
     };
-    for (unsigned u = blockIdx.x * EMIT_WARPS + wib; u < nbig; u += stride) {
+    for (unsigned u = next(); u < nbig; u = next()) {
         const int o = VE ? c.free_list[u] : c.big[c.big_base[QK] + u];
         float lo[3], hi[3];
         bool qimm;
@@ -2529,6 +2543,7 @@ void launch_build(const DevCtx& c, const float4* x, cudaStream_t st, int mode, c
     cudaMemsetAsync(c.big_count, 0, 2 * sizeof(unsigned), st);
     cudaMemsetAsync(c.bucket_count, 0, (size_t)(n_buckets_total + 1) * sizeof(unsigned), st);
     cudaMemsetAsync(c.bucket_fill, 0, (size_t)n_buckets_total * sizeof(unsigned), st);
+    cudaMemsetAsync(c.sched, 0, N_SCHED * sizeof(unsigned), st);
     if (tm) tm->mark(ST_MISC, st);
     if (c.n_items > 0) k_extent<<<nblk(c.n_items, 256), 256, 0, st>>>(c, x);
     if (tm) tm->mark(ST_GRID_EXTENT, st);
