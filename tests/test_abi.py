@@ -50,6 +50,11 @@ def test_host_checks_reject_bad_arguments_without_gpu():
     p.r, p.xi, p.pad, p.eps_dep, p.dt, p.solver_iters = 1e-3, 1e-3, 1.5e-3, 1e-6, 1 / 60, 1
     p.plane_capacity = 33                      # not a multiple of 32
     assert lib.ccfr_create(C.byref(m), C.byref(p), None, C.byref(h)) == 1
+    p.plane_capacity = 64
+    for bad in (-1, 1025):                     # candidate-pair buffer capacity out of range
+        p.pair_capacity = bad
+        assert lib.ccfr_create(C.byref(m), C.byref(p), None, C.byref(h)) == 1
+    p.pair_capacity = 0
     assert lib.ccfr_destroy(None) == 1
     assert lib.ccfr_step(None, None, None, None) == 1
     # mixed scenes: the extension is checked before any copy to or from the device
