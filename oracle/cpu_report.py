@@ -1,5 +1,5 @@
-"""Timing of the FP64 oracle on the host cores for the configurations of the
-CPU-baseline plan: the 1,024-vertex cloth on the sphere in full (20 substeps
+"""Timing of the FP64 oracle on the host cores, for a CPU baseline of each
+configuration: the 1,024-vertex cloth on the sphere in full (20 substeps
 of 10 iterations), the 262,144-vertex stack and the 1.2 M-vertex wires for a
 bounded number of iterations, and 16 of the 512 batched scenes for a bounded
 number of substeps.  At every host core (OpenMP) and at one core (the large
