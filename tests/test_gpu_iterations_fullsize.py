@@ -1,7 +1,8 @@
-"""Per-iteration parity at the benchmarked size: the 262,144-vertex cloth stack
-(4 x 256 x 256, 20 iterations) in the launch configuration bench.py times
-(one context, plane capacity 1024, default tuning).  After one substep into
-the tangled state, ccfr_step_record records the next substep's prediction x~
+"""Per-iteration parity at the benchmarked sizes: the 262,144-vertex cloth stack
+(4 x 256 x 256, 20 iterations) and the 1,201,202-vertex wires (128 x 128
+strands of 64 segments over a grate, 10 iterations), each in the launch
+configuration bench.py times (one context, the scene's plane capacity, default
+tuning).  After one substep into the tangled state, ccfr_step_record records the next substep's prediction x~
 and the collision-free iterate x_c after every iteration; the FP64 oracle
 replays the first and the last iteration from the GPU's own state before
 each (compliance 0: the XPBD multipliers do not affect positions) and every
@@ -39,9 +40,10 @@ def cond_band(ymax, r, L):
     return 2.0 * U32 * (ymax + 2.0 * r) / (TOL_REL * L)
 
 
-def test_fullsize_stack_iterations(orc):
+@pytest.mark.parametrize("cfg", [2, 3])
+def test_fullsize_iterations(orc, cfg):
     orc.set_threads(0)
-    sc = S.config(2)
+    sc = S.config(cfg)
     assert sc.params["compliance"] == 0.0
     iters = sc.params["iters"]
     K = sc.params["plane_capacity"]
@@ -81,7 +83,8 @@ def test_fullsize_stack_iterations(orc):
         # decisions fall in the rho band: more are excluded than in the small scenes' first
         # substep, and each of them was checked above to be a valid outcome)
         assert frac <= 0.75, frac
-        line = {"case": f"cloth_stack 4x256x256, iteration {i + 1} of the second substep", "verts": sc.n_verts,
+        name = "cloth_stack 4x256x256" if cfg == 2 else "wires 128x128x64"
+        line = {"case": f"{name}, iteration {i + 1} of the second substep", "verts": sc.n_verts,
                 "compared": int(ok.sum()), "band_excluded": n_excl, "excluded_frac": frac,
                 "max_err_rel": float(err[ok].max() / L) if ok.any() else 0.0,
                 "median_err_rel": float(np.median(err[ok]) / L) if ok.any() else 0.0}
