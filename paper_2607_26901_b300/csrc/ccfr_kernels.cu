@@ -1486,6 +1486,7 @@ __device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get g
         first = false;
         const float4 P = tup_plane(best);
         walk_visit_warp(W, P, c.p.eps, c.p.eps_dep, lane);
+        if (W.S.m == 3) break;   // the iterate no longer moves in this pass
     }
     Dmax = sqrtf(W.dmax2);
     walk_end(W, c.p.eps);
@@ -1601,11 +1602,13 @@ __device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, 
     Walk<double> W;
     walk_begin(W, ypass);
     float4 Plast = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);   // no plane visited yet (a NaN)
-    for (int pos = 0; pos < m; pos += 32) {
+    // (once Alg. 1 holds three lines the iterate no longer moves in this pass, so the
+    // rest of the walk cannot change the pass result: it stops there)
+    for (int pos = 0; pos < m && W.S.m < 3; pos += 32) {
         const int e = pos + lane;
         const float4 P = (e < m) ? pl[sb.idx[0][e]] : make_float4(0.f, 0.f, 0.f, 0.f);
         int lo = 0;   // lanes below lo are already behind the walk
-        for (;;) {
+        while (W.S.m < 3) {
             const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f && !same_plane(P, Plast);
             const unsigned bal = __ballot_sync(FULL, viol);
             if (!bal) break;
@@ -2062,6 +2065,7 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
                 cur = best;
                 first = false;
                 walk_visit(W, tup_plane(best), c.p.eps, c.p.eps_dep);
+                if (W.S.m == 3) break;   // the iterate no longer moves in this pass
             }
             walk_end(W, c.p.eps);
             atomicAdd(&bc.glob_pass, 1u);
