@@ -475,10 +475,10 @@ def main():
                                "violated_verts": st["violated_verts"] / per_iter,
                                "halts": st["halts"] / per_iter, "ee_fp64": st["ee_fp64"] / per_iter,
                                "feas_fp64": st["feas_fp64"] / per_iter,
-                               "proj_smem_passes": st["aux"][0] / per_iter, "proj_full_passes": st["aux"][1] / per_iter,
+                               "proj_long_passes": st["aux"][0] / per_iter, "proj_short_passes": st["aux"][1] / per_iter,
                                "proj_violated_planes": st["aux"][2] / per_iter, "big_tris": st["aux"][3] / per_iter,
-                               "big_edges": st["aux"][4] / per_iter, "proj_retries": st["aux"][5] / per_iter,
-                               "proj_heavy_planes": planes_q, "proj_sorted_planes": st["aux"][7] / per_iter,
+                               "big_edges": st["aux"][4] / per_iter,
+                               "proj_heavy_planes": planes_q,
                                "proj_short_verts": n_s, "proj_short_planes": planes_s,
                                "big_cells": st["aux"][10] / per_iter, "big_table_scans": st["aux"][11] / per_iter,
                                "big_items": st["aux"][12] / per_iter, "bige_items": st["aux"][13] / per_iter,

@@ -143,16 +143,14 @@ typedef struct {
     unsigned long long iterations;                    /* solver iterations executed     */
     unsigned long long steps;                         /* ccfr_step calls                */
     unsigned long long aux[16];                       /* diagnostics: [0] projection passes
-                                                         over a sorted list in shared memory
-                                                         (long lists), [1] passes over the
-                                                         full list (short lists, one thread
-                                                         per vertex, and lists beyond shared
-                                                         memory), [2] violated planes
-                                                         processed, [3] oversized triangles,
-                                                         [4] oversized edges, [5] candidate-
-                                                         list retries, [6] planes of the
-                                                         violated vertices with long lists,
-                                                         [7] candidate planes sorted, [8]
+                                                         of the warp-per-vertex walk (long
+                                                         lists), [1] passes of the thread-per-
+                                                         vertex walk (short lists), [2]
+                                                         violated planes visited until Alg. 1
+                                                         holds three lines, [3] oversized
+                                                         triangles, [4] oversized edges, [5]
+                                                         zero, [6] planes of the violated
+                                                         vertices with long lists, [7] zero, [8]
                                                          violated vertices with short lists,
                                                          [9] their planes, [10] grid cells
                                                          scanned for oversized primitives,

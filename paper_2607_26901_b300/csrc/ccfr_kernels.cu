@@ -1407,27 +1407,12 @@ __device__ __forceinline__ f3 clamp_len(f3 y, float lim) {
 }
 
 struct BlockCounters {
-    unsigned viol, halt, over, f64, fhalt, maxc, smem_pass, glob_pass, nviol, retry;
-    unsigned long long planes, heavy_planes, sorted, short_planes;
+    unsigned viol, halt, over, f64, fhalt, maxc, long_pass, short_pass, nviol;
+    unsigned long long planes, heavy_planes, short_planes;
     unsigned short_verts;
 };
 
-// Per-warp shared memory of the projection: the slots of a pass's candidate
-// planes, double-buffered for a stable radix sort, the current pass's digit
-// of each entry and the digit histogram (6 KB).  The sort keys themselves are
-// not stored: each pass recomputes its digit from the plane (rho at the first
-// input, or the plane hash), a read that stays in L1 because the small
-// buffers leave it room for the warps' plane lists.  Dynamic shared memory
-// (PROJ_WARPS x 6 KB).
-constexpr int SCAP = 1024;
 constexpr int PROJ_WARPS = 4;
-struct SortBuf {
-    unsigned short idx[2][SCAP];
-    unsigned char dig[SCAP];
-    unsigned hist[256];
-};
-constexpr size_t PROJ_SMEM = PROJ_WARPS * sizeof(SortBuf);
-
 
 __device__ __forceinline__ Tup warp_min_tup(Tup best) {
     #pragma unroll
@@ -1453,172 +1438,50 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// One pass of Alg. 2 from the pass input ypass: visit the planes in ascending
-// order of the sort key (rho at the first input y0, then the plane's own bits
-// and slot), call Alg. 1 on each plane violated at the current iterate, and
-// retract the result by eps towards the build position.  `get(e, P, key, j)`
-// yields source entry e of n.  Returns the number of violated planes; y_out
-// receives the pass result and Dmax the largest distance from ypass of the
-// iterates at which planes were tested.
-template <typename Get>
-__device__ __forceinline__ int alg2_pass(const DevCtx& c, int lane, int n, Get get, f3 ypass, f3& y_out, float& Dmax) {
+// One pass of Alg. 2 over a vertex's np planes pl, by one warp, from the pass
+// input ypass (offsets from the build position; y0 the first pass input).
+// Alg. 2 sorts the planes once, by rho at y0, and walks them in that order,
+// handing each plane violated at the current iterate to Alg. 1.  Here each
+// visit selects the next such plane directly: a warp argmin, over the planes
+// after the last visited one in the pass order (key rho at y0, then plane
+// hash, plane bits, slot) that are violated at the current iterate (a copy of
+// the plane just visited skipped).  That is the plane the ordered walk would
+// meet next, so the pass is the same; once Alg. 1 holds three lines the
+// iterate no longer moves in the pass and the walk stops (2.8 visits per
+// violated vertex on the cloth stack, against some 300 planes to sort).  The
+// result is retracted once by eps.  Returns the number of visits; y_out gets
+// the pass result and Dmax the largest distance of the tested iterates from
+// ypass.  Four planes in flight per lane.
+__device__ int select_pass(const DevCtx& c, int lane, const float4* pl, int np, f3 y0, f3 ypass, f3& y_out,
+                           float& Dmax) {
     Walk<double> W;
     walk_begin(W, ypass);
-    Tup cur;
-    cur.a = cur.b = cur.c = 0ull;
-    cur.d = 0u;
+    Tup cur = tup_none();
     bool first = true;
-    for (int it = 0; it <= n; ++it) {
+    while (W.S.m < 3) {
         Tup best = tup_none();
-        for (int e = lane; e < n; e += 32) {
-            float4 P;
-            float key;
-            int j;
-            get(e, P, key, j);
-            if (rho_at(W.y, P) < 0.f && (first || !same_plane(P, tup_plane(cur)))) {
-                Tup t = make_tup(key, P, j);
-                if ((first || tless(cur, t)) && tless(t, best)) best = t;
+        const float4 Pc = tup_plane(cur);
+        for (int j0 = lane; j0 < np; j0 += 128) {
+            float4 P[4];
+            #pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = j0 + 32 * k;
+                P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 3.4e38f);
+            }
+            #pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int j = j0 + 32 * k;
+                if (j < np && rho_at(W.y, P[k]) < 0.f && (first || !same_plane(P[k], Pc))) {
+                    const Tup t = make_tup(rho_at(y0, P[k]), P[k], j);
+                    if ((first || tless(cur, t)) && tless(t, best)) best = t;
+                }
             }
         }
         best = warp_min_tup(best);
         if (best.d == ~0u) break;
         cur = best;
         first = false;
-        const float4 P = tup_plane(best);
-        walk_visit_warp(W, P, c.p.eps, c.p.eps_dep, lane);
-        if (W.S.m == 3) break;   // the iterate no longer moves in this pass
-    }
-    Dmax = sqrtf(W.dmax2);
-    walk_end(W, c.p.eps);
-    y_out = W.y;
-    return W.nv;
-}
-
-// One stable counting pass of a warp LSD radix sort over n slots from buffer
-// src into buffer src ^ 1, on the 8-bit digit dig(slot), computed once per
-// entry (four planes in flight per lane) and kept in sb.dig for the scatter.
-// Equal digits keep their relative order: ranks within each 32-entry chunk
-// come from the lanes that hold the same digit (one match instruction).
-template <typename Dig>
-__device__ __forceinline__ void radix_pass(SortBuf& sb, int n, int lane, int src, Dig dig) {
-    const unsigned lt = (1u << lane) - 1u;
-    for (int b = lane; b < 256; b += 32) sb.hist[b] = 0u;
-    __syncwarp();
-    for (int i0 = lane; i0 < n; i0 += 128) {
-        unsigned d[4];
-        #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = i0 + 32 * k;
-            d[k] = (i < n) ? dig(sb.idx[src][i]) : 0u;
-        }
-        #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = i0 + 32 * k;
-            if (i < n) {
-                sb.dig[i] = (unsigned char)d[k];
-                atomicAdd(&sb.hist[d[k]], 1u);
-            }
-        }
-    }
-    __syncwarp();
-    // exclusive scan of the 256 bins, 8 per lane
-    unsigned loc[8], tot = 0;
-    #pragma unroll
-    for (int k = 0; k < 8; ++k) { loc[k] = sb.hist[lane * 8 + k]; tot += loc[k]; }
-    unsigned inc = tot;
-    #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned t = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += t;
-    }
-    unsigned off = inc - tot;
-    __syncwarp();
-    #pragma unroll
-    for (int k = 0; k < 8; ++k) { sb.hist[lane * 8 + k] = off; off += loc[k]; }
-    __syncwarp();
-    for (int base = 0; base < n; base += 32) {
-        const int i = base + lane;
-        const bool valid = i < n;
-        const unsigned short j = valid ? sb.idx[src][i] : 0;
-        const unsigned dg = valid ? (unsigned)sb.dig[i] : 256u;
-        // lanes holding the same digit (the idle lanes, digit 256, form a group of their own)
-        const unsigned peers = __match_any_sync(FULL, dg);
-        const unsigned start = valid ? sb.hist[dg] : 0u;
-        __syncwarp();
-        if (valid) {
-            const unsigned dst = start + __popc(peers & lt);
-            sb.idx[src ^ 1][dst] = j;
-            if ((peers & lt) == 0u) sb.hist[dg] = start + __popc(peers);
-        }
-        __syncwarp();
-    }
-}
-
-// Sort key of a candidate plane: rho at the first input y0, as an ordered
-// integer (Alg. 2 sorts once, by the violation at the pass start).
-__device__ __forceinline__ unsigned plane_key(const float4* pl, int j, f3 y0) { return f2ord(rho_at(y0, pl[j])); }
-
-// Stable LSD radix sort by (rho key, plane hash) of the n slots in buffer 0,
-// which arrive in slot order: two passes on the hash, then four on the key.
-// Six passes: the sorted slots are back in buffer 0, ordered by (key, hash, slot).
-// One loop over a single pass body (the digit source chosen per pass), so that
-// the kernel holds one copy of the pass code.
-__device__ void warp_radix_sort(SortBuf& sb, int n, int lane, const float4* pl, f3 y0) {
-    #pragma unroll 1
-    for (int p = 0; p < 6; ++p) {
-        const bool hashp = p < 2;
-        const int shift = 8 * (hashp ? p : p - 2);
-        radix_pass(sb, n, lane, p & 1, [&](unsigned short j) {
-            const float4 P = pl[j];
-            const unsigned w = hashp ? plane_hash16(P) : f2ord(rho_at(y0, P));
-            return (w >> shift) & 255u;
-        });
-    }
-}
-
-// Plane order of Alg. 2 among equal (key, hash): the plane's own bits (d, n)
-// and its slot, as in tless (identical planes may go in any order; distinct
-// ones need a fixed one).
-__device__ __forceinline__ bool plane_less(const float4* pl, int a, int b) {
-    float4 A = pl[a], B = pl[b];
-    unsigned x0 = f2ord(A.w), y0 = f2ord(B.w);
-    if (x0 != y0) return x0 < y0;
-    x0 = f2ord(A.x); y0 = f2ord(B.x);
-    if (x0 != y0) return x0 < y0;
-    x0 = f2ord(A.y); y0 = f2ord(B.y);
-    if (x0 != y0) return x0 < y0;
-    x0 = f2ord(A.z); y0 = f2ord(B.z);
-    if (x0 != y0) return x0 < y0;
-    return a < b;
-}
-
-// One pass of Alg. 2 over the sorted candidates sb.idx[0][0..m): walk
-// the list in order, 32 planes per chunk held one per lane; the first plane of
-// the chunk violated at the current iterate is handled (Alg. 1) and the walk
-// resumes with the chunk's later planes, tested at the new iterate; the pass
-// result is retracted at the end.
-__device__ int sorted_pass(const DevCtx& c, int lane, const SortBuf& sb, int m, const float4* pl, f3 ypass,
-                           f3& y_out, float& Dmax) {
-    Walk<double> W;
-    walk_begin(W, ypass);
-    float4 Plast = make_float4(__int_as_float(-1), 0.f, 0.f, 0.f);   // no plane visited yet (a NaN)
-    // (once Alg. 1 holds three lines the iterate no longer moves in this pass, so the
-    // rest of the walk cannot change the pass result: it stops there)
-    for (int pos = 0; pos < m && W.S.m < 3; pos += 32) {
-        const int e = pos + lane;
-        const float4 P = (e < m) ? pl[sb.idx[0][e]] : make_float4(0.f, 0.f, 0.f, 0.f);
-        int lo = 0;   // lanes below lo are already behind the walk
-        while (W.S.m < 3) {
-            const bool viol = lane >= lo && e < m && rho_at(W.y, P) < 0.f && !same_plane(P, Plast);
-            const unsigned bal = __ballot_sync(FULL, viol);
-            if (!bal) break;
-            const int f = __ffs(bal) - 1;
-            const float4 Pf = make_float4(__shfl_sync(FULL, P.x, f), __shfl_sync(FULL, P.y, f),
-                                          __shfl_sync(FULL, P.z, f), __shfl_sync(FULL, P.w, f));
-            walk_visit_warp(W, Pf, c.p.eps, c.p.eps_dep, lane);
-            Plast = Pf;
-            lo = f + 1;
-        }
+        walk_visit_warp(W, tup_plane(best), c.p.eps, c.p.eps_dep, lane);
     }
     Dmax = sqrtf(W.dmax2);
     walk_end(W, c.p.eps);
@@ -1733,12 +1596,10 @@ __device__ __forceinline__ void flush_block_counters(const DevCtx& c, BlockCount
         if (bc.fhalt) atomicAdd(&c.stats->feas_halts, (u64)bc.fhalt);
         if (bc.maxc) atomicMax(&c.stats->max_planes, bc.maxc);
         if (bc.planes) atomicAdd(&c.stats->planes, bc.planes);
-        if (bc.smem_pass) atomicAdd(&c.stats->aux[0], (u64)bc.smem_pass);
-        if (bc.glob_pass) atomicAdd(&c.stats->aux[1], (u64)bc.glob_pass);
+        if (bc.long_pass) atomicAdd(&c.stats->aux[0], (u64)bc.long_pass);
+        if (bc.short_pass) atomicAdd(&c.stats->aux[1], (u64)bc.short_pass);
         if (bc.nviol) atomicAdd(&c.stats->aux[2], (u64)bc.nviol);
-        if (bc.retry) atomicAdd(&c.stats->aux[5], (u64)bc.retry);
         if (bc.heavy_planes) atomicAdd(&c.stats->aux[6], bc.heavy_planes);
-        if (bc.sorted) atomicAdd(&c.stats->aux[7], bc.sorted);
         if (bc.short_verts) atomicAdd(&c.stats->aux[8], (u64)bc.short_verts);
         if (bc.short_planes) atomicAdd(&c.stats->aux[9], bc.short_planes);
     }
@@ -1746,10 +1607,9 @@ __device__ __forceinline__ void flush_block_counters(const DevCtx& c, BlockCount
 
 __device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
     if (threadIdx.x == 0) {
-        bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.smem_pass = bc.glob_pass = bc.nviol = bc.retry = 0u;
+        bc.viol = bc.halt = bc.over = bc.f64 = bc.fhalt = bc.maxc = bc.long_pass = bc.short_pass = bc.nviol = 0u;
         bc.planes = 0ull;
         bc.heavy_planes = 0ull;
-        bc.sorted = 0ull;
         bc.short_planes = 0ull;
         bc.short_verts = 0u;
     }
@@ -1853,31 +1713,21 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
     flush_block_counters(c, bc);
 }
 
-// Projection, second kernel: the vertices with a violated plane, one warp
-// each (persistent warps over the queue).  A pass of Alg. 2 only ever acts on
-// planes violated at its current iterate.  With b the pass input and D the
-// largest distance the iterate moves from b during the pass,
-// rho_k(y) >= rho_k(b) - D for every plane, so planes with rho_k(b) > T >=
-// D + margin are never touched: the pass runs on the planes with
-// rho_k(b) <= T, sorted in shared memory, and is repeated with a larger T if
-// D turns out to exceed T - margin; the result equals a pass over the full
-// sorted list.  The last pass can only confirm convergence (any violation
-// there ends in the halt), so it is a single scan.
-// Six blocks of four warps per SM (80 registers, a few spilled): 2% faster
-// than the five that 96 registers allow.
+// Projection, second kernel: the vertices with a violated plane and a long
+// plane list, one warp each (persistent warps taking the queued vertices one
+// at a time from a shared counter: a vertex costs from a few hundred to many
+// thousands of instructions).  Each pass of Alg. 2 is a selection walk over
+// the whole list (select_pass); the last pass can only confirm convergence
+// (any violation there ends in the halt), so it is a single scan.
+// Six blocks of four warps per SM (80 registers).
 template <bool STEP>
 __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, const float4* x_b, const float4* x_in,
                                                                     float4* x_out, unsigned char* halt_out) {
     if (STEP && c.flags[1]) return;
     __shared__ BlockCounters bc;
-    extern __shared__ __align__(16) unsigned char proj_smem[];
     zero_block_counters(bc);
     const int lane = threadIdx.x & 31;
-    SortBuf& sb = reinterpret_cast<SortBuf*>(proj_smem)[threadIdx.x >> 5];
-    const float U = 5.9604645e-8f;   // unit roundoff of binary32
     const unsigned nwork = c.work_count[0];
-    // the queued vertices are taken one at a time from a shared counter (their costs vary
-    // with the list length and the number of visits; a fixed stride left long tails)
     auto next = [&]() {
         unsigned w = 0;
         if (lane == 0) w = atomicAdd(&c.work_count[2], 1u);
@@ -1886,7 +1736,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, 
     for (unsigned wi = next(); wi < nwork; wi = next()) {
         const int4 wk = c.work[wi];
         const int v = wk.x;
-        const float mn = __int_as_float(wk.y), dabs = __int_as_float(wk.z);
+        const float mn = __int_as_float(wk.y);
         const float4 X = x_b[v];
         const float4 XP = x_in[v];
         const f3 y0 = sub(xyz(XP), xyz(X));
@@ -1903,106 +1753,8 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, 
             if (pass == c.p.max_passes) break;
             f3 ynext;
             float Dmax;
-            bool done = false;
-            const float yb = len(ypass);
-            float T = 2.f * (-mnb);
-            for (int attempt = 0; attempt < 3 && !done; ++attempt) {
-                float margin = 1e-3f * T + 64.f * U * (yb + T + dabs) + 1e-12f;
-                T += margin;
-                // gather the planes with rho(ypass) <= T, keyed by rho at the first input
-                int m = 0;
-                for (int j0 = 0; j0 < np; j0 += 128) {
-                    float4 P[4];
-                    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int j = j0 + 32 * k + lane;
-                        P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 3.4e38f);
-                    }
-                    #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const int j = j0 + 32 * k + lane;
-                        const bool take = (j < np) && rho_at(ypass, P[k]) <= T;
-                        const unsigned bal = __ballot_sync(FULL, take);
-                        const int pos = m + __popc(bal & ((1u << lane) - 1u));
-                        if (take && pos < SCAP) sb.idx[0][pos] = (unsigned short)j;
-                        m += __popc(bal);
-                    }
-                }
-                __syncwarp();
-                if (m > SCAP || np > 65535) break;
-                if (attempt > 0 && lane == 0) atomicAdd(&bc.retry, 1u);
-                if (m <= 32) {
-                    // one candidate per lane: rank by the full order (key, plane bits, slot)
-                    Tup me = tup_none();
-                    unsigned short jj = 0;
-                    if (lane < m) {
-                        jj = sb.idx[0][lane];
-                        me = make_tup_ord(plane_key(pl, jj, y0), pl[jj], jj);
-                    }
-                    int rank = 0;
-                    for (int t = 0; t < m; ++t) {
-                        Tup o;
-                        o.a = __shfl_sync(FULL, me.a, t);
-                        o.b = __shfl_sync(FULL, me.b, t);
-                        o.c = __shfl_sync(FULL, me.c, t);
-                        o.d = __shfl_sync(FULL, me.d, t);
-                        rank += tless(o, me) ? 1 : 0;
-                    }
-                    __syncwarp();
-                    if (lane < m) sb.idx[0][rank] = jj;
-                    __syncwarp();
-                } else {
-                warp_radix_sort(sb, m, lane, pl, y0);
-                // equal (key, hash) on distinct planes (a hash collision; rare): order
-                // each such run by the plane itself (its bits, then its slot).
-                // Bitwise-identical planes act identically in any order.  Runs are
-                // disjoint: each lane sorts the runs that start at its indices.
-                bool tie = false;
-                for (int i = lane; i + 1 < m; i += 32) {
-                    const float4 A = pl[sb.idx[0][i]], B = pl[sb.idx[0][i + 1]];
-                    if (f2ord(rho_at(y0, A)) == f2ord(rho_at(y0, B)))
-                        tie |= !(A.x == B.x && A.y == B.y && A.z == B.z && A.w == B.w) &&
-                               plane_hash16(A) == plane_hash16(B);
-                }
-                if (__any_sync(FULL, tie)) {
-                    auto same = [&](int i, int k) {
-                        return plane_key(pl, sb.idx[0][i], y0) == plane_key(pl, sb.idx[0][k], y0) &&
-                               plane_hash16(pl[sb.idx[0][i]]) == plane_hash16(pl[sb.idx[0][k]]);
-                    };
-                    for (int i = lane; i < m; i += 32) {
-                        if ((i > 0 && same(i - 1, i)) || i + 1 >= m || !same(i, i + 1)) continue;
-                        int e = i + 2;
-                        while (e < m && same(i, e)) ++e;
-                        for (int a = i + 1; a < e; ++a) {
-                            const unsigned short jj = sb.idx[0][a];
-                            int q = a - 1;
-                            while (q >= i && plane_less(pl, jj, sb.idx[0][q])) {
-                                sb.idx[0][q + 1] = sb.idx[0][q];
-                                --q;
-                            }
-                            sb.idx[0][q + 1] = jj;
-                        }
-                    }
-                    __syncwarp();
-                }
-                }
-                if (lane == 0) atomicAdd(&bc.sorted, (unsigned long long)m);
-                int nvp = sorted_pass(c, lane, sb, m, pl, ypass, ynext, Dmax);
-                __syncwarp();
-                if (Dmax <= T - margin) {
-                    done = true;
-                    if (lane == 0) { atomicAdd(&bc.smem_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
-                } else {
-                    T = 2.f * Dmax;
-                }
-            }
-            if (!done) {
-                // too many candidate planes: pass over the full list in global memory
-                int nvp = alg2_pass(c, lane, np,
-                                    [&](int e, float4& P, float& key, int& j) { P = pl[e]; key = rho_at(y0, P); j = e; },
-                                    ypass, ynext, Dmax);
-                if (lane == 0) { atomicAdd(&bc.glob_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
-            }
+            const int nvp = select_pass(c, lane, pl, np, y0, ypass, ynext, Dmax);
+            if (lane == 0) { atomicAdd(&bc.long_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
             ypass = ynext;
         }
         const bool halted = !conv;
@@ -2068,7 +1820,7 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
                 if (W.S.m == 3) break;   // the iterate no longer moves in this pass
             }
             walk_end(W, c.p.eps);
-            atomicAdd(&bc.glob_pass, 1u);
+            atomicAdd(&bc.short_pass, 1u);
             atomicAdd(&bc.nviol, (unsigned)W.nv);
             ypass = W.y;
         }
@@ -2619,16 +2371,12 @@ static std::atomic<int> g_heavy_blocks_per_sm{4};
 #define HEAVY_BLOCKS_PER_SM g_heavy_blocks_per_sm.load(std::memory_order_relaxed)
 
 cudaError_t configure_kernels() {
-    cudaError_t e = cudaFuncSetAttribute(k_project_heavy<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PROJ_SMEM);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_project_heavy<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PROJ_SMEM);
     int nb = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_short<true>, 128, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_short<true>, 128, 0);
     if (e == cudaSuccess && nb > 0) g_short_blocks_per_sm.store(nb, std::memory_order_relaxed);
     nb = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_heavy<true>, PROJ_WARPS * 32, PROJ_SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_project_heavy<true>, PROJ_WARPS * 32, 0);
     if (e == cudaSuccess && nb > 0) g_heavy_blocks_per_sm.store(nb, std::memory_order_relaxed);
     return e;
 }
@@ -2643,7 +2391,7 @@ void launch_project(const DevCtx& c, const float4* xb, float4* xio, unsigned cha
     cudaMemsetAsync(c.work_count, 0, 4 * sizeof(unsigned), st);
     if (threads > 0) {
         k_project<false><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, xb, xio, xio, halt);
-        k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, xb, xio, xio, halt);
+        k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, 0, st>>>(c, xb, xio, xio, halt);
         k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, xb, xio, xio, halt);
     }
 }
@@ -2676,7 +2424,7 @@ void launch_iteration(const DevCtx& c, float4* x, cudaStream_t st, const int* co
     cudaMemsetAsync(c.work_count, 0, 4 * sizeof(unsigned), st);
     if (threads > 0) k_project<true><<<nblk(c.n_verts, 256), 256, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT, st);
-    if (threads > 0) k_project_heavy<true><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, st>>>(c, x, c.x_s, x, nullptr);
+    if (threads > 0) k_project_heavy<true><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_HEAVY, st);
     if (threads > 0) k_project_short<true><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, st>>>(c, x, c.x_s, x, nullptr);
     if (tm) tm->mark(ST_PROJECT_SHORT, st);
@@ -2819,7 +2567,7 @@ extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const fl
     c.n_sm = su->n_sm;
     k_static_dmin<<<nblk(n_verts, 256), 256, 0, s>>>(dmin_drop, sc->dmin, n_verts);
     k_project<false><<<nblk(n_verts, 256), 256, 0, s>>>(c, (const float4*)x, (float4*)x_io, (float4*)x_io, halt_out);
-    k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, PROJ_SMEM, s>>>(c, (const float4*)x, (float4*)x_io,
+    k_project_heavy<false><<<c.n_sm * HEAVY_BLOCKS_PER_SM, PROJ_WARPS * 32, 0, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                          (float4*)x_io, halt_out);
     k_project_short<false><<<c.n_sm * SHORT_BLOCKS_PER_SM, 128, 0, s>>>(c, (const float4*)x, (float4*)x_io,
                                                                        (float4*)x_io, halt_out);
