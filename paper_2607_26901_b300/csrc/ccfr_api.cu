@@ -276,6 +276,7 @@ static ccfr_status create_impl(const std::vector<int>& he, const std::vector<int
     d.alpha_vol = ex ? ex->vol_comp / (params->dt * params->dt) : 0.f;
     d.p.max_passes = params->max_passes;
     d.p.K = params->plane_capacity;
+    d.p.short_max = short_list_max(d.p.K);
     d.p.cell_size = params->cell_size;
     d.p.delta = params->delta;
     d.p.k_resp = params->response_stiffness;
@@ -855,6 +856,7 @@ ccfr_status ccfr_set_tuning(ccfr_ctx* c, const ccfr_tuning* t) {
         if (c->dc.keys) c->dc.keys = keys;
         if (c->dc.phi) c->dc.phi = phi;
         c->dc.p.K = t->plane_capacity;
+        c->dc.p.short_max = short_list_max(t->plane_capacity);
         c->prm.plane_capacity = t->plane_capacity;
         c->regions_valid = false;
     }

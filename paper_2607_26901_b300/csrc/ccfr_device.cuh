@@ -74,6 +74,7 @@ struct DevParams {
     float dt, gx, gy, gz, alpha_tilde;
     int max_passes;
     int K;
+    int short_max;              // plane lists up to this length are projected one thread per vertex
     float cell_size;
     float delta, k_resp, delta_v, mu_s, mu_k;   // contact response (Sec. 3.3); on when delta > 0
 };
@@ -186,6 +187,17 @@ __device__ __forceinline__ u64 pair_key(int kind, int a, int b) {
 // cell is the largest edge box.
 constexpr float BIGE_FACTOR = 2.0f;
 constexpr int N_SCHED = 24;
+
+// The longest plane list the projection gives a thread of its own
+// (k_project_short) rather than a warp (k_project_heavy): a warp spends its
+// Alg. 1 steps on one lane (and on this part an FP64 warp instruction holds
+// the FP64 pipe for the whole warp), a thread-per-vertex walk runs 32
+// vertices' steps in double-float side by side but scans its list alone.
+// Lists of contexts with a small capacity (<= 128: few planes per vertex)
+// are short up to 64 planes (the 1.2 M-vertex wires: 15% faster per substep
+// than at 32); otherwise up to 32 (the cloth stack's few lists of 33 to 64
+// planes carry long walks, and 64 cost 1% there).
+__host__ __device__ __forceinline__ int short_list_max(int K) { return K <= 128 ? 64 : 32; }
 
 // Default capacity of the candidate-pair buffers (ccfr_params.pair_capacity):
 // the main-stream buffer holds 32 pairs per triangle and edge, the edge-edge

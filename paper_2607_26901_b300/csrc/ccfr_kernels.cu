@@ -1616,8 +1616,8 @@ __device__ __forceinline__ void zero_block_counters(BlockCounters& bc) {
     __syncthreads();
 }
 
-// Plane lists up to this length are projected one thread per vertex
-// (k_project_short); longer ones one warp per vertex (k_project_heavy).
+// The contact response's short lists (one thread per vertex; longer ones one
+// warp per vertex).  The projection's bound is per context (DevParams::short_max).
 constexpr int SHORT_LIST = 32;
 
 // Projection, first kernel.  Vertices whose planes all hold at the candidate
@@ -1632,7 +1632,7 @@ template <bool STEP>
 __device__ __forceinline__ void queue_violated(const DevCtx& c, int v, int np, float mn, float dabs,
                                                BlockCounters& bc) {
     const int4 wk = make_int4(v, __float_as_int(mn), __float_as_int(dabs), 0);
-    if (np <= SHORT_LIST) {
+    if (np <= c.p.short_max) {
         const unsigned w = atomicAdd(&c.work_count[1], 1u);
         c.work[c.n_verts - 1 - (int)w] = wk;
     } else {
@@ -1657,7 +1657,7 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
         if (X.w > 0.f && (!STEP || vertex_active(c, v))) {
             const unsigned cnt = c.count[v];
             const int np = (int)min(cnt, (unsigned)c.p.K);
-            if (cnt > (unsigned)c.p.K || np > SHORT_LIST) {
+            if (cnt > (unsigned)c.p.K || np > c.p.short_max) {
                 warp_job = true;
             } else {
                 const f3 y0 = sub(xyz(XP), xyz(X));
@@ -2556,6 +2556,7 @@ extern "C" ccfr_status ccfr_project_static(const float* x, float* x_io, const fl
     c.p.tau = params->tau_feas;
     c.p.max_passes = params->max_passes;
     c.p.K = capacity;
+    c.p.short_max = short_list_max(capacity);
     c.n_verts = n_verts;
     c.planes = const_cast<float4*>((const float4*)planes);
     c.count = const_cast<unsigned*>((const unsigned*)count);
