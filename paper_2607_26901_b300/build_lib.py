@@ -16,7 +16,7 @@ CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 LIB = PKG / "_lib" / "libccfr.so"
 SOURCES = ["ccfr_kernels.cu", "ccfr_api.cu", "ccfr_server.cpp"]
-DEPS = SOURCES + ["ccfr_device.cuh", "ccfr_internal.h"]
+DEPS = SOURCES + ["ccfr_device.cuh", "ccfr_internal.h", "ccfr_df.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1312,39 +1312,58 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
     W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
 }
 
-// walk_visit for a warp that works on one vertex (every lane holds the same
-// walk): the extended-precision Alg. 1 step runs on lane 0 alone, and the new
-// iterate and line count are broadcast.  The result is the one every lane
-// would compute; only lane 0's call frame and Alg. 1 state are written, where
-// 32 lanes would otherwise write 32 copies of them to local memory.
-__device__ __forceinline__ void walk_visit_warp(Walk<double>& W, float4 P, float eps, float eps_dep, int lane) {
-    ++W.nv;
-    if (W.S.m == 0) {
-        const f3 n = xyz(P);
-        const float beta0 = dot(n, n);
-        if (!(fabsf(beta0) < eps_dep)) {
-            W.y = sub(W.y, mul(n, rho_at(W.y, P) / beta0));
-            W.P0 = P;
-            W.lazy0 = true;
-            W.S.m = 1;
-        }
-    } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
-        if (lane == 0) {
-            if (W.lazy0) {
-                W.yp = v3_of<double>(W.ypass);
-                walk_lazy0(W, W.yp);
+// Lanes per vertex in k_project_heavy: a warp projects 32 / HEAVY_GROUP
+// vertices side by side, each by a group of HEAVY_GROUP lanes (a power of two).
+#ifndef CCFR_HEAVY_GROUP
+#define CCFR_HEAVY_GROUP 8
+#endif
+constexpr int HEAVY_GROUP = CCFR_HEAVY_GROUP;
+static_assert(HEAVY_GROUP >= 2 && HEAVY_GROUP <= 32 && (HEAVY_GROUP & (HEAVY_GROUP - 1)) == 0,
+              "HEAVY_GROUP must be a power of two in [2, 32]");
+
+// walk_visit for a group of HEAVY_GROUP lanes that works on one vertex (every
+// lane of the group holds the same walk), called by all 32 lanes of the warp;
+// `on`: this group visits plane P.  The extended-precision Alg. 1 step runs on
+// the group's first lane alone, and the new iterate and line count are
+// broadcast to the group.  The leaders of all groups that take an FP64 step
+// in the same call take it in the same warp instructions: on this part an
+// FP64 warp instruction occupies the FP64 pipe as long with one active lane
+// as with 32, so the groups share that cost.  The result is the one every
+// lane would compute.
+__device__ __forceinline__ void walk_visit_group(Walk<double>& W, float4 P, bool on, float eps, float eps_dep,
+                                                 int lane) {
+    const int gl = lane & (HEAVY_GROUP - 1), leader = lane & ~(HEAVY_GROUP - 1);
+    if (on) {
+        ++W.nv;
+        if (W.S.m == 0) {
+            const f3 n = xyz(P);
+            const float beta0 = dot(n, n);
+            if (!(fabsf(beta0) < eps_dep)) {
+                W.y = sub(W.y, mul(n, rho_at(W.y, P) / beta0));
+                W.P0 = P;
+                W.lazy0 = true;
+                W.S.m = 1;
             }
-            const V3<double> nd = v3_of<double>(xyz(P));
-            ortho_step<double>(W.z, xyz(P), nd, plane_b_nd<double>(P.w, nd, W.yp), W.S, eps_dep);
-            const V3<double> yn = v3_add(W.yp, W.z);
-            W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
+        } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
+            if (gl == 0) {
+                if (W.lazy0) {
+                    W.yp = v3_of<double>(W.ypass);
+                    walk_lazy0(W, W.yp);
+                }
+                const V3<double> nd = v3_of<double>(xyz(P));
+                ortho_step<double>(W.z, xyz(P), nd, plane_b_nd<double>(P.w, nd, W.yp), W.S, eps_dep);
+                const V3<double> yn = v3_add(W.yp, W.z);
+                W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
+            }
+            W.lazy0 = false;
         }
-        W.lazy0 = false;
-        W.y = mk(__shfl_sync(FULL, W.y.x, 0), __shfl_sync(FULL, W.y.y, 0), __shfl_sync(FULL, W.y.z, 0));
-        W.S.m = __shfl_sync(FULL, W.S.m, 0);
     }
-    const f3 dz = sub(W.y, W.ypass);
-    W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
+    W.y = mk(__shfl_sync(FULL, W.y.x, leader), __shfl_sync(FULL, W.y.y, leader), __shfl_sync(FULL, W.y.z, leader));
+    W.S.m = __shfl_sync(FULL, W.S.m, leader);
+    if (on) {
+        const f3 dz = sub(W.y, W.ypass);
+        W.dmax2 = fmaxf(W.dmax2, dot(dz, dz));
+    }
 }
 
 // End of a pass: the pass result (the projected boundary position) is
@@ -1438,55 +1457,54 @@ __device__ __forceinline__ float warp_max(float v) {
     return v;
 }
 
-// One pass of Alg. 2 over a vertex's np planes pl, by one warp, from the pass
-// input ypass (offsets from the build position; y0 the first pass input).
-// Alg. 2 sorts the planes once, by rho at y0, and walks them in that order,
-// handing each plane violated at the current iterate to Alg. 1.  Here each
-// visit selects the next such plane directly: a warp argmin, over the planes
-// after the last visited one in the pass order (key rho at y0, then plane
-// hash, plane bits, slot) that are violated at the current iterate (a copy of
-// the plane just visited skipped).  That is the plane the ordered walk would
-// meet next, so the pass is the same; once Alg. 1 holds three lines the
-// iterate no longer moves in the pass and the walk stops (2.8 visits per
-// violated vertex on the cloth stack, against some 300 planes to sort).  The
-// result is retracted once by eps.  Returns the number of visits; y_out gets
-// the pass result and Dmax the largest distance of the tested iterates from
-// ypass.  Four planes in flight per lane.
-__device__ int select_pass(const DevCtx& c, int lane, const float4* pl, int np, f3 y0, f3 ypass, f3& y_out,
-                           float& Dmax) {
-    Walk<double> W;
-    walk_begin(W, ypass);
-    Tup cur = tup_none();
-    bool first = true;
-    while (W.S.m < 3) {
-        Tup best = tup_none();
+// Minimum of the pass order within each group of HEAVY_GROUP lanes.
+__device__ __forceinline__ Tup group_min_tup(Tup best) {
+    #pragma unroll
+    for (int o = HEAVY_GROUP / 2; o > 0; o >>= 1) {
+        Tup t;
+        t.a = __shfl_xor_sync(FULL, best.a, o);
+        t.b = __shfl_xor_sync(FULL, best.b, o);
+        t.c = __shfl_xor_sync(FULL, best.c, o);
+        t.d = __shfl_xor_sync(FULL, best.d, o);
+        if (tless(t, best)) best = t;
+    }
+    return best;
+}
+
+// One visit of a pass of Alg. 2 over a vertex's np planes pl, by a group of
+// HEAVY_GROUP lanes (called by all 32 lanes; `on`: this group selects).
+// Alg. 2 sorts the planes once, by rho at the first pass input y0, and walks
+// them in that order, handing each plane violated at the current iterate to
+// Alg. 1.  Here each visit selects the next such plane directly: the minimum,
+// in the pass order (key rho at y0, then plane hash, plane bits, slot), of
+// the planes violated at the current iterate y that come after the last
+// visited one, cur (a copy of the plane just visited skipped); `first`: no
+// plane visited yet in this pass.  That is the plane the ordered walk would
+// meet next, so the pass is the same.  Returns tup_none() when there is none.
+// Four planes in flight per lane.
+__device__ __forceinline__ Tup group_select(const float4* pl, int np, f3 y, f3 y0, const Tup& cur, bool first,
+                                            bool on, int lane) {
+    Tup best = tup_none();
+    if (on) {
         const float4 Pc = tup_plane(cur);
-        for (int j0 = lane; j0 < np; j0 += 128) {
+        for (int j0 = lane & (HEAVY_GROUP - 1); j0 < np; j0 += 4 * HEAVY_GROUP) {
             float4 P[4];
             #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int j = j0 + 32 * k;
+                const int j = j0 + HEAVY_GROUP * k;
                 P[k] = (j < np) ? pl[j] : make_float4(0.f, 0.f, 0.f, 3.4e38f);
             }
             #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int j = j0 + 32 * k;
-                if (j < np && rho_at(W.y, P[k]) < 0.f && (first || !same_plane(P[k], Pc))) {
+                const int j = j0 + HEAVY_GROUP * k;
+                if (j < np && rho_at(y, P[k]) < 0.f && (first || !same_plane(P[k], Pc))) {
                     const Tup t = make_tup(rho_at(y0, P[k]), P[k], j);
                     if ((first || tless(cur, t)) && tless(t, best)) best = t;
                 }
             }
         }
-        best = warp_min_tup(best);
-        if (best.d == ~0u) break;
-        cur = best;
-        first = false;
-        walk_visit_warp(W, tup_plane(best), c.p.eps, c.p.eps_dep, lane);
     }
-    Dmax = sqrtf(W.dmax2);
-    walk_end(W, c.p.eps);
-    y_out = W.y;
-    return W.nv;
+    return group_min_tup(best);
 }
 
 // Minimum of rho over a vertex's planes at y, and the largest |d|; four
@@ -1513,17 +1531,14 @@ __device__ __forceinline__ void scan_min_rho(const float4* pl, int np, f3 y, int
 
 // Final feasibility check on the stored binary32 position xn: every plane
 // must hold within tau plus the binary32 rounding of the position; a
-// rounding-error filter decides most planes, FP64 the rest.  Returns true
-// when the position fails (the vertex then halts).  THREAD: one thread checks
-// all planes; otherwise the warp's lanes share them.
-template <bool THREAD>
-__device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4* pl, int np, float4 X, f3 xn,
-                                                  int lane, bool& used_fp64) {
+// rounding-error filter decides most planes, FP64 the rest.  This part checks
+// the planes j_start, j_start + j_step, ... and sets fail (a plane fails) and
+// undecided (FP64 was needed).
+__device__ __forceinline__ void final_check_planes(const DevCtx& c, const float4* pl, int np, float4 X, f3 xn,
+                                                   int j_start, int j_step, bool& fail, bool& undecided) {
     const float U = 5.9604645e-8f;
-    const int j_start = THREAD ? 0 : lane, j_step = THREAD ? 1 : 32;
     f3 dl = sub(xn, xyz(X));
     float tau = c.p.tau + 2.f * U * (fabsf(xn.x) + fabsf(xn.y) + fabsf(xn.z));
-    bool fail = false, undecided = false;
     for (int j0 = j_start; j0 < np; j0 += 4 * j_step) {
         float4 P[4];
         #pragma unroll
@@ -1544,6 +1559,16 @@ __device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4*
             if (rd < -(double)tau) fail = true;
         }
     }
+}
+
+// The final check of one vertex.  Returns true when the position fails (the
+// vertex then halts).  THREAD: one thread checks all planes; otherwise the
+// warp's lanes share them.
+template <bool THREAD>
+__device__ __forceinline__ bool final_check_fails(const DevCtx& c, const float4* pl, int np, float4 X, f3 xn,
+                                                  int lane, bool& used_fp64) {
+    bool fail = false, undecided = false;
+    final_check_planes(c, pl, np, X, xn, THREAD ? 0 : lane, THREAD ? 1 : 32, fail, undecided);
     if (THREAD) {
         used_fp64 = undecided;
         return fail;
@@ -1573,6 +1598,44 @@ __device__ __forceinline__ void finish_vertex(const DevCtx& c, int lane, int v, 
         }
         if (f64 && leader) atomicAdd(&bc.f64, 1u);
     }
+    if (leader) {
+        if (halted) atomicAdd(&bc.halt, 1u);
+        if (cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
+        if (STEP) {
+            if (len(sub(y, y0)) > 2.f * c.p.eps) c.flags[0] = 1;
+            x_out[v] = make_float4(xn.x, xn.y, xn.z, X.w);
+        } else {
+            x_out[v] = make_float4(xn.x, xn.y, xn.z, XP.w);
+            if (halt_out) halt_out[v] = halted ? 1 : 0;
+        }
+    }
+}
+
+// finish_vertex for the groups of k_project_heavy, called by all 32 lanes;
+// `on`: this group's vertex v ends here (its lanes share the final check, its
+// first lane writes).  The same end as finish_vertex<STEP, false> for a vertex
+// within its plane capacity.
+template <bool STEP>
+__device__ __forceinline__ void finish_vertex_group(const DevCtx& c, int lane, bool on, int v, float4 X, float4 XP,
+                                                    f3 y0, f3 y, bool halted, const float4* pl, int np, unsigned cnt,
+                                                    BlockCounters& bc, float4* x_out, unsigned char* halt_out) {
+    const bool leader = on && (lane & (HEAVY_GROUP - 1)) == 0;
+    if (on && STEP && !halted) y = clamp_len(y, scene_params(c, scene_of(c, v)).r);
+    f3 xn = add(xyz(X), y);
+    const bool changed = (y.x != y0.x || y.y != y0.y || y.z != y0.z);
+    const bool check = on && !halted && np > 0 && changed;
+    bool fail = false, undecided = false;
+    if (check) final_check_planes(c, pl, np, X, xn, lane & (HEAVY_GROUP - 1), HEAVY_GROUP, fail, undecided);
+    const unsigned gbits = (HEAVY_GROUP == 32) ? FULL : (((1u << HEAVY_GROUP) - 1u) << (lane & ~(HEAVY_GROUP - 1)));
+    fail = (__ballot_sync(FULL, fail) & gbits) != 0u;
+    undecided = (__ballot_sync(FULL, undecided) & gbits) != 0u;
+    if (check && fail) {
+        halted = true;
+        y = mk(0.f, 0.f, 0.f);
+        xn = xyz(X);
+        if (leader) atomicAdd(&bc.fhalt, 1u);
+    }
+    if (check && undecided && leader) atomicAdd(&bc.f64, 1u);
     if (leader) {
         if (halted) atomicAdd(&bc.halt, 1u);
         if (cnt) { atomicMax(&bc.maxc, cnt); atomicAdd(&bc.planes, (unsigned long long)cnt); }
@@ -1714,52 +1777,91 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
 }
 
 // Projection, second kernel: the vertices with a violated plane and a long
-// plane list, one warp each (persistent warps taking the queued vertices one
-// at a time from a shared counter: a vertex costs from a few hundred to many
-// thousands of instructions).  Each pass of Alg. 2 is a selection walk over
-// the whole list (select_pass); the last pass can only confirm convergence
-// (any violation there ends in the halt), so it is a single scan.
-// Six blocks of four warps per SM (80 registers).
+// plane list.  Each warp projects 32 / HEAVY_GROUP vertices side by side, one
+// per group of HEAVY_GROUP lanes, and a group takes the next queued vertex
+// from a shared counter as soon as its vertex is done (a vertex costs from a
+// few hundred to many thousands of instructions).  All groups advance in
+// lockstep, one visit per round: each round every busy group selects the next
+// plane of its pass (group_select) and hands it to Alg. 1, whose FP64 steps
+// the groups' first lanes take together (walk_visit_group).  A pass of Alg. 2
+// is the run of visits from its input; it ends when no violated plane is left
+// after the last visited one or once Alg. 1 holds three lines (the iterate no
+// longer moves), and its result is retracted once by eps.  The first
+// selection of a pass also decides convergence: no plane violated at the pass
+// input means Alg. 2 returns it; a violated plane at the input of pass
+// max_passes means the vertex halts.  Six blocks of four warps per SM.
 template <bool STEP>
 __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, const float4* x_b, const float4* x_in,
                                                                     float4* x_out, unsigned char* halt_out) {
     if (STEP && c.flags[1]) return;
     __shared__ BlockCounters bc;
     zero_block_counters(bc);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, gl = lane & (HEAVY_GROUP - 1), leader = lane & ~(HEAVY_GROUP - 1);
     const unsigned nwork = c.work_count[0];
-    auto next = [&]() {
+    const float eps = c.p.eps, eps_dep = c.p.eps_dep;
+    int v = -1;                          // the group's vertex; -1: take the next one; -2: queue drained
+    float4 X = make_float4(0.f, 0.f, 0.f, 0.f), XP = X;
+    f3 y0 = mk(0.f, 0.f, 0.f), ypass = y0;
+    int np = 0, pass = 0;
+    unsigned cnt = 0;
+    const float4* pl = c.planes;
+    bool first = true;
+    Tup cur = tup_none();
+    Walk<double> W;
+    walk_begin(W, ypass);
+    for (;;) {
         unsigned w = 0;
-        if (lane == 0) w = atomicAdd(&c.work_count[2], 1u);
-        return __shfl_sync(FULL, w, 0);
-    };
-    for (unsigned wi = next(); wi < nwork; wi = next()) {
-        const int4 wk = c.work[wi];
-        const int v = wk.x;
-        const float mn = __int_as_float(wk.y);
-        const float4 X = x_b[v];
-        const float4 XP = x_in[v];
-        const f3 y0 = sub(xyz(XP), xyz(X));
-        const unsigned cnt = c.count[v];
-        const int np = (int)min(cnt, (unsigned)c.p.K);
-        const float4* pl = c.planes + (size_t)v * c.p.K;
-        if (lane == 0) atomicAdd(&bc.heavy_planes, (unsigned long long)np);
-        f3 ypass = y0;
-        bool conv = false;
-        for (int pass = 0; pass <= c.p.max_passes; ++pass) {
-            float mnb = mn, dd;
-            if (pass > 0) scan_min_rho(pl, np, ypass, lane, mnb, dd);
-            if (mnb >= 0.f) { conv = true; break; }
-            if (pass == c.p.max_passes) break;
-            f3 ynext;
-            float Dmax;
-            const int nvp = select_pass(c, lane, pl, np, y0, ypass, ynext, Dmax);
-            if (lane == 0) { atomicAdd(&bc.long_pass, 1u); atomicAdd(&bc.nviol, (unsigned)nvp); }
-            ypass = ynext;
+        if (v == -1 && gl == 0) w = atomicAdd(&c.work_count[2], 1u);
+        w = __shfl_sync(FULL, w, leader);
+        if (v == -1) {
+            if (w < nwork) {
+                v = c.work[w].x;
+                X = x_b[v];
+                XP = x_in[v];
+                y0 = sub(xyz(XP), xyz(X));
+                cnt = c.count[v];
+                np = (int)min(cnt, (unsigned)c.p.K);
+                pl = c.planes + (size_t)v * c.p.K;
+                if (gl == 0) atomicAdd(&bc.heavy_planes, (unsigned long long)np);
+                ypass = y0;
+                pass = 0;
+                first = true;
+                cur = tup_none();
+                walk_begin(W, ypass);
+            } else {
+                v = -2;
+            }
         }
-        const bool halted = !conv;
-        finish_vertex<STEP, false>(c, lane, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, false, cnt, bc,
-                            x_out, halt_out);
+        if (__all_sync(FULL, v == -2)) break;
+        const bool sel = v >= 0;
+        const Tup best = group_select(pl, np, W.y, y0, cur, first, sel, lane);
+        bool visit = false, end_pass = false, done = false, halted = false;
+        if (sel) {
+            if (best.d == ~0u) {
+                if (first) done = true;            // converged: no plane violated at the pass input
+                else end_pass = true;
+            } else if (first && pass == c.p.max_passes) {
+                done = halted = true;              // still violated after max_passes passes
+            } else {
+                visit = true;
+                cur = best;
+                first = false;
+            }
+        }
+        walk_visit_group(W, tup_plane(best), visit, eps, eps_dep, lane);
+        if (visit && W.S.m == 3) end_pass = true;
+        if (end_pass) {
+            walk_end(W, eps);
+            if (gl == 0) { atomicAdd(&bc.long_pass, 1u); atomicAdd(&bc.nviol, (unsigned)W.nv); }
+            ypass = W.y;
+            ++pass;
+            first = true;
+            cur = tup_none();
+            walk_begin(W, ypass);
+        }
+        finish_vertex_group<STEP>(c, lane, done, v, X, XP, y0, halted ? mk(0.f, 0.f, 0.f) : ypass, halted, pl, np, cnt,
+                                  bc, x_out, halt_out);
+        if (done) v = -1;
     }
     flush_block_counters(c, bc);
 }
