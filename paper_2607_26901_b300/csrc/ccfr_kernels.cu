@@ -1318,6 +1318,13 @@ template <typename R> __device__ __forceinline__ void walk_visit(Walk<R>& W, flo
 #define CCFR_HEAVY_GROUP 8
 #endif
 constexpr int HEAVY_GROUP = CCFR_HEAVY_GROUP;
+// Extended precision of the heavy projection's Alg. 1 steps (double-float in
+// its place was 47% slower on the cloth stack: the steps then compete with the
+// selection scans for issue slots) and its resident blocks per SM.
+using HeavyR = double;
+#ifndef CCFR_HEAVY_BPS
+#define CCFR_HEAVY_BPS 8
+#endif
 static_assert(HEAVY_GROUP >= 2 && HEAVY_GROUP <= 32 && (HEAVY_GROUP & (HEAVY_GROUP - 1)) == 0,
               "HEAVY_GROUP must be a power of two in [2, 32]");
 
@@ -1330,8 +1337,8 @@ static_assert(HEAVY_GROUP >= 2 && HEAVY_GROUP <= 32 && (HEAVY_GROUP & (HEAVY_GRO
 // FP64 warp instruction occupies the FP64 pipe as long with one active lane
 // as with 32, so the groups share that cost.  The result is the one every
 // lane would compute.
-__device__ __forceinline__ void walk_visit_group(Walk<double>& W, float4 P, bool on, float eps, float eps_dep,
-                                                 int lane) {
+template <typename R>
+__device__ __forceinline__ void walk_visit_group(Walk<R>& W, float4 P, bool on, float eps, float eps_dep, int lane) {
     const int gl = lane & (HEAVY_GROUP - 1), leader = lane & ~(HEAVY_GROUP - 1);
     if (on) {
         ++W.nv;
@@ -1347,13 +1354,13 @@ __device__ __forceinline__ void walk_visit_group(Walk<double>& W, float4 P, bool
         } else if (W.S.m < 3 && !(P.x == W.P0.x && P.y == W.P0.y && P.z == W.P0.z)) {
             if (gl == 0) {
                 if (W.lazy0) {
-                    W.yp = v3_of<double>(W.ypass);
+                    W.yp = v3_of<R>(W.ypass);
                     walk_lazy0(W, W.yp);
                 }
-                const V3<double> nd = v3_of<double>(xyz(P));
-                ortho_step<double>(W.z, xyz(P), nd, plane_b_nd<double>(P.w, nd, W.yp), W.S, eps_dep);
-                const V3<double> yn = v3_add(W.yp, W.z);
-                W.y = mk(XP<double>::to_float(yn.x), XP<double>::to_float(yn.y), XP<double>::to_float(yn.z));
+                const V3<R> nd = v3_of<R>(xyz(P));
+                ortho_step<R>(W.z, xyz(P), nd, plane_b_nd<R>(P.w, nd, W.yp), W.S, eps_dep);
+                const V3<R> yn = v3_add(W.yp, W.z);
+                W.y = mk(XP<R>::to_float(yn.x), XP<R>::to_float(yn.y), XP<R>::to_float(yn.z));
             }
             W.lazy0 = false;
         }
@@ -1789,9 +1796,10 @@ __global__ void __launch_bounds__(256) k_project(DevCtx c, const float4* x_b, co
 // longer moves), and its result is retracted once by eps.  The first
 // selection of a pass also decides convergence: no plane violated at the pass
 // input means Alg. 2 returns it; a violated plane at the input of pass
-// max_passes means the vertex halts.  Six blocks of four warps per SM.
+// max_passes means the vertex halts.  Eight blocks of four warps per SM (64
+// registers, a few spilled: 4% faster than six blocks at 80).
 template <bool STEP>
-__global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, const float4* x_b, const float4* x_in,
+__global__ void __launch_bounds__(PROJ_WARPS * 32, CCFR_HEAVY_BPS) k_project_heavy(DevCtx c, const float4* x_b, const float4* x_in,
                                                                     float4* x_out, unsigned char* halt_out) {
     if (STEP && c.flags[1]) return;
     __shared__ BlockCounters bc;
@@ -1807,7 +1815,7 @@ __global__ void __launch_bounds__(PROJ_WARPS * 32, 6) k_project_heavy(DevCtx c, 
     const float4* pl = c.planes;
     bool first = true;
     Tup cur = tup_none();
-    Walk<double> W;
+    Walk<HeavyR> W;
     walk_begin(W, ypass);
     for (;;) {
         unsigned w = 0;
