@@ -405,10 +405,17 @@ def main():
                 traffic = int(ent["bytes_per_launch"] * units_now[dom] / ent["units"])
         except Exception:
             traffic = None
+    # every kernel of the path against the same roofline (algorithmic bytes per launch / stage time)
+    by_kernel = {}
+    for k_, b_ in alg.items():
+        if kernel_ms[k_] > 0 and b_ > 0:
+            a_ = b_ / (kernel_ms[k_] / 1e3) / 1e9
+            by_kernel[k_] = {"achieved": round(a_, 1), "frac": round(a_ / peak, 4), "launch_ms": round(kernel_ms[k_], 4),
+                             "algorithmic_bytes_per_launch": int(b_)}
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "peak_source": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                 "traffic": traffic, "algorithmic_bytes_per_launch": int(alg[dom]),
-                "launch_ms": round(kernel_ms[dom], 4)}
+                "launch_ms": round(kernel_ms[dom], 4), "by_kernel": by_kernel}
 
     # e2e through the C ABI with host buffers: the same K substeps as the timed
     # region, replayed from its start state (host -> device copy of x and v, the
