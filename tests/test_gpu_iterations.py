@@ -60,6 +60,16 @@ SCENES = {
     # compliance 0 the multipliers do not affect positions, as for the other scenes
     "codimensional 829 verts, compliance 0": lambda: S.codimensional(rod_seg=16, cube_n=3, cloth_bending=0.0,
                                                                      rod_bending=0.0, volume_compliance=0.0),
+    # the contact response of Sec. 3.3 (repulsion, visibility weights, Gauss-Seidel order) in every
+    # iteration; friction off, because its tangential displacement is measured from the substep's
+    # start, which a replay of one iteration from x_c does not carry (friction is checked in one
+    # iteration and by the Coulomb deceleration in test_gpu_response.py)
+    "cloth_stack 3x16x16 response, no friction": lambda: S.with_response(
+        S.cloth_stack(n_side=16, layers=3, speed=0.1, seed=4, jitter=2e-4, plane_capacity=1024),
+        delta=5e-4, k_resp=2.0, mu_s=0.0, mu_k=0.0),
+    "cloth_on_sphere 16x16 response, no friction": lambda: S.with_response(
+        S.cloth_on_sphere(n_side=16, radius=0.05, slices=24, stacks=14, lift=0.002, seed=1, plane_capacity=1024),
+        delta=2e-3, k_resp=200.0, mu_s=0.0, mu_k=0.0),
 }
 
 

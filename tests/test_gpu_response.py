@@ -65,7 +65,10 @@ def test_response_step_parity(orc, name, iters):
     if it == 1:
         assert err[ok].max() <= TOL_REL * L, (name, err[ok].max() / L)
     else:
-        # several iterations: decisions outside the bands can still differ (see the precision test)
+        # several iterations in one shot: a band decision in an early iteration moves its vertex
+        # by up to r and spreads through the later sweeps, so this is a coarse check only; the
+        # strict multi-iteration check replays every iteration of the response scenes from the
+        # GPU's own state (test_gpu_iterations.py, friction off) within 1e-5 L outside the bands
         assert np.mean(err[ok] <= TOL_REL * L) >= 0.99, (name, np.sort(err[ok])[-5:] / L)
 
 
