@@ -143,7 +143,7 @@ typedef struct {
     unsigned long long iterations;                    /* solver iterations executed     */
     unsigned long long steps;                         /* ccfr_step calls                */
     unsigned long long aux[16];                       /* diagnostics: [0] projection passes
-                                                         of the warp-per-vertex walk (long
+                                                         of the group-per-vertex walk (long
                                                          lists), [1] passes of the thread-per-
                                                          vertex walk (short lists), [2]
                                                          violated planes visited until Alg. 1

@@ -1,7 +1,7 @@
 """Alg. 2 on long plane lists (900 and 1,400 planes per vertex, up to a
-capacity of 2,048): the warp-per-vertex kernel selects each next plane of the
-pass order over the whole list (a warp argmin per visit) until Alg. 1 holds
-three lines.  GPU against the oracle, which sorts the planes and walks them,
+capacity of 2,048): the heavy kernel (eight lanes per vertex, four vertices
+per warp) selects each next plane of the pass order over the whole list (the
+group's argmin per visit) until Alg. 1 holds three lines.  GPU against the oracle, which sorts the planes and walks them,
 on identical binary32 planes and inputs.
 
 Input: 48 vertices, each with its own synthetic plane list: normals in a
