@@ -1097,9 +1097,11 @@ __global__ void __launch_bounds__(256, 4) k_pair_narrow(DevCtx c, const float4* 
 // Alg. 1 divides by the dependence measures beta; with nearly dependent planes
 // (beta ~ 1e-3, e.g. two normals 0.05 rad apart) binary32 would lose the
 // result's accuracy, so the steps run in an extended precision R:
-//   double: FP64, for the warp kernels, where the step is one warp-uniform
-//     computation (few instructions; the FP64 pipe, a small fraction of the
-//     binary32 rate on this part, is far from saturated);
+//   double: FP64, for the kernels where a group of lanes works on one vertex
+//     (the step, a few dozen FP64 instructions, runs on the group's first
+//     lane; in the heavy projection the four groups of a warp take theirs in
+//     the same warp instructions, since the FP64 pipe, a small fraction of the
+//     binary32 rate on this part, is charged per warp instruction);
 //   dfl: double-float (two binary32 words, about 48 significant bits;
 //     ccfr_df.cuh), for the one-thread-per-vertex kernel, where 32 steps run
 //     side by side and FP64 would saturate its pipe.
