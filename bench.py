@@ -320,10 +320,10 @@ def main():
         if k == n_warm - 1 and not args.no_autotune:
             # tune on the state the timed substeps start from (scratch copies of x, v: the
             # state does not advance); the last warm-up substep then records the graph
-            tuning, tuned_ms = ctx.autotune(x, v, steps=2, plane_capacity=ctx.capacity)
+            tuning, tuned_ms = ctx.autotune(x, v, steps=4, plane_capacity=ctx.capacity)
         ctx.step(x, v)
     if n_warm == 0 and not args.no_autotune:
-        tuning, tuned_ms = ctx.autotune(x, v, steps=2, plane_capacity=ctx.capacity)
+        tuning, tuned_ms = ctx.autotune(x, v, steps=4, plane_capacity=ctx.capacity)
     torch.cuda.synchronize()
     ctx.reset_stats()
 
