@@ -1904,12 +1904,14 @@ __global__ void __launch_bounds__(128) k_project_short(DevCtx c, const float4* x
         f3 ypass = y0;
         bool conv = false;
         for (int pass = 0; pass <= c.p.max_passes; ++pass) {
-            float mnb = mn;
+            // converged when no plane is violated at the pass input (the scan stops at
+            // the first violated one)
+            bool viol = mn < 0.f;
             if (pass > 0) {
-                mnb = 3.4e38f;
-                for (int j = 0; j < np; ++j) mnb = fminf(mnb, rho_at(ypass, pl[j]));
+                viol = false;
+                for (int j = 0; j < np && !viol; ++j) viol = rho_at(ypass, pl[j]) < 0.f;
             }
-            if (mnb >= 0.f) { conv = true; break; }
+            if (!viol) { conv = true; break; }
             if (pass == c.p.max_passes) break;
             Walk<dfl> W;
             walk_begin(W, ypass);
