@@ -401,7 +401,9 @@ def main():
     if tp.exists():
         try:
             ent = json.loads(tp.read_text()).get("kernels", {}).get(dom)
-            if ent and ent.get("kernel_sha") == kernel_sha() and dom in units_now and ent.get("units") > 0:
+            # only for the recipe it was captured on (bytes per unit depend on the scene)
+            same_recipe = args.workload in ent.get("applies_to", []) if ent else False
+            if ent and same_recipe and ent.get("kernel_sha") == kernel_sha() and dom in units_now and ent.get("units") > 0:
                 traffic = int(ent["bytes_per_launch"] * units_now[dom] / ent["units"])
         except Exception:
             traffic = None
