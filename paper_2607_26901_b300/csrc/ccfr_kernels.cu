@@ -673,6 +673,39 @@ __device__ __forceinline__ void warp_cell_items(const DevCtx& c, int lane, bool 
     }
 }
 
+// The same items as warp_cell_items, cell after cell: each non-empty cell's
+// list is dealt out 32 items per round, item k of the cell to lane k % 32.
+// No owner search per round, at the price of a partial round at the end of
+// each cell; for the oversized primitives, which scan their cells with one
+// query per warp, the search was a third of the loop.  Items come in the same
+// order.
+template <typename F>
+__device__ __forceinline__ void warp_cell_items_seq(const DevCtx& c, int lane, bool has, unsigned b, unsigned pk, F f) {
+    unsigned t0 = 0, cnt = 0;
+    if (has) {
+        t0 = c.bucket_count[b];
+        cnt = c.bucket_count[b + 1] - t0;
+    }
+    unsigned nonempty = __ballot_sync(FULL, cnt > 0u);
+    while (nonempty) {
+        const int j = __ffs(nonempty) - 1;
+        nonempty &= nonempty - 1u;
+        const unsigned tj = __shfl_sync(FULL, t0, j), cj = __shfl_sync(FULL, cnt, j), pj = __shfl_sync(FULL, pk, j);
+        for (unsigned base = 0; base < cj; base += 32) {
+            const unsigned k = base + (unsigned)lane;
+            bool valid = k < cj;
+            float4 i0 = make_float4(0.f, 0.f, 0.f, 0.f), i1 = i0;
+            if (valid) {
+                const unsigned s = tj + k;
+                i0 = c.rec[2 * s];
+                i1 = c.rec[2 * s + 1];
+                valid = __float_as_uint(i1.w) == pj;
+            }
+            f(valid, i0, i1, j);
+        }
+    }
+}
+
 // QK: query table (KIND_TRI: triangles against the vertex table, KIND_EDGE,
 // KIND_PT: against their own table).  Persistent warps stride over the units.
 // A table queried against itself needs only half of the neighbourhood: the
@@ -849,8 +882,10 @@ __device__ __forceinline__ unsigned prim_box(const DevCtx& c, const float4* __re
 // the scan runs at the occupancy of its own small register set.  FALLBACK:
 // the fused scan and narrow phase, run only when the pair buffer of this kind
 // overflowed (k_pair_narrow then left the kind untouched).
+// five blocks per SM (48 registers, a few spilled; 64 and four blocks without the bound)
+constexpr int BIG_MIN_BLOCKS = 5;
 template <int QK, int MODE, bool VE = false, bool FALLBACK = false>
-__global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po,
+__global__ void __launch_bounds__(EMIT_WARPS * 32, BIG_MIN_BLOCKS) k_emit_big(DevCtx c, const float4* __restrict__ x, PairOut po,
                                                               PairBuf pb) {
     if (c.flags[1]) return;
     if (FALLBACK && *pb.count <= (u64)pb.cap) return;
@@ -944,7 +979,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                     b = tbase + (cell_hash(cx, cy, cz, qs) & tmask);
                     pk = cell_pack(cx, cy, cz, qs);
                 }
-                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
+                warp_cell_items_seq(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                     int2 pr = make_int2(-1, -1);
                     if (valid) pr = test(i0, i1);
                     items += valid ? 1ull : 0ull;
@@ -997,7 +1032,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                     b = tb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & tm);
                     pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
                 }
-                warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
+                warp_cell_items_seq(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int) {
                     int2 pr = make_int2(-1, -1);
                     bige_items += valid ? 1ull : 0ull;
                     if (valid && overlaps(i0, i1)) pr = accept((unsigned)__float_as_int(i0.w));
@@ -1017,7 +1052,7 @@ __global__ void __launch_bounds__(EMIT_WARPS * 32) k_emit_big(DevCtx c, const fl
                         b = bb + (cell_hash(bx + dx, by + dy, bz + dz, qs) & bm);
                         pk = cell_pack(bx + dx, by + dy, bz + dz, qs);
                     }
-                    warp_cell_items(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
+                    warp_cell_items_seq(c, lane, has, b, pk, [&](bool valid, float4 i0, float4 i1, int j) {
                         int2 pr = make_int2(-1, -1);
                         bige_items += valid ? 1ull : 0ull;
                         if (valid) {
