@@ -111,3 +111,35 @@ def test_response_is_along_the_normal_and_occlusion_silences_farther_contacts(or
     # farther by less than delta_v: partly visible, moves the vertex further out
     y3, _ = orc.response(y, x, x, two, [phi_near, phi_near + 1e-4], [1, 2], w, P)
     assert (y3 - y1) @ n >= 0.0
+
+
+# the cubic smoothstep 3t^2 - 2t^3 at t = 1/4, 1/2, 3/4 (textbook values:
+# S(1/2) = 1/2 and S(t) + S(1 - t) = 1)
+SMOOTHSTEP_AT = {0.25: 0.15625, 0.5: 0.5, 0.75: 0.84375}
+
+
+@pytest.mark.parametrize("t", sorted(SMOOTHSTEP_AT))
+def test_partly_occluded_contact_acts_with_its_visibility_weight(orc, t):
+    """Two contacts with the same normal, the farther one t * delta_v behind
+    the nearer (F2): the nearer is fully visible and acts first (F4); the
+    farther acts after it as a lone contact whose stiffness is k times its
+    visibility 1 - S(t), S the cubic smoothstep (F2, F3: compliance
+    1 / (k w_c))."""
+    rng = np.random.default_rng(5)
+    n = rng.normal(size=3)
+    n /= np.linalg.norm(n)
+    x = np.zeros(3)
+    y = 1e-4 * rng.normal(size=3)
+    k, dv = 3.0, 2e-4
+    P = orc.make_params(S.default_params(2e-3, 1e-3, delta=1e-3, k_resp=k, delta_v=dv), capacity=0)
+    w = 1e3
+    phi_a = 1e-4 - n @ (y - x)
+    phi_b = phi_a + t * dv
+    two = np.array([[*n, 0.0], [*n, 0.0]])
+    got, _ = orc.response(y, x, x, two, [phi_a, phi_b], [1, 2], w, P)
+    y_a, _ = orc.response(y, x, x, two[:1], [phi_a], [1], w, P)
+    Pw = orc.make_params(S.default_params(2e-3, 1e-3, delta=1e-3, k_resp=k * (1.0 - SMOOTHSTEP_AT[t]),
+                                          delta_v=dv), capacity=0)
+    want, _ = orc.response(y_a, x, x, two[1:], [phi_b], [2], w, Pw)
+    assert (want - y_a) @ n > 1e-7          # the farther contact still acts
+    np.testing.assert_allclose(got - y, want - y, rtol=1e-9, atol=0.0)
