@@ -184,6 +184,31 @@ def test_volume_constraint_is_a_linearised_projection(orc):
     np.testing.assert_allclose(x, xr, atol=1e-15)
 
 
+def test_volume_compliance_halves_the_first_order_correction(orc):
+    """XPBD with compliance alpha (X2): one sweep from lambda = 0 scales the
+    first-order correction of a constraint by S / (S + alpha / dt^2), where
+    S = sum_i w_i |grad_i C|^2.  With alpha = S dt^2 the residual is half the
+    initial error, up to second order.  The gradients are taken by central
+    differences of the signed volume, which is linear in each coordinate."""
+    rest = np.array([[0.0, 0.0, 0.0], [0.1, 0.0, 0.0], [0.02, 0.09, 0.0], [0.03, 0.02, 0.08]])
+    x0 = rest.copy()
+    x0[3, 2] -= 1e-4 * 0.08
+    h = 1e-6
+    S2 = 0.0
+    for i in range(4):
+        for a in range(3):
+            xp, xm = x0.copy(), x0.copy()
+            xp[i, a] += h
+            xm[i, a] -= h
+            g = (orc.tet_volumes6(xp, [[0, 1, 2, 3]])[0] - orc.tet_volumes6(xm, [[0, 1, 2, 3]])[0]) / (2 * h)
+            S2 += 1.0 * g * g
+    dt = S.default_params(2e-3, 1e-3)["dt"]
+    x, v6 = one_tet_step(orc, x0, rest, compliance=S2 * dt * dt)
+    c0 = orc.tet_volumes6(x0, [[0, 1, 2, 3]])[0] - v6
+    c1 = orc.tet_volumes6(x, [[0, 1, 2, 3]])[0] - v6
+    assert abs(c1 / c0 - 0.5) < 1e-3
+
+
 def test_link_compliance_limits(orc):
     """Two vertices joined by one link, stretched 1 mm beyond its 10 mm rest
     length: compliance 0 restores the rest length in one sweep; a compliance

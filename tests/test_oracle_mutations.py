@@ -13,13 +13,18 @@ The parts and what each mutation plants:
   acceptance threshold r instead of 2r, the two sides' shares swapped, side B
   given +n, the unweighted generalized inverse mass, the edge-edge closest
   point with its barycentric weights swapped;
-- Alg. 1 and the overflow rule (R7, R16): the first stored offset negated,
-  the overflow bound taken as the largest offset;
+- Alg. 1 and the overflow rule (R7, R16): the first stored offset negated, a
+  stored line's offset with the wrong sign, a step along the first stored
+  direction instead of the last, the overflow bound taken as the largest
+  offset;
 - the step (Alg. 4, R12-R15, X2): gravity dropped from the prediction, the
   XPBD multiplier's sign flipped, the iterate not restarted from the
   prediction, the regions built at the prediction, the max-step clamp
   dropped, the velocity update multiplied by dt, the first colour starting at
   1, the volume gradient of one corner negated;
+- mixed scenes (X1, X2, X4, X5): volume-interior vertices colliding,
+  point-edge pairs with triangle edges, the links' compliance or the volume
+  compliance ignored;
 - the contact response (Sec. 3.3, F1-F5): the gap taken at the build position,
   static friction against mu_k, a wrong smoothstep, the compliance without the
   visibility weight.
@@ -75,6 +80,10 @@ PINS = {
              TS.test_xpbd_sweep_satisfies_last_colour, TM.test_volume_constraint_is_a_linearised_projection,
              TM.test_link_compliance_limits, TS.test_card_stack_stays_static,
              TS.test_trajectory_is_penetration_free],
+    "mixed": [TM.test_volume_interior_takes_no_part_in_collision, TM.test_no_point_edge_pairs_with_triangle_edges,
+              TM.test_point_edge_candidates_match_definition, TM.test_point_edge_plane_worked_example,
+              TM.test_link_compliance_limits, TM.test_volume_constraint_is_a_linearised_projection,
+              TM.test_volume_compliance_halves_the_first_order_correction],
     "response": [TR.test_rest_gap_is_force_balance, TR.test_no_response_outside_band_and_delta_zero,
                  TR.test_kinetic_friction_decelerates_at_mu_g, TR.test_static_friction_stops_sliding,
                  TR.test_response_is_along_the_normal_and_occlusion_silences_farther_contacts,
@@ -116,6 +125,10 @@ MUTATIONS = {
          "pa[i] = s * x3[3 * A[0] + i] + (1 - s) * x3[3 * A[1] + i];")]),
     # Alg. 1 and the overflow rule
     "Alg. 1 first offset negated": ("projection", [("        S->B[0] = b;\n", "        S->B[0] = -b;\n")]),
+    "Alg. 1 offset of a stored line with the wrong sign": ("projection", [
+        ("double alpha_w = bj - b0 - dot3(dnj, wv);", "double alpha_w = bj + b0 - dot3(dnj, wv);")]),
+    "Alg. 1 step along the first stored direction": ("projection", [
+        ("u[i] = xt[i] + (alpha_u / beta_u) * S->V[m - 1][i];", "u[i] = xt[i] + (alpha_u / beta_u) * S->V[0][i];")]),
     "overflow bound is the largest offset": ("projection", [
         ("if (R->p[k].d < m) m = R->p[k].d;", "if (!(R->p[k].d < m) || m == INFINITY) m = R->p[k].d;")]),
     # the step
@@ -135,6 +148,14 @@ MUTATIONS = {
     "volume gradient of corner 0 negated": ("step", [
         ("for (int k = 0; k < 3; ++k) g[0][k] = -(g[1][k] + g[2][k] + g[3][k]);",
          "for (int k = 0; k < 3; ++k) g[0][k] = g[1][k] + g[2][k] + g[3][k];")]),
+    # mixed scenes
+    "interior volume vertices collide (X5)": ("mixed", [
+        ("t->collides[i] = used[i] != 2;", "t->collides[i] = 1;")]),
+    "point-edge pairs with triangle edges (X4)": ("mixed", [("    if (!t->free_edge[e]) return 0;\n", "")]),
+    "links take the edges' compliance (X1)": ("mixed", [
+        ("dcomp[ne + l] = ex->link_compliance[l];", "dcomp[ne + l] = P->compliance;")]),
+    "volume compliance ignored (X2)": ("mixed", [
+        ("double atv = ex ? ex->volume_compliance / (dt * dt) : 0.0;", "double atv = 0.0;")]),
     # the contact response
     "response gap at the build position": ("response", [
         ("double C = P->delta - (phi[all[a].k] + dot3(n, d));", "double C = P->delta - phi[all[a].k];")]),
