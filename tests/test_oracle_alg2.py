@@ -162,3 +162,49 @@ def test_pins_catch_mutation(mutation):
         except AssertionError:
             caught.append(name)
     assert caught, f"no pin catches the mutation {mutation!r}"
+
+
+def _without_exact_copies(R):
+    """The regions with every plane that repeats an earlier plane of the same
+    vertex bit for bit (n and d) removed; each list keeps its key order."""
+    offs, planes, keys = R["offs"], R["planes"], R["key"]
+    keep = np.zeros(len(planes), bool)
+    for v in range(len(offs) - 1):
+        a, b = offs[v], offs[v + 1]
+        if a < b:
+            bits = np.ascontiguousarray(planes[a:b]).view(np.uint64).reshape(-1, 4)
+            keep[a + np.unique(bits, axis=0, return_index=True)[1]] = True
+    vert = np.repeat(np.arange(len(offs) - 1), np.diff(offs))
+    noffs = np.concatenate([[0], np.cumsum(np.bincount(vert[keep], minlength=len(offs) - 1))])
+    return noffs, planes[keep], keys[keep]
+
+
+@pytest.mark.parametrize("make,step_first", [
+    (lambda: S.cloth_stack(n_side=12, layers=4, speed=0.5, seed=5, iters=3), True),
+    (lambda: S.card_stack(n_cards=8), False),
+])
+def test_alg2_unchanged_by_exact_copies_of_planes(orc, make, step_first):
+    """A plane that repeats one of the vertex's planes bit for bit (one
+    contact reached through several pairs) changes nothing in Alg. 2: the copy
+    has the same rho as the original at every iterate, so it is violated
+    exactly when the original is, and once Alg. 1 holds the original its copy
+    is dependent (beta = 0).  Results and halts are bitwise those of the lists
+    without copies; only the count of violated planes differs."""
+    sc = make()
+    P = orc.make_params(sc.params, capacity=0)
+    x3 = sc.x[:, :3].astype(np.float64)
+    if step_first:                       # leave the exactly parallel start
+        rest = orc.rest_lengths(x3, sc.edges)
+        x3, _, _, _ = orc.step(x3, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, rest, P)
+    x4 = sc.x.copy()
+    x4[:, :3] = x3
+    R = orc.build_regions(x3, x4, sc.edges, sc.tris, P)
+    noffs, nplanes, nkeys = _without_exact_copies(R)
+    assert len(nplanes) < len(R["planes"])
+    for seed in range(3):
+        xp = x3 + np.random.default_rng(seed).normal(scale=2e-3, size=x3.shape)
+        a = orc.project(x3, xp, sc.x[:, 3], R["offs"], R["planes"], R["key"], None, P)
+        b = orc.project(x3, xp, sc.x[:, 3], noffs, nplanes, nkeys, None, P)
+        np.testing.assert_array_equal(a[0], b[0])
+        np.testing.assert_array_equal(a[1], b[1])
+        assert a[1].sum() > 0 or not step_first
