@@ -148,3 +148,30 @@ def test_card_stack_stays_static(orc):
     yc = x[cards, 1].reshape(-1, 4).mean(axis=1)
     assert np.all(np.diff(yc) >= sc.params["xi"] - 1e-9)
     assert np.all(yc <= y0[cards].reshape(-1, 4).mean(axis=1) + 1e-12)
+
+
+def test_threads_do_not_change_results(orc):
+    """The oracle's OpenMP loops run over independent queries, pairs,
+    vertices and same-colour constraints, and every list is put in its one
+    order (by vertex and key) before use: one thread and all threads give
+    bitwise the same regions and the same step."""
+    sc = S.cloth_stack(n_side=10, layers=3, speed=0.5, seed=8, iters=4)
+    P = orc.make_params(sc.params, capacity=0)
+    x = sc.x[:, :3].astype(np.float64)
+    rest = orc.rest_lengths(x, sc.edges)
+    outs = []
+    try:
+        for threads in (1, 0):
+            orc.set_threads(threads)
+            R = orc.build_regions(x, sc.x, sc.edges, sc.tris, P)
+            xs, vs, info, band = orc.step(x, sc.v[:, :3].astype(np.float64), sc.x, sc.edges, sc.tris, rest, P)
+            outs.append((R, xs, vs, (info.planes, info.violated, info.halts, info.iters_run), band))
+    finally:
+        orc.set_threads(0)
+    (R1, x1, v1, i1, b1), (R2, x2, v2, i2, b2) = outs
+    for k in ("offs", "planes", "phi", "key", "vflag"):
+        np.testing.assert_array_equal(R1[k], R2[k])
+    np.testing.assert_array_equal(x1, x2)
+    np.testing.assert_array_equal(v1, v2)
+    np.testing.assert_array_equal(b1, b2)
+    assert i1 == i2 and i1[0] > 0 and i1[1] > 0
