@@ -40,3 +40,21 @@ def test_card_stack_recipe():
     assert movable.sum() == 52 * 4
     y = np.sort(sc.x[movable, 1].reshape(-1, 4).mean(axis=1))
     np.testing.assert_allclose(np.diff(y), 1.5e-3, rtol=1e-5)
+
+
+def test_workload_recipes_have_their_stated_sizes():
+    """The three single-scene workloads at full size: vertex, edge and
+    triangle counts and the parameters their recipes state."""
+    c1 = S.config(1)
+    assert (c1.n_verts, len(c1.tris)) == (1024 + 2002, 1922 + 4000)
+    assert (c1.params["r"], c1.params["xi"], c1.params["iters"]) == (5e-3, 1e-3, 10)
+    assert int((c1.x[:, 3] > 0).sum()) == 1024                 # the sphere is static
+    c2 = S.config(2)
+    assert (c2.n_verts, len(c2.edges), len(c2.tris)) == (262144, 782340, 520200)
+    assert (c2.params["r"], c2.params["xi"], c2.params["iters"], c2.params["plane_capacity"]) == \
+        (2e-3, 1e-3, 20, 1024)
+    assert np.abs(c2.v[:, :3]).max() <= 0.5
+    c3 = S.config(3)
+    strands = int((c3.x[:, 3] > 0).sum())
+    assert strands == 128 * 128 * 65 and len(c3.tris) == 0
+    assert (c3.params["r"], c3.params["xi"], c3.params["iters"]) == (1e-3, 5e-4, 10)
