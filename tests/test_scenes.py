@@ -58,3 +58,17 @@ def test_workload_recipes_have_their_stated_sizes():
     strands = int((c3.x[:, 3] > 0).sum())
     assert strands == 128 * 128 * 65 and len(c3.tris) == 0
     assert (c3.params["r"], c3.params["xi"], c3.params["iters"]) == (1e-3, 5e-4, 10)
+
+
+def test_batch_recipe():
+    """512 independent scenes of uneven sizes: movable vertices within the
+    clipped range (a cloth's side is rounded), about a fifth particle clouds,
+    each over a static sphere."""
+    scenes = S.batch()
+    assert len(scenes) == 512
+    movable = np.array([int((s.x[:, 3] > 0).sum()) for s in scenes])
+    assert movable.min() >= 1024 - 2 * 32 and movable.max() <= 65536 + 2 * 256 + 1
+    n_particles = sum("particle_cloud" in s.name for s in scenes)
+    assert 0.12 < n_particles / 512 < 0.28
+    assert all((s.x[:, 3] == 0).any() for s in scenes)
+    assert movable.sum() == 5340148                 # the seeded recipe: about 5.3 M movable vertices
